@@ -1,0 +1,344 @@
+"""Pins of the FP64 oracle against things other than itself: closed forms of
+Chebyshev derivatives, brute-force polynomial interpolation, symbolic
+calculus, the paper's manufactured solutions and printed boundary data, and
+invariants (exactness for polynomials, dot-product test, finite differences).
+CPU only."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import sympy as sp
+
+import oracle as O
+import workloads as W
+
+
+# ---------------------------------------------------------------- nodes / D
+
+@pytest.mark.parametrize("N", [2, 3, 4, 7, 8, 16, 33])
+def test_nodes_are_cgl(N):
+    x = O.cgl_nodes(N)
+    ref = np.cos(np.pi * np.arange(N + 1) / N)
+    assert np.allclose(x, ref, atol=2e-16 * N)
+    assert x[0] == 1.0 and x[-1] == -1.0
+    assert np.array_equal(x, -x[::-1])
+    t = O.cgl_nodes(N, 0.0, 2.0)
+    assert np.allclose(t, x + 1.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 7, 8, 16, 32, 64])
+def test_D_differentiates_each_Tk_exactly(N):
+    """(D T_k)(x_n) = k sin(k th)/sin(th) inside, k^2 at x=+1 and (-1)^(k+1) k^2
+    at x=-1 (endpoint formulas of Sec. 2.2; T_k = cos k th, Sec. 2.1)."""
+    x = O.cgl_nodes(N)
+    th = np.pi * np.arange(N + 1) / N
+    D = O.diff_matrix(N)
+    for k in range(N + 1):
+        Tk = np.cos(k * th)
+        d = D @ Tk
+        ex = np.empty(N + 1)
+        ex[1:-1] = k * np.sin(k * th[1:-1]) / np.sin(th[1:-1])
+        ex[0] = k * k
+        ex[-1] = (-1) ** (k + 1) * k * k
+        assert np.abs(d - ex).max() <= 1e-14 * max(1, k * k) * N, (N, k)
+    assert np.abs(D @ np.ones(N + 1)).max() < 1e-13 * N * N
+    assert np.abs(D @ x - 1.0).max() < 1e-13 * N * N
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_D_matches_brute_force_interpolant(N):
+    """Fit the degree-N polynomial through random nodal data with numpy's
+    polynomial module, differentiate it symbolically, evaluate at the nodes."""
+    g = W.rng(N)
+    x = np.cos(np.pi * np.arange(N + 1) / N)
+    f = g.standard_normal(N + 1)
+    c = np.polynomial.polynomial.polyfit(x, f, N)
+    dref = np.polynomial.polynomial.polyval(x, np.polynomial.polynomial.polyder(c))
+    assert np.allclose(O.diff_matrix(N) @ f, dref, atol=1e-11, rtol=1e-11)
+
+
+@pytest.mark.parametrize("N", [4, 9, 16, 31])
+def test_D_diagonal_closed_form(N):
+    D = O.diff_matrix(N)
+    x = np.cos(np.pi * np.arange(N + 1) / N)
+    d00 = (2 * N * N + 1) / 6.0
+    assert abs(D[0, 0] - d00) < 1e-12 * d00
+    assert abs(D[N, N] + d00) < 1e-12 * d00
+    inner = -x[1:-1] / (2 * (1 - x[1:-1] ** 2))
+    assert np.allclose(np.diag(D)[1:-1], inner, atol=1e-11 * N * N)
+
+
+def test_affine_scaling():
+    """Physical derivative = (2/(b-a)) x reference derivative (Sec. 2.2)."""
+    N, a, b = 12, 0.25, 3.0
+    t = O.cgl_nodes(N, a, b)
+    D = O.diff_matrix(N, a, b)
+    assert np.allclose(D @ (t ** 3 - 2 * t), 3 * t ** 2 - 2, atol=1e-11)
+
+
+@pytest.mark.parametrize("N", [4, 8, 12, 16, 32])
+def test_cc_weights_integrate_polynomials(N):
+    t = O.cgl_nodes(N, -0.5, 2.0)
+    w = O.cc_weights(N, -0.5, 2.0)
+    for k in range(N + 1):
+        exact = (2.0 ** (k + 1) - (-0.5) ** (k + 1)) / (k + 1)
+        assert abs(w @ t ** k - exact) < 1e-12 * max(1.0, abs(exact)) * N
+
+
+# ---------------------------------------------------------------- owners
+
+def test_owner_rules_by_hand():
+    """Dirichlet beats Neumann; among one type the lowest axis owns.
+    bc = x-:N, x+:D, y-:N, y+:N, z-:D, z+:N on a 3^3 grid."""
+    g = O.Grid((3, 3, 3), bc=[1, 0, 1, 1, 0, 1])
+    own = O.owners(g)
+    # index 0 = hi side, index 2 = lo side; array is [z][y][x]
+    assert own[1, 1, 1] == -1
+    assert own[1, 1, 0] == 1          # x+ (Dirichlet) face centre
+    assert own[1, 1, 2] == 0          # x- (Neumann) face centre
+    assert own[2, 1, 1] == 4          # z- Dirichlet
+    assert own[0, 1, 1] == 5          # z+ Neumann
+    assert own[1, 0, 2] == 0          # x- & y+ both Neumann -> x owns
+    assert own[2, 0, 2] == 4          # x-(N), y+(N), z-(D) corner -> z- (Dirichlet)
+    assert own[0, 0, 0] == 1          # x+(D) beats z+(N), y+(N)
+    assert own[0, 2, 1] == 2          # y-(N) vs z+(N) -> y
+    assert own[2, 2, 0] == 1          # x+(D) vs z-(D) -> x (lowest axis)
+
+
+# ---------------------------------------------------------------- operator
+
+def _sym_problem():
+    X, Y, Z = sp.symbols("x y z")
+    K = 1 + sp.Rational(1, 2) * X * Y + sp.Rational(1, 4) * Z ** 2
+    u = X ** 2 * Y + Y * Z ** 3 + X * Z - 2 * Y ** 2
+    Lu = -(sp.diff(K * sp.diff(u, X), X) + sp.diff(K * sp.diff(u, Y), Y)
+           + sp.diff(K * sp.diff(u, Z), Z))
+    return [sp.lambdify((X, Y, Z), e, "numpy") for e in (K, u, Lu)]
+
+
+@pytest.mark.parametrize("n", [(6, 6, 6), (7, 5, 8)])
+def test_operator_exact_for_polynomial_K_and_u(n):
+    """-div(K grad u) for polynomial K, u whose fluxes have degree <= N per axis
+    is reproduced exactly at the nodes; closed form from sympy."""
+    Kf, uf, Lf = _sym_problem()
+    g = O.Grid(n, lo=(-1.0, 0.0, -0.5), hi=(1.0, 2.0, 1.5))
+    X, Y, Z = g.mesh()
+    K = Kf(X, Y, Z) * np.ones_like(X)
+    u = uf(X, Y, Z) * np.ones_like(X)
+    L = O.interior_operator(u, K, g)
+    assert np.allclose(L, Lf(X, Y, Z), atol=1e-10 * np.abs(L).max())
+
+
+def test_operator_K_placement_matters():
+    """A swapped K (K grad(grad u) instead of grad(K grad u)) fails the pin above;
+    checks the pin's power to catch a transposed operand."""
+    Kf, uf, Lf = _sym_problem()
+    g = O.Grid((7, 7, 7))
+    X, Y, Z = g.mesh()
+    K, u = Kf(X, Y, Z), uf(X, Y, Z)
+    wrong = -sum(K * O.grad(O.grad(u, g, a), g, a) for a in range(3))
+    assert not np.allclose(wrong, Lf(X, Y, Z), atol=1e-6)
+
+
+@pytest.mark.parametrize("bc", [list(t) for t in itertools.product([0, 1], repeat=6)][1::9])
+def test_apply_matches_kronecker_assembly(bc):
+    if all(bc):
+        bc[0] = 0
+    g = O.Grid((5, 4, 3), lo=(0, -1, 2), hi=(1, 1, 3.5), bc=bc)
+    u = W.random_field(g.shape, 1)
+    K = W.random_positive_field(g.shape, 2)
+    A = O.assemble(K, g)
+    assert np.allclose(O.apply(u, K, g).ravel(), A @ u.ravel(), rtol=1e-13, atol=1e-12 * np.abs(A).max())
+
+
+def test_every_mixed_bc_set_is_nonsingular_pure_neumann_singular():
+    g0 = O.Grid((5, 5, 5))
+    K = W.random_positive_field(g0.shape, 3)
+    for bc in itertools.product([0, 1], repeat=6):
+        g = O.Grid((5, 5, 5), bc=bc)
+        A = O.assemble(K, g)
+        sv = np.linalg.svd(A, compute_uv=False)
+        if all(bc):
+            assert sv[-1] / sv[0] < 1e-12
+        else:
+            assert sv[-1] / sv[0] > 1e-8, bc
+
+
+# ---------------------------------------------------------------- solves
+
+@pytest.mark.parametrize("bc", [[0, 0, 0, 0, 0, 0], [0, 1, 1, 1, 1, 1], [1, 0, 0, 1, 1, 0]])
+def test_polynomial_solution_is_exact(bc):
+    """Any u of degree <= N per axis is the exact discrete solution (f = -lap u,
+    consistent Dirichlet/Neumann data)."""
+    g = O.Grid((7, 6, 8), lo=(0, 0, -1), hi=(1, 2, 1), bc=bc)
+    coeffs = {(3, 2, 1): 0.5, (1, 0, 4): -1.0, (0, 3, 2): 0.25, (2, 2, 2): 1.0, (0, 0, 0): 2.0}
+    fn = lambda X, Y, Z: W.polynomial_3d(coeffs, X, Y, Z)
+    X, Y, Z = g.mesh()
+    u, _, lap = fn(X, Y, Z)
+    faces = W.face_values(bc, g.nodes(0), g.nodes(1), g.nodes(2), fn)
+    b = O.rhs(-lap, faces, g)
+    us = O.solve_direct(np.ones(g.shape), b, g)
+    assert np.abs(us - u).max() < 1e-11 * np.abs(u).max()
+
+
+def test_paper_3d_boundary_data_signs():
+    """The paper's printed face data for u = exp(x+y+z) + x^2 + 2y - z^2 on
+    (0,1)^3 (Sec. 3.2): grad u . n = -(e^{x+z} + 2) on y=0, e^{x+1+z} + 2 on
+    y=1, e^{x+y+1} - 2 on z=1; u = e^{y+z} + 2y - z^2 on x=0."""
+    bc = [0, 0, 1, 1, 0, 1]
+    g = O.Grid((6, 6, 6), (0, 0, 0), (1, 1, 1), bc)
+    x, y, z = g.nodes(0), g.nodes(1), g.nodes(2)
+    faces = W.face_values(bc, x, y, z, W.paper_exp_poly_3d)
+    Zz, Xx = np.meshgrid(z, x, indexing="ij")
+    assert np.allclose(faces[2], -(np.exp(Xx + Zz) + 2))
+    assert np.allclose(faces[3], np.exp(Xx + 1 + Zz) + 2)
+    Yy, Xx2 = np.meshgrid(y, x, indexing="ij")
+    assert np.allclose(faces[5], np.exp(Xx2 + Yy + 1) - 2)
+    Zz, Yy = np.meshgrid(z, y, indexing="ij")
+    assert np.allclose(faces[0], np.exp(Yy + Zz) + 2 * Yy - Zz ** 2)
+
+
+def test_paper_3d_manufactured_accuracy():
+    """Sec. 3.2: max local relative error below 1e-9 from N = 8 on."""
+    bc = [0, 0, 1, 1, 0, 1]
+    errs = {}
+    for N in (4, 6, 8, 12):
+        g = O.Grid((N + 1,) * 3, (0, 0, 0), (1, 1, 1), bc)
+        X, Y, Z = g.mesh()
+        u, _, lap = W.paper_exp_poly_3d(X, Y, Z)
+        faces = W.face_values(bc, g.nodes(0), g.nodes(1), g.nodes(2), W.paper_exp_poly_3d)
+        us = O.solve_direct(np.ones(g.shape), O.rhs(-lap, faces, g), g)
+        errs[N] = (np.abs(us - u) / np.abs(u)).max()
+    assert errs[8] < 1e-9
+    assert errs[12] < 1e-12
+    assert errs[4] > errs[6] > errs[8] > errs[12]
+
+
+def test_paper_1d_poisson_spectral_decay():
+    """Sec. 3.1: u'' = exp(4x), u(+-1) = 0; geometric error decay reaching
+    machine precision near N = 64."""
+    errs = []
+    for N in (8, 12, 16, 20, 64):
+        g = O.Grid((N + 1,))
+        X, Y, Z = g.mesh()
+        u, _, lap = W.paper_exp4x_1d(X, Y, Z)
+        faces = W.face_values(g.bc, g.nodes(0), g.nodes(1), g.nodes(2), W.paper_exp4x_1d, dim=1)
+        us = O.solve_direct(np.ones(g.shape), O.rhs(-lap, faces, g), g)
+        errs.append(np.abs(us - u).max())
+    assert errs[0] > errs[1] > errs[2] > errs[3]
+    assert errs[-1] < 1e-12
+
+
+def test_config1_manufactured_1d():
+    """u = exp(x) sin(3x), Dirichlet at x = -1, Neumann u'(1) = e (sin 3 + 3 cos 3)."""
+    bc = [0, 1, 0, 0, 0, 0]
+    g = O.Grid((33,), bc=bc)
+    X, Y, Z = g.mesh()
+    u, _, lap = W.exp_sin3_1d(X, Y, Z)
+    faces = W.face_values(bc, g.nodes(0), g.nodes(1), g.nodes(2), W.exp_sin3_1d, dim=1)
+    assert abs(faces[1].item() - math.e * (math.sin(3) + 3 * math.cos(3))) < 1e-14
+    us = O.solve_direct(np.ones(g.shape), O.rhs(-lap, faces, g), g)
+    assert np.abs(us - u).max() < 1e-12
+
+
+def test_gmres_matches_direct():
+    g = O.Grid((7, 6, 5), bc=[0, 1, 1, 0, 1, 1])
+    K = W.random_positive_field(g.shape, 7)
+    b = W.random_field(g.shape, 8)
+    ud = O.solve_direct(K, b, g)
+    ug, info = O.gmres(lambda v: O.apply(v, K, g), b, rtol=1e-14, restart=60, maxiter=5000)
+    A = O.assemble(K, g)
+    tol = np.linalg.cond(A) * 1e-15 * 10
+    assert np.linalg.norm(ug - ud) / np.linalg.norm(ud) < max(tol, 1e-10)
+
+
+def test_elimination_equals_row_replacement():
+    """The paper's G/H elimination (Sec. 2.3.1) and row replacement give one solution."""
+    bc = [1, 0, 1, 1, 0, 1]
+    g = O.Grid((6, 5, 7), lo=(0, 0, 0), hi=(1, 1, 2), bc=bc)
+    K = W.random_positive_field(g.shape, 11)
+    f = W.random_field(g.shape, 12)
+    faces = [W.random_field(s, 20 + i) for i, s in enumerate(
+        [(7, 5), (7, 5), (7, 6), (7, 6), (5, 6), (5, 6)])]
+    u1 = O.solve_direct(K, O.rhs(f, faces, g), g)
+    u2 = O.eliminate_solve(K, f, faces, g)
+    assert np.allclose(u1, u2, atol=1e-10 * np.abs(u1).max())
+
+
+# ---------------------------------------------------------------- prolongation
+
+@pytest.mark.parametrize("Nc", [2, 3, 4, 8, 16])
+def test_prolongation_exact_for_each_Tk(Nc):
+    Nf = 2 * Nc
+    P = O.barycentric_matrix(Nc, Nf)
+    xc, xf = O.cgl_nodes(Nc), O.cgl_nodes(Nf)
+    for k in range(Nc + 1):
+        assert np.allclose(P @ np.cos(k * np.arccos(xc)), np.cos(k * np.arccos(xf)), atol=1e-13)
+    assert np.allclose(P[::2], np.eye(Nc + 1))
+
+
+def test_prolongation_3d_and_injection():
+    gc = O.Grid((9, 5, 7), lo=(0, -1, 0), hi=(2, 1, 1))
+    gf = O.Grid((17, 9, 13), lo=(0, -1, 0), hi=(2, 1, 1))
+    coeffs = {(8, 0, 0): 1.0, (3, 4, 6): -0.5, (0, 2, 1): 2.0}
+    Xc, Yc, Zc = gc.mesh()
+    Xf, Yf, Zf = gf.mesh()
+    uc = W.polynomial_3d(coeffs, Xc, Yc, Zc)[0]
+    uf = W.polynomial_3d(coeffs, Xf, Yf, Zf)[0]
+    up = O.prolong(uc, gc, gf)
+    assert np.allclose(up, uf, atol=1e-12 * np.abs(uf).max())
+    assert np.array_equal(O.restrict_inject(up, gc, gf), uc)
+    assert O.e_ref(uf, up) < 1e-13
+
+
+# ---------------------------------------------------------------- adjoint
+
+def test_adjoint_dot_product_and_dense_transpose():
+    g = O.Grid((6, 5, 7), bc=[1, 0, 1, 1, 0, 1])
+    K = W.random_positive_field(g.shape, 31)
+    x = W.random_field(g.shape, 32)
+    y = W.random_field(g.shape, 33)
+    Ax = O.apply(x, K, g)
+    ATy = O.adjoint_apply(y, K, g)
+    assert abs((Ax * y).sum() - (x * ATy).sum()) < 1e-12 * np.abs(Ax).max() * np.abs(y).sum()
+    A = O.assemble(K, g)
+    assert np.allclose(ATy.ravel(), A.T @ y.ravel(), atol=1e-11 * np.abs(A).max())
+
+
+def test_grad_K_against_central_differences():
+    """J(K) = <c, u(K)>: adjoint gradient vs central finite differences."""
+    g = O.Grid((6, 6, 5), bc=[0, 0, 1, 1, 1, 0])
+    K = W.random_positive_field(g.shape, 41)
+    b = W.random_field(g.shape, 42)
+    c = W.random_field(g.shape, 43)
+    u = O.solve_direct(K, b, g)
+    lam = O.adjoint_solve_direct(K, c, g)
+    gK = O.grad_K(u, lam, g)
+    dK = W.random_field(g.shape, 44)
+    h = 1e-5
+    Jp = (c * O.solve_direct(K + h * dK, b, g)).sum()
+    Jm = (c * O.solve_direct(K - h * dK, b, g)).sum()
+    fd = (Jp - Jm) / (2 * h)
+    assert abs(fd - (gK * dK).sum()) < 1e-7 * abs(fd)
+    # dJ/db = lambda
+    db = W.random_field(g.shape, 45)
+    fdb = ((c * O.solve_direct(K, b + h * db, g)).sum() - (c * O.solve_direct(K, b - h * db, g)).sum()) / (2 * h)
+    assert abs(fdb - (lam * db).sum()) < 1e-7 * abs(fdb)
+
+
+# ---------------------------------------------------------------- Picard
+
+def test_picard_fixed_point():
+    bc = [0, 0, 1, 1, 0, 1]
+    g = O.Grid((7, 7, 7), bc=bc)
+    X, Y, Z = g.mesh()
+    K0 = W.lognormal_conductivity(X, Y, Z, seed=5)
+    faces = W.face_values(bc, g.nodes(0), g.nodes(1), g.nodes(2),
+                          lambda X, Y, Z: (X, (np.ones_like(X), 0 * X, 0 * X), 0 * X))
+    b = O.rhs(np.zeros(g.shape), faces, g)
+    u, info = O.picard_solve(K0, b, g, tol=1e-13, maxit=400)
+    K = O.picard_conductivity(K0, u, g)
+    r = O.apply(u, K, g) - b
+    assert np.linalg.norm(r) < 1e-9 * np.linalg.norm(b)
+    assert info["iterations"] > 2
