@@ -1,0 +1,135 @@
+/*
+ * cheb.h - C ABI of the B300 Chebyshev-collocation diffusion solver.
+ *
+ * The library solves -div(K grad u) = f on a box [lo, hi] (1-D, 2-D or 3-D)
+ * by collocation at the Chebyshev-Gauss-Lobatto (CGL) points with per-face
+ * Dirichlet / Neumann data (Quecedo & Segurado, "An FFT-based solver with
+ * general boundary conditions for stationary diffusion problems based on
+ * Chebyshev collocation", Sec. 2).  Every numerical step runs in the
+ * library's own CUDA kernels for sm_103a; the header uses plain pointers
+ * and sizes only.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: n[a] points along axis a (x = 0, y = 1, z = 2), N_a = n[a] - 1.
+ *    Node j of axis a sits at t_j = (hi-lo)/2 cos(pi j / N_a) + (hi+lo)/2
+ *    (Sec. 2.2, affine mapping): node 0 is the hi end, node N_a the lo end.
+ *    Unused axes of 1-D / 2-D problems have n = 1.  Active axes need n >= 3.
+ *  - Fields: row-major [nz][ny][nx] arrays (x fastest), device memory,
+ *    double (FP64) or float (FP32) as the call states.  The caller owns
+ *    every field buffer; buffers of one call must not overlap unless stated.
+ *  - Faces: id f = 2a + side, side 0 = lo, side 1 = hi: x-, x+, y-, y+, z-, z+.
+ *    Face data of face f is a device array shaped like a field with axis a
+ *    removed (x faces [nz][ny], y faces [nz][nx], z faces [ny][nx]).
+ *  - Boundary rows (Sec. 2 "Extension to the three-dimensional setting":
+ *    equations at boundary nodes are replaced by the boundary conditions):
+ *    each boundary node has ONE owner face; Dirichlet faces beat Neumann
+ *    faces, and among faces of one type the lowest axis wins.  A Dirichlet
+ *    row reads u_p = g; a Neumann row reads n.grad u = g with n the outward
+ *    normal (+d_a u on the hi face, -d_a u on the lo face).
+ *  - Streams: every call is ordered on the plan's stream.  Calls that
+ *    return data to the host (solves, norms) synchronise that stream.
+ *  - Errors: every function returns a cheb_status; no call aborts the
+ *    process.  CHEB_ERR_ARG leaves outputs untouched.  CHEB_ERR_CUDA
+ *    reports a failed CUDA call (message in cheb_last_error()).
+ */
+#ifndef CHEB_H
+#define CHEB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cheb_plan_s* cheb_plan;
+
+enum cheb_bc { CHEB_DIRICHLET = 0, CHEB_NEUMANN = 1 };
+
+/* arithmetic of an operator application (buffer element type) */
+enum cheb_prec { CHEB_FP64 = 0, CHEB_FP32 = 1 };
+
+/* solve mode: plain FP64 LGMRES, or FP32 inner LGMRES inside an FP64
+ * iterative-refinement loop */
+enum cheb_solve_mode { CHEB_SOLVE_FP64 = 0, CHEB_SOLVE_MIXED = 1 };
+
+/* per-axis line-derivative route: FFT-based DCT-I + recurrence, or the
+ * dense differentiation matrix.  CHEB_ROUTE_AUTO lets the plan choose. */
+enum cheb_route { CHEB_ROUTE_AUTO = -1, CHEB_ROUTE_TRANSFORM = 0, CHEB_ROUTE_DENSE = 1 };
+
+enum cheb_status {
+  CHEB_OK = 0,
+  CHEB_ERR_NOT_CONVERGED = 1,   /* solve stopped at maxiter; best iterate written */
+  CHEB_ERR_ARG = -1,            /* invalid argument (null pointer, bad size, ...) */
+  CHEB_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  CHEB_ERR_NOMEM = -3,          /* device allocation failed */
+  CHEB_ERR_NONFINITE = -4,      /* NaN / Inf met in a residual norm */
+  CHEB_ERR_SINGULAR_BC = -5,    /* no Dirichlet face: A is singular */
+  CHEB_ERR_UNSUPPORTED = -6     /* size / route combination not supported */
+};
+
+/* Create a plan for one grid.
+ *   dim      1, 2 or 3 (the first dim axes are active)
+ *   n        points per axis, n[a] >= 3 for a < dim, n[a] = 1 otherwise
+ *            (route TRANSFORM needs n - 1 a power of two, 4 <= n - 1 <= 512;
+ *             route DENSE needs n <= 129; every axis needs one of them)
+ *   lo, hi   interval of each axis (hi > lo); entries of unused axes ignored
+ *   bc_type  six CHEB_DIRICHLET / CHEB_NEUMANN values, faces x-,x+,y-,y+,z-,z+
+ *   stream   cudaStream_t to order the plan's work on (NULL = legacy stream)
+ * The plan owns its device tables and, once a solve runs, its Krylov
+ * workspace; cheb_plan_destroy frees them.  A pure-Neumann set is accepted
+ * here (cheb_apply is defined for it) but cheb_solve rejects it with
+ * CHEB_ERR_SINGULAR_BC. */
+int cheb_plan_create(cheb_plan* out, int dim, const int n[3], const double lo[3],
+                     const double hi[3], const int bc_type[6], void* stream);
+int cheb_plan_destroy(cheb_plan plan);
+int cheb_plan_set_stream(cheb_plan plan, void* stream);
+
+/* Force the line-derivative route of one axis (CHEB_ROUTE_*); fails with
+ * CHEB_ERR_UNSUPPORTED when the axis size does not allow it. */
+int cheb_plan_set_route(cheb_plan plan, int axis, int route);
+int cheb_plan_get_route(cheb_plan plan, int axis, int* route);
+
+/* Host copy of the CGL coordinates of one axis (n[axis] doubles, node 0 =
+ * hi end).  Callers sample f, K and face data at these points. */
+int cheb_nodes(cheb_plan plan, int axis, double* out_host);
+
+/* Number of grid points nx*ny*nz. */
+size_t cheb_plan_size(cheb_plan plan);
+
+/* One first-derivative line pass (Alg. 1 semantics; Sec. 2.2):
+ * du = d u / d t_axis at every node, computed per line as forward DCT-I
+ * to Chebyshev coefficients, the backward derivative recurrence
+ * b_{k-1} = b_{k+1} + 2k a_k (k = N..1, b_0 halved) and the inverse DCT-I,
+ * times 2/(hi-lo).  u, du: device fields of type prec; must not overlap. */
+int cheb_deriv(cheb_plan plan, int prec, int axis, const void* u, void* du);
+
+/* Transposed line pass: du = D_axis^T u (used by the discrete adjoint). */
+int cheb_deriv_t(cheb_plan plan, int prec, int axis, const void* u, void* du);
+
+/* Operator apply with boundary rows (Alg. 3; Eq. (eq1) of Sec. 3.3):
+ *   interior node p:  (Au)_p = -sum_a [D_a (K * D_a u)]_p
+ *   boundary node p:  Dirichlet u_p, Neumann +-(D_a u)_p (owner face's axis)
+ * K, u, Au: device fields of type prec.  Au must not alias K or u. */
+int cheb_apply(cheb_plan plan, int prec, const void* K, const void* u, void* Au);
+
+/* Transposed operator: ATlam = A^T lam with A as in cheb_apply (the
+ * discrete adjoint; boundary rows transposed too).  Same buffer rules. */
+int cheb_adjoint_apply(cheb_plan plan, int prec, const void* K, const void* lam, void* ATlam);
+
+/* Right-hand side with boundary rows: b_p = f_p at interior nodes and the
+ * owner face's datum at boundary nodes (Eqs. (eq:residualN), (eq:boundaryN)).
+ * f, b: FP64 device fields (may alias); face_vals[f]: FP64 device face
+ * arrays (entries of unused axes ignored). */
+int cheb_rhs(cheb_plan plan, const double* f, const double* const face_vals[6], double* b);
+
+/* Human-readable text of a status code, and the message of the last failed
+ * call on the calling thread. */
+const char* cheb_status_str(int status);
+const char* cheb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEB_H */

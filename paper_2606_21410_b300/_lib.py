@@ -1,0 +1,111 @@
+"""ctypes loader of the in-tree ``libcheb_b300.so`` and its C signatures.
+
+There is no fallback: importing this module fails loudly when the library
+is missing (build it with ``python -m paper_2606_21410_b300.build``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcheb_b300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} not found: the CUDA library is required (no CPU fallback); "
+        "build it with `python -m paper_2606_21410_b300.build`")
+
+lib = C.CDLL(LIB_PATH)
+
+vp = C.c_void_p
+i32 = C.c_int
+f64p = C.POINTER(C.c_double)
+i32p = C.POINTER(C.c_int)
+
+
+class SolveOpts(C.Structure):
+    """Mirror of ``cheb_solve_opts``."""
+    _fields_ = [
+        ("mode", i32),
+        ("rtol", C.c_double),
+        ("atol", C.c_double),
+        ("restart", i32),
+        ("augment", i32),
+        ("maxiter", i32),
+        ("inner_rtol", C.c_double),
+        ("inner_maxiter", i32),
+        ("max_refinements", i32),
+        ("reorth", i32),
+        ("row_scaling", i32),
+        ("precond", i32),
+        ("use_graph", i32),
+        ("verbose", i32),
+    ]
+
+
+class SolveInfo(C.Structure):
+    """Mirror of ``cheb_solve_info``."""
+    _fields_ = [
+        ("status", i32),
+        ("iterations", i32),
+        ("cycles", i32),
+        ("refinements", i32),
+        ("applies_fp64", i32),
+        ("applies_fp32", i32),
+        ("rel_residual", C.c_double),
+        ("rel_residual_inner", C.c_double),
+        ("seconds", C.c_double),
+        ("e_ref", C.c_double),
+    ]
+
+
+_SIGS = {
+    "cheb_plan_create": (i32, [C.POINTER(vp), i32, i32p, f64p, f64p, i32p, vp]),
+    "cheb_plan_destroy": (i32, [vp]),
+    "cheb_plan_set_stream": (i32, [vp, vp]),
+    "cheb_plan_set_route": (i32, [vp, i32, i32]),
+    "cheb_plan_get_route": (i32, [vp, i32, i32p]),
+    "cheb_nodes": (i32, [vp, i32, f64p]),
+    "cheb_plan_size": (C.c_size_t, [vp]),
+    "cheb_deriv": (i32, [vp, i32, i32, vp, vp]),
+    "cheb_deriv_t": (i32, [vp, i32, i32, vp, vp]),
+    "cheb_apply": (i32, [vp, i32, vp, vp, vp]),
+    "cheb_adjoint_apply": (i32, [vp, i32, vp, vp, vp]),
+    "cheb_rhs": (i32, [vp, vp, C.POINTER(vp), vp]),
+    "cheb_status_str": (C.c_char_p, [i32]),
+    "cheb_last_error": (C.c_char_p, []),
+}
+
+OPTIONAL = {}
+
+
+def _bind():
+    missing = []
+    for name, (res, args) in {**_SIGS, **OPTIONAL}.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            if name in _SIGS:
+                missing.append(name)
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    if missing:
+        raise ImportError(f"{LIB_PATH} lacks symbols {missing}; rebuild it")
+
+
+_bind()
+
+
+class ChebError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib.cheb_status_str(status).decode()
+        detail = lib.cheb_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+def check(status: int, where: str) -> int:
+    if status < 0:
+        raise ChebError(status, where)
+    return status

@@ -1,0 +1,457 @@
+// Line passes of the collocation operator (Alg. 1 and Alg. 3 of the paper,
+// Sec. 2.2 / Sec. 2.3.2) and the right-hand side with boundary rows.
+//
+// One CTA owns a tile of kTileL lines along one axis.  The tile is staged in
+// shared memory with coalesced loads: for the x axis the lines are
+// contiguous in memory, for y and z the tile holds kTileL x-adjacent lines
+// so every row of the tile is a contiguous run of kTileL elements.
+//
+// Line derivative, transform route (N = n - 1, P = 2N a power of two):
+//   F = DCT-I(f) as the real part of a length-P FFT of the even extension
+//       (two lines share one complex FFT: line A real part, line B imaginary),
+//   G_k = k c_k (2/(hi-lo)) F_k / N      (c_N = 1/2: a_k = c_k F_k / N),
+//   beta_k = sum_{j>k, j-k odd} G_j      (the backward recurrence
+//       b_{k-1} = b_{k+1} + 2k a_k with b_0 halved, in closed form, as a
+//       parity-interleaved warp suffix scan; beta_k = b_k / 2, beta_N = 0),
+//   f' = DCT-I(beta)                      (= sum_k b_k T_k at the nodes).
+// Each line pair is processed by one warp without block-wide barriers.
+// Dense route: f' = D f with D staged in shared memory.
+#include <cstdio>
+
+#include "device.cuh"
+
+namespace cheb {
+
+template <typename T>
+struct AxisK {
+  int n, N;
+  T scale;
+  const typename C2<T>::t* tw;  // P twiddles (transform route)
+  const T* D;                   // n x n row-major (dense route)
+};
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Shared-memory layout of a line pass: X (tile), ends (2 x kTileL x 2),
+// then the route's buffers.
+template <typename T>
+static size_t pass_smem_bytes(int route, int n, int P) {
+  const int ldx = n | 1;
+  size_t b = align16(sizeof(T) * kTileL * ldx) + align16(sizeof(T) * kTileL * 4);
+  if (route == CHEB_ROUTE_TRANSFORM) {
+    b += align16(2 * sizeof(T) * (size_t)(kTileL / 2) * P) + align16(2 * sizeof(T) * (size_t)P);
+  } else {
+    b += align16(sizeof(T) * kTileL * ldx) + align16(sizeof(T) * (size_t)n * n);
+  }
+  return b;
+}
+
+// Tile <-> global mapping of element (lane l, point pt).
+struct TileMap {
+  int axis, nx, ny, nz;
+  int line0;      // axis 0: first line of the tile
+  int i0, outer;  // axes 1, 2: first x index, fixed k (axis 1) or j (axis 2)
+  __device__ __forceinline__ bool at(int l, int pt, size_t& gidx, int& i, int& j, int& k) const {
+    if (axis == 0) {
+      const int line = line0 + l;
+      if (line >= ny * nz) return false;
+      i = pt; j = line % ny; k = line / ny;
+      gidx = (size_t)line * nx + pt;
+    } else {
+      i = i0 + l;
+      if (i >= nx) return false;
+      if (axis == 1) { j = pt; k = outer; }
+      else { j = outer; k = pt; }
+      gidx = ((size_t)k * ny + j) * nx + i;
+    }
+    return true;
+  }
+  // element e of the tile in a coalesced enumeration order
+  __device__ __forceinline__ void split(int e, int n, int& l, int& pt) const {
+    if (axis == 0) { l = e / n; pt = e - l * n; }
+    else { pt = e / kTileL; l = e - pt * kTileL; }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// per-warp transform derivative of lines 2w, 2w+1 (in place in X)
+// ---------------------------------------------------------------------------
+template <typename T, int P, int CM, bool TRANSPOSE>
+__device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* buf,
+                                              const typename C2<T>::t* tw, int N, T scale,
+                                              int w, int lane) {
+  typedef typename C2<T>::t C;
+  T* xa = X + (2 * w) * ldx;
+  T* xb = X + (2 * w + 1) * ldx;
+  const T invN = (T)1 / (T)N;
+  // weight m_j of the DCT-I matrix columns: 1 at the ends, 2 inside
+  auto pack = [&](bool divide_m) {
+    for (int j = lane; j < P; j += 32) {
+      const int jj = j <= N ? j : P - j;
+      C v;
+      v.x = xa[jj];
+      v.y = xb[jj];
+      if (divide_m && jj != 0 && jj != N) { v.x *= (T)0.5; v.y *= (T)0.5; }
+      buf[j] = v;
+    }
+    __syncwarp();
+  };
+  auto weight = [&](int k) -> T {  // w_k = k c_k scale / N
+    T wk = (T)k * scale * invN;
+    return k == N ? (T)0.5 * wk : wk;
+  };
+  if (!TRANSPOSE) {
+    pack(false);
+    warp_fft<T, P>(buf, tw, lane);
+    for (int k = lane; k <= N; k += 32) {
+      const T wk = weight(k);
+      const C F = buf[k];
+      xa[k] = wk * F.x;
+      xb[k] = wk * F.y;
+    }
+    __syncwarp();
+    warp_parity_scan<T, CM, true>(xa, N, lane);
+    warp_parity_scan<T, CM, true>(xb, N, lane);
+    pack(false);
+    warp_fft<T, P>(buf, tw, lane);
+    for (int k = lane; k <= N; k += 32) {
+      const C F = buf[k];
+      xa[k] = F.x;
+      xb[k] = F.y;
+    }
+    __syncwarp();
+  } else {
+    // D^T = diag(m) M diag(1/m) W S^T diag(m) M diag(1/m), M = DCT-I matrix,
+    // S^T the exclusive parity prefix scan.
+    pack(true);
+    warp_fft<T, P>(buf, tw, lane);
+    for (int k = lane; k <= N; k += 32) {
+      const T mk = (k == 0 || k == N) ? (T)1 : (T)2;
+      const C F = buf[k];
+      xa[k] = mk * F.x;
+      xb[k] = mk * F.y;
+    }
+    __syncwarp();
+    warp_parity_scan<T, CM, false>(xa, N, lane);
+    warp_parity_scan<T, CM, false>(xb, N, lane);
+    for (int k = lane; k <= N; k += 32) {
+      const T wk = weight(k);
+      xa[k] *= wk;
+      xb[k] *= wk;
+    }
+    __syncwarp();
+    pack(true);
+    warp_fft<T, P>(buf, tw, lane);
+    for (int k = lane; k <= N; k += 32) {
+      const T mk = (k == 0 || k == N) ? (T)1 : (T)2;
+      const C F = buf[k];
+      xa[k] = mk * F.x;
+      xb[k] = mk * F.y;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// block-wide dense derivative X <- D X (or D^T X), tile lines as rows
+// ---------------------------------------------------------------------------
+template <typename T, bool TRANSPOSE>
+__device__ __forceinline__ void block_deriv_dense(T* X, T* tmp, int ldx, const T* Dm, int n) {
+  constexpr int G = 4;                  // lines per work item
+  const int items = n * (kTileL / G);
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int i = it % n;
+    const int l0 = (it / n) * G;
+    T acc[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g] = (T)0;
+    for (int m = 0; m < n; ++m) {
+      const T d = TRANSPOSE ? Dm[m * n + i] : Dm[i * n + m];
+#pragma unroll
+      for (int g = 0; g < G; ++g) acc[g] += d * X[(l0 + g) * ldx + m];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) tmp[(l0 + g) * ldx + i] = acc[g];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kTileL * ldx; e += blockDim.x) X[e] = tmp[e];
+  __syncthreads();
+}
+
+template <typename T, int ROUTE, int P, int CM, bool TRANSPOSE>
+__device__ __forceinline__ void tile_deriv(T* X, T* tmp, int ldx, typename C2<T>::t* Cb,
+                                           const typename C2<T>::t* tw, const T* Dm, int n,
+                                           T scale) {
+  if constexpr (ROUTE == CHEB_ROUTE_TRANSFORM) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    warp_deriv_tf<T, P, CM, TRANSPOSE>(X, ldx, Cb + (size_t)w * P, tw, n - 1, scale, w, lane);
+    __syncthreads();
+  } else {
+    __syncthreads();
+    block_deriv_dense<T, TRANSPOSE>(X, tmp, ldx, Dm, n);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// the line-pass kernel
+// ---------------------------------------------------------------------------
+template <typename T, int ROUTE, int P, int CM>
+__global__ void __launch_bounds__(kThreads)
+line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
+                 const T* __restrict__ u, T* __restrict__ out) {
+  typedef typename C2<T>::t C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = ax.n, N = ax.N;
+  const int ldx = n | 1;
+  unsigned char* p = smem_raw;
+  T* X = (T*)p;            p += align16(sizeof(T) * kTileL * ldx);
+  T* ends = (T*)p;         p += align16(sizeof(T) * kTileL * 4);
+  C* Cb = nullptr; C* tw = nullptr; T* tmp = nullptr; T* Dm = nullptr;
+  if (ROUTE == CHEB_ROUTE_TRANSFORM) {
+    Cb = (C*)p;            p += align16(2 * sizeof(T) * (size_t)(kTileL / 2) * P);
+    tw = (C*)p;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = ax.tw[t];
+  } else {
+    tmp = (T*)p;           p += align16(sizeof(T) * kTileL * ldx);
+    Dm = (T*)p;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Dm[t] = ax.D[t];
+  }
+
+  TileMap map;
+  map.axis = axis; map.nx = g.n[0]; map.ny = g.n[1]; map.nz = g.n[2];
+  if (axis == 0) {
+    map.line0 = blockIdx.x * kTileL; map.i0 = 0; map.outer = 0;
+  } else {
+    const int nbx = (g.n[0] + kTileL - 1) / kTileL;
+    map.line0 = 0;
+    map.i0 = (blockIdx.x % nbx) * kTileL;
+    map.outer = blockIdx.x / nbx;
+  }
+  const int tile_elems = kTileL * n;
+
+  // load the input tile (u, or lambda for the adjoint)
+  for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+    int l, pt; map.split(e, n, l, pt);
+    size_t gi; int i, j, k;
+    T v = (T)0;
+    if (map.at(l, pt, gi, i, j, k)) v = u[gi];
+    X[l * ldx + pt] = v;
+  }
+  __syncthreads();
+
+  const bool adj = (kind == kAdjFirst || kind == kAdjAcc);
+  if (kind == kDeriv || kind == kDerivT) {
+    if (kind == kDeriv) tile_deriv<T, ROUTE, P, CM, false>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    else tile_deriv<T, ROUTE, P, CM, true>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+      int l, pt; map.split(e, n, l, pt);
+      size_t gi; int i, j, k;
+      if (map.at(l, pt, gi, i, j, k)) out[gi] = X[l * ldx + pt];
+    }
+    return;
+  }
+
+  if (!adj) {
+    // ---- A u: D_a u, keep line-end derivatives for Neumann rows
+    tile_deriv<T, ROUTE, P, CM, false>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    if (threadIdx.x < kTileL) {
+      ends[threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
+      ends[threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+      int l, pt; map.split(e, n, l, pt);
+      size_t gi; int i, j, k;
+      if (map.at(l, pt, gi, i, j, k)) X[l * ldx + pt] *= K[gi];
+    }
+    tile_deriv<T, ROUTE, P, CM, false>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    const bool first = (kind == kApplyFirst);
+    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+      int l, pt; map.split(e, n, l, pt);
+      size_t gi; int i, j, k;
+      if (!map.at(l, pt, gi, i, j, k)) continue;
+      const int o = owner_face(g, i, j, k);
+      if (o < 0) {
+        const T v = -X[l * ldx + pt];
+        if (first) out[gi] = v;
+        else out[gi] += v;
+      } else if (g.bc[o] == CHEB_DIRICHLET) {
+        if (first) out[gi] = u[gi];
+      } else if ((o >> 1) == axis) {
+        // hi face (side 1) is line point 0, lo face (side 0) is point N
+        out[gi] = (o & 1) ? ends[l * 2 + 0] : -ends[l * 2 + 1];
+      } else if (first) {
+        out[gi] = (T)0;  // Neumann row of a later axis: written by that pass
+      }
+    }
+  } else {
+    // ---- A^T lam for this axis: D_a^T (S_a lam - K * D_a^T (P_int lam))
+    // S_a lam: +-lam at line ends owned by a Neumann face of this axis.
+    if (threadIdx.x < kTileL) {
+      const int l = threadIdx.x;
+      size_t gi; int i, j, k;
+      T s0 = (T)0, sN = (T)0;
+      if (map.at(l, 0, gi, i, j, k)) {
+        const int o = owner_face(g, i, j, k);
+        if (o == 2 * axis + 1 && g.bc[o] == CHEB_NEUMANN) s0 = X[l * ldx + 0];
+      }
+      if (map.at(l, N, gi, i, j, k)) {
+        const int o = owner_face(g, i, j, k);
+        if (o == 2 * axis && g.bc[o] == CHEB_NEUMANN) sN = -X[l * ldx + N];
+      }
+      ends[l * 2 + 0] = s0;
+      ends[l * 2 + 1] = sN;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+      int l, pt; map.split(e, n, l, pt);
+      size_t gi; int i, j, k;
+      if (map.at(l, pt, gi, i, j, k) && owner_face(g, i, j, k) >= 0) X[l * ldx + pt] = (T)0;
+    }
+    tile_deriv<T, ROUTE, P, CM, true>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+      int l, pt; map.split(e, n, l, pt);
+      size_t gi; int i, j, k;
+      T v = (T)0;
+      if (map.at(l, pt, gi, i, j, k)) {
+        v = -K[gi] * X[l * ldx + pt];
+        if (pt == 0) v += ends[l * 2 + 0];
+        if (pt == N) v += ends[l * 2 + 1];
+      }
+      X[l * ldx + pt] = v;
+    }
+    tile_deriv<T, ROUTE, P, CM, true>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    const bool first = (kind == kAdjFirst);
+    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
+      int l, pt; map.split(e, n, l, pt);
+      size_t gi; int i, j, k;
+      if (!map.at(l, pt, gi, i, j, k)) continue;
+      T v = X[l * ldx + pt];
+      if (first) {
+        const int o = owner_face(g, i, j, k);
+        if (o >= 0 && g.bc[o] == CHEB_DIRICHLET) v += u[gi];
+        out[gi] = v;
+      } else {
+        out[gi] += v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host dispatch
+// ---------------------------------------------------------------------------
+template <typename T> static AxisK<T> axis_k(const AxisTables& t);
+template <> AxisK<double> axis_k<double>(const AxisTables& t) {
+  AxisK<double> a; a.n = t.n; a.N = t.N; a.scale = t.scale; a.tw = t.tw64; a.D = t.D64; return a;
+}
+template <> AxisK<float> axis_k<float>(const AxisTables& t) {
+  AxisK<float> a; a.n = t.n; a.N = t.N; a.scale = (float)t.scale; a.tw = t.tw32; a.D = t.D32; return a;
+}
+
+template <typename T, int ROUTE, int P, int CM>
+static int launch_kernel(const Geom& g, int axis, int kind, const AxisK<T>& ak, const T* K,
+                         const T* u, T* out, cudaStream_t s, int nblocks) {
+  auto kern = line_pass_kernel<T, ROUTE, P, CM>;
+  const size_t smem = pass_smem_bytes<T>(ROUTE, ak.n, P);
+  static size_t configured = 0;  // per instantiation
+  if (smem > configured) {
+    CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
+  CHEB_LAUNCH_CHECK("line_pass_kernel");
+  return CHEB_OK;
+}
+
+template <typename T>
+int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u, T* out,
+                cudaStream_t s) {
+  const Geom g = p->geom();
+  const AxisTables& t = p->ax[axis];
+  const AxisK<T> ak = axis_k<T>(t);
+  int nblocks;
+  if (axis == 0) nblocks = (g.n[1] * g.n[2] + kTileL - 1) / kTileL;
+  else {
+    const int nbx = (g.n[0] + kTileL - 1) / kTileL;
+    nblocks = nbx * (axis == 1 ? g.n[2] : g.n[1]);
+  }
+  if (nblocks == 0) return CHEB_OK;
+  if (t.route == CHEB_ROUTE_DENSE)
+    return launch_kernel<T, CHEB_ROUTE_DENSE, 0, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
+  switch (t.P) {
+    case 8: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 8, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
+    case 16: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 16, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
+    case 32: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 32, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
+    case 64: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 64, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
+    case 128: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 128, 2>(g, axis, kind, ak, K, u, out, s, nblocks);
+    case 256: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 256, 3>(g, axis, kind, ak, K, u, out, s, nblocks);
+    case 512: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 512, 5>(g, axis, kind, ak, K, u, out, s, nblocks);
+    case 1024: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 1024, 9>(g, axis, kind, ak, K, u, out, s, nblocks);
+    default:
+      set_error("transform route needs 2N a power of two in [8, 1024]");
+      return CHEB_ERR_UNSUPPORTED;
+  }
+}
+
+template int launch_pass<double>(const cheb_plan_s*, int, int, const double*, const double*, double*, cudaStream_t);
+template int launch_pass<float>(const cheb_plan_s*, int, int, const float*, const float*, float*, cudaStream_t);
+
+template <typename T>
+int launch_apply(const cheb_plan_s* p, const T* K, const T* u, T* out, cudaStream_t s) {
+  for (int a = 0; a < p->dim; ++a) {
+    int st = launch_pass<T>(p, a, a == 0 ? kApplyFirst : kApplyAcc, K, u, out, s);
+    if (st != CHEB_OK) return st;
+  }
+  return CHEB_OK;
+}
+template int launch_apply<double>(const cheb_plan_s*, const double*, const double*, double*, cudaStream_t);
+template int launch_apply<float>(const cheb_plan_s*, const float*, const float*, float*, cudaStream_t);
+
+template <typename T>
+int launch_adjoint_apply(const cheb_plan_s* p, const T* K, const T* lam, T* out, cudaStream_t s) {
+  for (int a = 0; a < p->dim; ++a) {
+    int st = launch_pass<T>(p, a, a == 0 ? kAdjFirst : kAdjAcc, K, lam, out, s);
+    if (st != CHEB_OK) return st;
+  }
+  return CHEB_OK;
+}
+template int launch_adjoint_apply<double>(const cheb_plan_s*, const double*, const double*, double*, cudaStream_t);
+template int launch_adjoint_apply<float>(const cheb_plan_s*, const float*, const float*, float*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// right-hand side with boundary rows
+// ---------------------------------------------------------------------------
+struct FacePtrs { const double* f[6]; };
+
+__global__ void rhs_kernel(Geom g, const double* f, FacePtrs faces, double* b) {
+  const size_t total = (size_t)g.n[0] * g.n[1] * g.n[2];
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % g.n[0]);
+    const int j = (int)((idx / g.n[0]) % g.n[1]);
+    const int k = (int)(idx / ((size_t)g.n[0] * g.n[1]));
+    const int o = owner_face(g, i, j, k);
+    if (o < 0) { b[idx] = f[idx]; continue; }
+    const int a = o >> 1;
+    size_t fi;
+    if (a == 0) fi = (size_t)k * g.n[1] + j;
+    else if (a == 1) fi = (size_t)k * g.n[0] + i;
+    else fi = (size_t)j * g.n[0] + i;
+    b[idx] = faces.f[o][fi];
+  }
+}
+
+int launch_rhs(const cheb_plan_s* p, const double* f, const double* const face_vals[6], double* b,
+               cudaStream_t s) {
+  FacePtrs fp;
+  for (int i = 0; i < 6; ++i) fp.f[i] = face_vals[i];
+  const size_t total = p->size();
+  int blocks = (int)std::min<size_t>((total + 255) / 256, 148 * 16);
+  rhs_kernel<<<blocks, 256, 0, s>>>(p->geom(), f, fp, b);
+  CHEB_LAUNCH_CHECK("rhs_kernel");
+  return CHEB_OK;
+}
+
+}  // namespace cheb

@@ -1,0 +1,103 @@
+// Internal host-side definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/cheb.h"
+
+namespace cheb {
+
+constexpr int kTileL = 16;      // lines per CTA in the line passes
+constexpr int kThreads = 256;   // threads per CTA in the line passes
+constexpr int kDenseMaxN = 129; // largest axis size of the dense route
+constexpr int kTransformMaxN = 512;
+
+// Per-axis device tables.  The transform route needs the FFT twiddles
+// exp(-2 pi i t / P), t < P = 2N; the dense route the differentiation matrix.
+struct AxisTables {
+  int n = 1;           // points
+  int N = 0;           // n - 1
+  int P = 0;           // FFT length 2N (transform route), 0 otherwise
+  double scale = 1.0;  // 2 / (hi - lo)
+  int route = CHEB_ROUTE_TRANSFORM;
+  bool transform_ok = false;
+  bool dense_ok = false;
+  double2* tw64 = nullptr;
+  float2* tw32 = nullptr;
+  double* D64 = nullptr;   // row-major D (n x n)
+  float* D32 = nullptr;
+};
+
+// Geometry passed by value to kernels.
+struct Geom {
+  int n[3];
+  int dim;
+  int bc[6];
+};
+
+struct Workspace;  // Krylov / solver workspace (solve.cu)
+
+}  // namespace cheb
+
+struct cheb_plan_s {
+  int dim = 0;
+  int n[3] = {1, 1, 1};
+  double lo[3] = {-1, -1, -1};
+  double hi[3] = {1, 1, 1};
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  cheb::AxisTables ax[3];
+  cheb::Workspace* ws = nullptr;
+  size_t size() const { return (size_t)n[0] * n[1] * n[2]; }
+  cheb::Geom geom() const {
+    cheb::Geom g;
+    for (int a = 0; a < 3; ++a) g.n[a] = n[a];
+    g.dim = dim;
+    for (int f = 0; f < 6; ++f) g.bc[f] = bc[f];
+    return g;
+  }
+};
+
+namespace cheb {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define CHEB_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::cheb::cuda_fail(_e, #call); \
+  } while (0)
+
+#define CHEB_LAUNCH_CHECK(what)                           \
+  do {                                                    \
+    cudaError_t _e = cudaGetLastError();                  \
+    if (_e != cudaSuccess) return ::cheb::cuda_fail(_e, what); \
+  } while (0)
+
+// Line-pass kinds (apply.cu).
+enum PassKind {
+  kApplyFirst = 0,  // A u, first axis: writes every node
+  kApplyAcc = 1,    // A u, later axes: accumulates interior, writes own Neumann rows
+  kDeriv = 2,       // du = D_a u
+  kDerivT = 3,      // du = D_a^T u
+  kAdjFirst = 4,    // A^T lam, first axis
+  kAdjAcc = 5,      // A^T lam, later axes
+};
+
+template <typename T>
+int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u, T* out,
+                cudaStream_t s);
+
+// Krylov helpers (krylov.cu)
+template <typename T>
+int launch_apply(const cheb_plan_s* p, const T* K, const T* u, T* out, cudaStream_t s);
+template <typename T>
+int launch_adjoint_apply(const cheb_plan_s* p, const T* K, const T* lam, T* out, cudaStream_t s);
+
+}  // namespace cheb

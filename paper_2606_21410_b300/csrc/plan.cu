@@ -1,0 +1,260 @@
+// Plan creation and the plain entry points: nodes, routes, derivative line
+// passes, operator apply (forward and transposed), right-hand side.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace cheb {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? CHEB_ERR_NOMEM : CHEB_ERR_CUDA;
+}
+
+int launch_rhs(const cheb_plan_s* p, const double* f, const double* const face_vals[6], double* b,
+               cudaStream_t s);
+void free_workspace(cheb_plan_s* p);
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Reference CGL coordinate x_j = cos(pi j / N), evaluated as
+// sin(pi (N - 2j) / (2N)) (same value; exactly antisymmetric).
+static double cgl_ref(int j, int N) { return std::sin(M_PI * (double)(N - 2 * j) / (2.0 * N)); }
+
+// Dense derivative matrix on [lo, hi], built column by column from the
+// transform-route definition (DCT-I, closed-form recurrence, DCT-I) with
+// direct cosine sums in FP64.  Row-major: D[i * n + j] = d(l_j)/dt at t_i.
+static std::vector<double> dense_from_transform(int N, double scale) {
+  const int n = N + 1;
+  std::vector<double> cosv(2 * N);
+  for (int t = 0; t < 2 * N; ++t) cosv[t] = std::cos(M_PI * t / N);
+  auto m = [&](int k) { return (k == 0 || k == N) ? 1.0 : 2.0; };
+  std::vector<double> D((size_t)n * n), G(n), beta(n);
+  for (int col = 0; col < n; ++col) {
+    // F_k = sum_n m_n cos(pi k n / N) e_col[n] = m_col cos(pi k col / N)
+    for (int k = 0; k < n; ++k) {
+      const double F = m(col) * cosv[(k * col) % (2 * N)];
+      const double ck = (k == N) ? 0.5 : 1.0;
+      G[k] = k * ck * scale / N * F;
+    }
+    for (int k = 0; k < n; ++k) {
+      double s = 0.0;
+      for (int j = k + 1; j <= N; j += 2) s += G[j];
+      beta[k] = (k == N) ? 0.0 : s;
+    }
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += m(k) * cosv[(k * i) % (2 * N)] * beta[k];
+      D[(size_t)i * n + col] = s;
+    }
+  }
+  return D;
+}
+
+static int build_axis(cheb_plan_s* p, int a) {
+  AxisTables& t = p->ax[a];
+  t.n = p->n[a];
+  t.N = t.n - 1;
+  t.scale = 2.0 / (p->hi[a] - p->lo[a]);
+  t.transform_ok = is_pow2(t.N) && t.N >= 4 && t.N <= kTransformMaxN;
+  t.dense_ok = t.n <= kDenseMaxN;
+  t.route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  if (t.transform_ok) {
+    t.P = 2 * t.N;
+    std::vector<double2> tw64(t.P);
+    std::vector<float2> tw32(t.P);
+    for (int k = 0; k < t.P; ++k) {
+      const double ang = -2.0 * M_PI * (double)k / (double)t.P;
+      tw64[k] = make_double2(std::cos(ang), std::sin(ang));
+      tw32[k] = make_float2((float)tw64[k].x, (float)tw64[k].y);
+    }
+    CHEB_CUDA(cudaMalloc(&t.tw64, sizeof(double2) * t.P));
+    CHEB_CUDA(cudaMalloc(&t.tw32, sizeof(float2) * t.P));
+    CHEB_CUDA(cudaMemcpy(t.tw64, tw64.data(), sizeof(double2) * t.P, cudaMemcpyHostToDevice));
+    CHEB_CUDA(cudaMemcpy(t.tw32, tw32.data(), sizeof(float2) * t.P, cudaMemcpyHostToDevice));
+  }
+  if (t.dense_ok) {
+    std::vector<double> D = dense_from_transform(t.N, t.scale);
+    std::vector<float> D32(D.size());
+    for (size_t i = 0; i < D.size(); ++i) D32[i] = (float)D[i];
+    CHEB_CUDA(cudaMalloc(&t.D64, sizeof(double) * D.size()));
+    CHEB_CUDA(cudaMalloc(&t.D32, sizeof(float) * D.size()));
+    CHEB_CUDA(cudaMemcpy(t.D64, D.data(), sizeof(double) * D.size(), cudaMemcpyHostToDevice));
+    CHEB_CUDA(cudaMemcpy(t.D32, D32.data(), sizeof(float) * D.size(), cudaMemcpyHostToDevice));
+  }
+  if (!t.transform_ok && !t.dense_ok) {
+    set_error("axis size supported by neither route");
+    return CHEB_ERR_UNSUPPORTED;
+  }
+  return CHEB_OK;
+}
+
+static void free_axis(AxisTables& t) {
+  cudaFree(t.tw64); cudaFree(t.tw32); cudaFree(t.D64); cudaFree(t.D32);
+  t.tw64 = nullptr; t.tw32 = nullptr; t.D64 = nullptr; t.D32 = nullptr;
+}
+
+}  // namespace cheb
+
+using namespace cheb;
+
+extern "C" {
+
+const char* cheb_last_error(void) { return g_last_error.c_str(); }
+
+const char* cheb_status_str(int status) {
+  switch (status) {
+    case CHEB_OK: return "ok";
+    case CHEB_ERR_NOT_CONVERGED: return "not converged";
+    case CHEB_ERR_ARG: return "invalid argument";
+    case CHEB_ERR_CUDA: return "CUDA error";
+    case CHEB_ERR_NOMEM: return "out of device memory";
+    case CHEB_ERR_NONFINITE: return "non-finite residual";
+    case CHEB_ERR_SINGULAR_BC: return "singular boundary conditions (no Dirichlet face)";
+    case CHEB_ERR_UNSUPPORTED: return "unsupported size or route";
+    default: return "unknown status";
+  }
+}
+
+int cheb_plan_create(cheb_plan* out, int dim, const int n[3], const double lo[3],
+                     const double hi[3], const int bc_type[6], void* stream) {
+  if (!out || !n || !lo || !hi || !bc_type) { set_error("null argument"); return CHEB_ERR_ARG; }
+  *out = nullptr;
+  if (dim < 1 || dim > 3) { set_error("dim must be 1, 2 or 3"); return CHEB_ERR_ARG; }
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      if (n[a] < 3) { set_error("active axes need n >= 3"); return CHEB_ERR_ARG; }
+      if (!(hi[a] > lo[a]) || !std::isfinite(hi[a] - lo[a])) {
+        set_error("need hi > lo"); return CHEB_ERR_ARG;
+      }
+    } else if (n[a] != 1) { set_error("unused axes need n = 1"); return CHEB_ERR_ARG; }
+  }
+  for (int f = 0; f < 6; ++f)
+    if (bc_type[f] != CHEB_DIRICHLET && bc_type[f] != CHEB_NEUMANN) {
+      set_error("bc_type must be CHEB_DIRICHLET or CHEB_NEUMANN"); return CHEB_ERR_ARG;
+    }
+  cheb_plan_s* p = new cheb_plan_s();
+  p->dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    p->n[a] = n[a];
+    p->lo[a] = a < dim ? lo[a] : -1.0;
+    p->hi[a] = a < dim ? hi[a] : 1.0;
+  }
+  for (int f = 0; f < 6; ++f) p->bc[f] = bc_type[f];
+  p->stream = (cudaStream_t)stream;
+  cudaGetDevice(&p->device);
+  for (int a = 0; a < dim; ++a) {
+    int st = build_axis(p, a);
+    if (st != CHEB_OK) { cheb_plan_destroy(p); return st; }
+  }
+  *out = p;
+  return CHEB_OK;
+}
+
+int cheb_plan_destroy(cheb_plan p) {
+  if (!p) return CHEB_OK;
+  free_workspace(p);
+  for (int a = 0; a < 3; ++a) free_axis(p->ax[a]);
+  delete p;
+  return CHEB_OK;
+}
+
+int cheb_plan_set_stream(cheb_plan p, void* stream) {
+  if (!p) return CHEB_ERR_ARG;
+  p->stream = (cudaStream_t)stream;
+  return CHEB_OK;
+}
+
+int cheb_plan_set_route(cheb_plan p, int axis, int route) {
+  if (!p || axis < 0 || axis >= p->dim) { set_error("bad plan or axis"); return CHEB_ERR_ARG; }
+  AxisTables& t = p->ax[axis];
+  if (route == CHEB_ROUTE_AUTO) route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  if (route == CHEB_ROUTE_TRANSFORM && !t.transform_ok) {
+    set_error("transform route needs n - 1 a power of two in [4, 512]"); return CHEB_ERR_UNSUPPORTED;
+  }
+  if (route == CHEB_ROUTE_DENSE && !t.dense_ok) {
+    set_error("dense route needs n <= 129"); return CHEB_ERR_UNSUPPORTED;
+  }
+  if (route != CHEB_ROUTE_TRANSFORM && route != CHEB_ROUTE_DENSE) {
+    set_error("unknown route"); return CHEB_ERR_ARG;
+  }
+  t.route = route;
+  return CHEB_OK;
+}
+
+int cheb_plan_get_route(cheb_plan p, int axis, int* route) {
+  if (!p || !route || axis < 0 || axis >= p->dim) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  *route = p->ax[axis].route;
+  return CHEB_OK;
+}
+
+size_t cheb_plan_size(cheb_plan p) { return p ? p->size() : 0; }
+
+int cheb_nodes(cheb_plan p, int axis, double* out) {
+  if (!p || !out || axis < 0 || axis > 2) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  if (axis >= p->dim) { out[0] = 0.0; return CHEB_OK; }
+  const int N = p->n[axis] - 1;
+  const double h = 0.5 * (p->hi[axis] - p->lo[axis]), c = 0.5 * (p->hi[axis] + p->lo[axis]);
+  for (int j = 0; j <= N; ++j) out[j] = h * cgl_ref(j, N) + c;
+  return CHEB_OK;
+}
+
+int cheb_deriv(cheb_plan p, int prec, int axis, const void* u, void* du) {
+  if (!p || !u || !du || axis < 0 || axis >= p->dim) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  if (prec == CHEB_FP64)
+    return launch_pass<double>(p, axis, kDeriv, nullptr, (const double*)u, (double*)du, p->stream);
+  if (prec == CHEB_FP32)
+    return launch_pass<float>(p, axis, kDeriv, nullptr, (const float*)u, (float*)du, p->stream);
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+int cheb_deriv_t(cheb_plan p, int prec, int axis, const void* u, void* du) {
+  if (!p || !u || !du || axis < 0 || axis >= p->dim) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  if (prec == CHEB_FP64)
+    return launch_pass<double>(p, axis, kDerivT, nullptr, (const double*)u, (double*)du, p->stream);
+  if (prec == CHEB_FP32)
+    return launch_pass<float>(p, axis, kDerivT, nullptr, (const float*)u, (float*)du, p->stream);
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+int cheb_apply(cheb_plan p, int prec, const void* K, const void* u, void* Au) {
+  if (!p || !K || !u || !Au) { set_error("null argument"); return CHEB_ERR_ARG; }
+  if (Au == u || Au == K) { set_error("Au must not alias K or u"); return CHEB_ERR_ARG; }
+  if (prec == CHEB_FP64)
+    return launch_apply<double>(p, (const double*)K, (const double*)u, (double*)Au, p->stream);
+  if (prec == CHEB_FP32)
+    return launch_apply<float>(p, (const float*)K, (const float*)u, (float*)Au, p->stream);
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+int cheb_adjoint_apply(cheb_plan p, int prec, const void* K, const void* lam, void* ATlam) {
+  if (!p || !K || !lam || !ATlam) { set_error("null argument"); return CHEB_ERR_ARG; }
+  if (ATlam == lam || ATlam == K) { set_error("output must not alias K or lam"); return CHEB_ERR_ARG; }
+  if (prec == CHEB_FP64)
+    return launch_adjoint_apply<double>(p, (const double*)K, (const double*)lam, (double*)ATlam, p->stream);
+  if (prec == CHEB_FP32)
+    return launch_adjoint_apply<float>(p, (const float*)K, (const float*)lam, (float*)ATlam, p->stream);
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+int cheb_rhs(cheb_plan p, const double* f, const double* const face_vals[6], double* b) {
+  if (!p || !f || !b || !face_vals) { set_error("null argument"); return CHEB_ERR_ARG; }
+  for (int fc = 0; fc < 2 * p->dim; ++fc)
+    if (!face_vals[fc]) { set_error("null face array of an active axis"); return CHEB_ERR_ARG; }
+  const double* fv[6];
+  for (int fc = 0; fc < 6; ++fc) fv[fc] = fc < 2 * p->dim ? face_vals[fc] : f;
+  return launch_rhs(p, f, fv, b, p->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+"""Parity of the CUDA line passes with the FP64 oracle: first derivatives
+(transform and dense routes, FP64 and FP32, every axis, uneven sizes with
+ragged tiles), their transposes, the operator apply with every boundary-type
+pattern, the adjoint apply, and the right-hand side.
+
+Tolerances (relative L2 of the whole field).  One derivative of the degree-N
+interpolant amplifies input rounding by ~||D|| ~ N^2, the apply applies two,
+so both are bounded by C N^2 eps relative to the output scale with
+C = 4 in FP64 (eps = 2.2e-16) and C = 8 in FP32 (eps = 1.2e-7); the apply is
+compared relative to ||D||-scaled magnitude max|K| ||D||^2 ||u||."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+EPS = {torch.float64: 2.2e-16, torch.float32: 1.2e-7}
+C_TOL = {torch.float64: 4.0, torch.float32: 8.0}
+
+
+def _plan(n, lo=(-1, -1, -1), hi=(1, 1, 1), bc=(0,) * 6):
+    import paper_2606_21410_b300 as P
+    return P.Plan(n, lo, hi, bc)
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _tol(N, dtype):
+    return C_TOL[dtype] * N * N * EPS[dtype]
+
+
+CASES = [
+    ((17, 9, 33), (-1, 0, 0.5), (1, 2, 3.0)),
+    ((65, 33, 9), (0, 0, 0), (1, 1, 1)),
+    ((9, 17, 5), (-2, -1, 0), (2, 1, 0.25)),
+]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("case", CASES)
+def test_deriv_transform_route_matches_dense_D(case, dtype):
+    n, lo, hi = case
+    g = O.Grid(n, lo, hi)
+    p = _plan(n, lo, hi)
+    u = W.random_field(g.shape, 101)
+    ud = _dev(u, dtype)
+    for a in range(3):
+        assert p.route(a) == 0
+        ref = O.grad(u, g, a)
+        got = p.deriv(ud, a).double().cpu().numpy()
+        N = n[a] - 1
+        assert _rel(got, ref) < _tol(N, dtype), (a, _rel(got, ref))
+        refT = np.moveaxis(np.tensordot(g.D(a).T, u, axes=([1], [2 - a])), 0, 2 - a)
+        gotT = p.deriv(ud, a, transpose=True).double().cpu().numpy()
+        assert _rel(gotT, refT) < _tol(N, dtype), (a, "T", _rel(gotT, refT))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_deriv_dense_route_any_size(dtype):
+    n, lo, hi = (12, 7, 10), (0, -1, -1), (3, 1, 2)
+    g = O.Grid(n, lo, hi)
+    p = _plan(n, lo, hi)
+    u = W.random_field(g.shape, 102)
+    for a in range(3):
+        assert p.route(a) == 1
+        got = p.deriv(_dev(u, dtype), a).double().cpu().numpy()
+        assert _rel(got, O.grad(u, g, a)) < _tol(n[a] - 1, dtype)
+        gotT = p.deriv(_dev(u, dtype), a, transpose=True).double().cpu().numpy()
+        refT = np.moveaxis(np.tensordot(g.D(a).T, u, axes=([1], [2 - a])), 0, 2 - a)
+        assert _rel(gotT, refT) < _tol(n[a] - 1, dtype)
+
+
+def test_dense_and_transform_routes_agree():
+    n = (33, 17, 9)
+    p = _plan(n)
+    u = _dev(W.random_field((9, 17, 33), 103))
+    K = _dev(W.random_positive_field((9, 17, 33), 104))
+    a0 = p.apply(K, u).cpu().numpy()
+    for a in range(3):
+        p.set_route(a, 1)
+    a1 = p.apply(K, u).cpu().numpy()
+    assert _rel(a1, a0) < 1e-12
+
+
+def test_deriv_exact_on_chebyshev_polynomials():
+    """d/dx T_k = k U_{k-1} at every node, for every k <= N (FP64, 1-D)."""
+    N = 64
+    p = _plan((N + 1,))
+    th = np.pi * np.arange(N + 1) / N
+    for k in range(N + 1):
+        Tk = np.cos(k * th)
+        d = p.deriv(_dev(Tk), 0).cpu().numpy()
+        ex = np.empty(N + 1)
+        ex[1:-1] = k * np.sin(k * th[1:-1]) / np.sin(th[1:-1])
+        ex[0], ex[-1] = k * k, (-1) ** (k + 1) * k * k
+        assert np.abs(d - ex).max() < 1e-13 * max(1, k * k) * N
+
+
+def _apply_scale(K, u, g):
+    s = np.abs(K).max() * np.linalg.norm(u)
+    return s * max(np.abs(g.D(a)).max() ** 2 for a in g.axes)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("bc", [list(t) for t in itertools.product([0, 1], repeat=6)][::7])
+def test_apply_every_bc_pattern(bc, dtype):
+    n, lo, hi = (17, 9, 33), (0, -1, 0), (1, 1, 2)
+    g = O.Grid(n, lo, hi, bc)
+    p = _plan(n, lo, hi, bc)
+    u = W.random_field(g.shape, 201)
+    K = W.random_positive_field(g.shape, 202)
+    ref = O.apply(u, K, g)
+    got = p.apply(_dev(K, dtype), _dev(u, dtype)).double().cpu().numpy()
+    err = np.linalg.norm(got - ref) / _apply_scale(K, u, g)
+    assert err < _tol(32, dtype), err
+    # boundary rows exactly: Dirichlet rows copy u
+    own = O.owners(g)
+    dmask = np.isin(own, [f for f in range(6) if bc[f] == 0])
+    if dtype == torch.float64:
+        assert np.array_equal(got[dmask], u[dmask])
+
+
+@pytest.mark.parametrize("dim,n", [(1, (33,)), (2, (17, 65)), (3, (5, 9, 3))])
+def test_apply_lower_dimensions(dim, n):
+    bc = [1, 0, 0, 1, 0, 0]
+    g = O.Grid(n, bc=bc)
+    p = _plan(n, bc=bc)
+    u = W.random_field(g.shape, 300 + dim)
+    K = W.random_positive_field(g.shape, 310 + dim)
+    ref = O.apply(u, K, g)
+    got = p.apply(_dev(K), _dev(u)).cpu().numpy()
+    assert np.linalg.norm(got - ref) / _apply_scale(K, u, g) < _tol(max(n) - 1, torch.float64)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_adjoint_apply_matches_oracle_and_dot_product(dtype):
+    bc = [1, 0, 1, 1, 0, 1]
+    n, lo, hi = (17, 9, 33), (0, 0, 0), (1, 2, 1)
+    g = O.Grid(n, lo, hi, bc)
+    p = _plan(n, lo, hi, bc)
+    lam = W.random_field(g.shape, 401)
+    K = W.random_positive_field(g.shape, 402)
+    ref = O.adjoint_apply(lam, K, g)
+    got = p.adjoint_apply(_dev(K, dtype), _dev(lam, dtype)).double().cpu().numpy()
+    assert np.linalg.norm(got - ref) / _apply_scale(K, lam, g) < _tol(32, dtype)
+    if dtype == torch.float64:
+        x = W.random_field(g.shape, 403)
+        Ax = p.apply(_dev(K), _dev(x)).cpu().numpy()
+        lhs, rhs = (Ax * lam).sum(), (x * got).sum()
+        assert abs(lhs - rhs) < 1e-12 * np.abs(Ax).sum() * np.abs(lam).max()
+
+
+def test_rhs_boundary_rows():
+    bc = [0, 1, 1, 0, 0, 1]
+    n = (9, 17, 5)
+    g = O.Grid(n, bc=bc)
+    p = _plan(n, bc=bc)
+    f = W.random_field(g.shape, 501)
+    shapes = [(5, 17), (5, 17), (5, 9), (5, 9), (17, 9), (17, 9)]
+    faces = [W.random_field(s, 510 + i) for i, s in enumerate(shapes)]
+    ref = O.rhs(f, faces, g)
+    got = p.rhs(_dev(f), [_dev(x) for x in faces]).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------- large sizes
+
+def _line_apply_samples(u, K, g, pts):
+    """(A u)_p at sample interior nodes p, from the oracle's dense D one line
+    at a time (cheap at any size)."""
+    out = []
+    for (k, j, i) in pts:
+        v = 0.0
+        idx = {0: i, 1: j, 2: k}
+        for a in g.axes:
+            D = g.D(a)
+            sl = [k, j, i]
+            sl[2 - a] = slice(None)
+            line_u = u[tuple(sl)]
+            line_K = K[tuple(sl)]
+            q = line_K * (D @ line_u)
+            v -= D[idx[a]] @ q
+        out.append(v)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("nn", [129, 257])
+def test_apply_full_size_sampled(nn):
+    """At 129^3 and 257^3 (the solve sizes), sampled interior rows against
+    the oracle's per-line dense evaluation, FP64 and FP32."""
+    bc = [0, 0, 1, 1, 1, 1]
+    g = O.Grid((nn,) * 3, bc=bc)
+    p = _plan((nn,) * 3, bc=bc)
+    X, Y, Z = g.mesh()
+    u = np.sin(2 * X + Y) * np.cos(3 * Z) + 0.01 * W.random_field(g.shape, 601)
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 10.0)
+    rng = W.rng(602)
+    pts = [tuple(int(v) for v in rng.integers(1, nn - 1, size=3)) for _ in range(200)]
+    ref = _line_apply_samples(u, K, g, pts)
+    scale = np.abs(ref).max()
+    for dtype in (torch.float64, torch.float32):
+        got = p.apply(_dev(K, dtype), _dev(u, dtype)).double().cpu().numpy()
+        vals = np.array([got[k, j, i] for (k, j, i) in pts])
+        assert np.abs(vals - ref).max() / scale < 20 * _tol(nn - 1, dtype), dtype
