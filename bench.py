@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the hierarchical Chebyshev-collocation solve on B300.
+
+Workload (one "step"): the 257^3 heterogeneous two-phase problem solved by
+hierarchical refinement 65^3 -> 129^3 -> 257^3 with modal prolongation
+(seeded non-overlapping spheres, radii U(0.08, 0.15), 20% volume fraction,
+K_incl / K_matrix = 100, f = 0, Dirichlet u = x on x = +-1, zero-flux Neumann
+elsewhere), mixed precision (FP32 inner LGMRES, FP64 refinement), stopping at
+a preconditioned relative residual of 1e-12.  The metric is the time to
+solve; the same line reports the operator apply throughput (GDOF/s) in FP32
+and FP64, the plain-FP64 time to solve, the roofline of the dominant
+kernel, the oracle timed on the host cores, and an end-to-end time through
+the public API with host buffers.
+
+``--impl reference`` times the FP64 CPU oracle instead (bounded sample).
+Multi-GPU: independent replicas (the single-grid solve does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "257³ time-to-solve at rel.err≤1e-8 and apply GDOF/s, mixed vs FP64, same B300"
+BC = [0, 0, 1, 1, 1, 1]   # x faces Dirichlet, y and z faces Neumann
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--levels", default="65,129,257")
+    ap.add_argument("--contrast", type=float, default=100.0)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+
+def x_boundary(X, Y, Z):
+    return X, (np.ones_like(X), 0 * X, 0 * X), 0 * X
+
+
+def host_level(n, spheres, contrast, nodes):
+    """K and b of one level on the host, sampled at the given node arrays."""
+    import workloads as W
+    X, Y, Z = W.mesh(*nodes)
+    K = W.two_phase_conductivity(X, Y, Z, spheres, 1.0, contrast)
+    faces = W.face_values(BC, nodes[0], nodes[1], nodes[2], x_boundary)
+    return K, faces
+
+
+def setup_gpu(levels, contrast):
+    import torch
+    import paper_2606_21410_b300 as P
+    import workloads as W
+    sp = W.sphere_packing(0)
+    plans, Ks, bs, hostK, hostb = [], [], [], [], []
+    for n in levels:
+        p = P.Plan((n, n, n), bc=BC)
+        K, faces = host_level(n, sp, contrast, [p.nodes(0), p.nodes(1), p.nodes(2)])
+        Kd = torch.from_numpy(K).cuda()
+        bd = p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"),
+                   [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in faces])
+        plans.append(p)
+        Ks.append(Kd)
+        bs.append(bd)
+        hostK.append(torch.from_numpy(K).pin_memory())
+        hostb.append(bd.cpu().pin_memory())
+    return plans, Ks, bs, hostK, hostb
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# oracle timing (cpu baseline / reference arm)
+# ----------------------------------------------------------------------------
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_iteration_seconds(n, contrast, reps=1):
+    """Seconds of one oracle GMRES iteration (dense Kronecker apply + the
+    oracle's constant-K preconditioner) at n^3, FP64, on the host cores."""
+    import oracle as O
+    import workloads as W
+    g = O.Grid((n,) * 3, bc=BC)
+    sp = W.sphere_packing(0)
+    K, faces = host_level(n, sp, contrast, [g.nodes(0), g.nodes(1), g.nodes(2)])
+    b = O.rhs(np.zeros(g.shape), faces, g)
+    M = O.FDMPreconditioner(g, O.geometric_mean(K))
+    v = b / np.linalg.norm(b)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        v = M(O.apply(v, K, g))
+        v /= np.linalg.norm(v)
+    return (time.perf_counter() - t0) / reps
+
+
+def oracle_estimate(levels, contrast, its_per_level, reps=1):
+    """Oracle time-to-solve estimate: measured seconds per iteration at each
+    level times the iteration count of that level."""
+    per = [oracle_iteration_seconds(n, contrast, reps) for n in levels]
+    return sum(p * max(1, i) for p, i in zip(per, its_per_level)), per
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    levels = [int(v) for v in args.levels.split(",")]
+    import oracle as O
+    import workloads as W
+    # iteration count from the oracle's own full solve at the coarsest level
+    n0 = levels[0]
+    g = O.Grid((n0,) * 3, bc=BC)
+    K, faces = host_level(n0, W.sphere_packing(0), args.contrast, [g.nodes(0), g.nodes(1), g.nodes(2)])
+    b = O.rhs(np.zeros(g.shape), faces, g)
+    t0 = time.perf_counter()
+    _, info = O.solve_preconditioned(K, b, g, rtol=1e-12)
+    t_coarse = time.perf_counter() - t0
+    its = info["iterations"]
+    times = []
+    for s in range(args.warmup + args.steps):
+        est, per = oracle_estimate(levels[1:], args.contrast, [its] * (len(levels) - 1))
+        if s >= args.warmup:
+            times.append(t_coarse + est)
+    v = float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(levels, args.contrast),
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": (f"oracle full preconditioned-GMRES solve at {n0}^3 ({its} "
+                                    f"iterations, {t_coarse:.1f} s) plus one timed iteration per "
+                                    f"finer level x {its} iterations")},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(levels, contrast):
+    return {"workload": f"two-phase spheres, hierarchical {'->'.join(f'{n}^3' for n in levels)}, "
+                        f"K_incl/K_matrix={contrast:g}, mixed FP32/FP64, rtol 1e-12",
+            "levels": levels, "precond": "FDM (constant-K fast diagonalization)",
+            "lgmres": "restart 30, augment 3", "l2": "inputs larger than L2 (257^3 FP64 = 136 MB)"}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2606_21410_b300 as P
+    lib = P.lib
+    levels = [int(v) for v in args.levels.split(",")]
+    plans, Ks, bs, hostK, hostb = setup_gpu(levels, args.contrast)
+    opts = dict(mode=1, rtol=1e-12)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return P.solve_hierarchy(plans, Ks, bs, **opts)
+
+    for _ in range(max(3, args.warmup)):
+        us, infos, eref = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- timed region
+    import ctypes as C
+    lib.cheb_profile_enable(1)
+    l0 = lib.cheb_launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            us, infos, eref = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = lib.cheb_launch_count() - l0
+    ms = (C.c_double * 8)()
+    cnt = (C.c_longlong * 8)()
+    lib.cheb_profile_read(ms, cnt)
+    lib.cheb_profile_enable(0)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    per_step = elapsed / args.steps
+    phase = {nm: {"ms": ms[i] / args.steps, "count": cnt[i] // args.steps} for i, nm in enumerate(
+        ["apply64", "apply32", "prec64", "prec32", "orth64", "orth32", "prolong", "other"])}
+
+    # ---- apply throughput at the finest level
+    pf, nf = plans[-1], levels[-1]
+    ntot = nf ** 3
+
+    def time_apply(dtype, reps=20):
+        K = Ks[-1].to(dtype)
+        u = us[-1].to(dtype)
+        out = torch.empty_like(u)
+        for _ in range(3):
+            pf.apply(K, u, out)
+        torch.cuda.synchronize()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            pf.apply(K, u, out)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b2) / 1e3 / reps
+
+    t32 = time_apply(torch.float32)
+    t64 = time_apply(torch.float64)
+    apply = {"fp32_gdofs": ntot / t32 / 1e9, "fp64_gdofs": ntot / t64 / 1e9,
+             "fp32_ms": t32 * 1e3, "fp64_ms": t64 * 1e3}
+
+    # ---- plain FP64 comparison solve
+    fp64 = None
+    if not args.no_fp64:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u64, infos64, _ = P.solve_hierarchy(plans, Ks, bs, mode=0, rtol=1e-12, check_status=False)
+        torch.cuda.synchronize()
+        fp64 = {"time_to_solve_s": time.perf_counter() - t0,
+                "iterations": [i["iterations"] for i in infos64],
+                "status": [i["status"] for i in infos64],
+                "rel_diff_mixed_vs_fp64": P.rel_diff(pf, u64[-1], us[-1])}
+
+    # ---- end to end through the public API with host buffers
+    torch.cuda.synchronize()
+    out_host = torch.empty(plans[-1].shape, dtype=torch.float64).pin_memory()
+    t0 = time.perf_counter()
+    Kd2 = [k.to("cuda", non_blocking=True) for k in hostK]
+    bd2 = [b.to("cuda", non_blocking=True) for b in hostb]
+    ue, _, _ = P.solve_hierarchy(plans, Kd2, bd2, **opts)
+    out_host.copy_(ue[-1], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    h2d = sum(k.numel() * 8 + b.numel() * 8 for k, b in zip(hostK, hostb))
+    d2h = out_host.numel() * 8
+
+    # ---- roofline of the dominant kernel group
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    top = max(phase, key=lambda k: phase[k]["ms"])
+    m = nf - 2
+    if top.startswith("prec"):
+        # 6 dense contractions of m x m matrices per application: 12 m^4 flops
+        flops = 12.0 * m ** 4
+        per = phase[top]["ms"] / max(1, phase[top]["count"]) / 1e3
+        sm_mhz = peaks.get("sm_max_mhz", 2032.0)
+        fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        fp64_peak = fp32_peak / 64.0
+        peak = fp32_peak if top.endswith("32") else fp64_peak
+        roof = {"bound": "alu", "kernel": "fdm preconditioner (gemm_kernel contractions)",
+                "achieved": flops / per / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / per / 1e12 / peak, "traffic": None,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock "
+                               "(FP64 = FP32/64 nominal, unmeasured)"}
+    else:
+        words = 11.0 / 3.0 if top.startswith("apply") else None
+        wb = 4 if top.endswith("32") else 8
+        per = phase[top]["ms"] / max(1, phase[top]["count"]) / 1e3
+        if words is not None:
+            per_launch = per / 3.0
+            algo = words * wb * ntot
+            roof = {"bound": "hbm", "kernel": "line_pass_kernel", "achieved": algo / per_launch / 1e9,
+                    "peak": hbm, "unit": "GB/s", "frac": algo / per_launch / 1e9 / hbm, "traffic": None}
+        else:
+            roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": hbm, "unit": "GB/s",
+                    "frac": None, "traffic": None}
+    # apply kernel roofline, stated beside (the hot path's streaming kernel)
+    apply_roof = {"bound": "hbm", "kernel": "line_pass_kernel (FP32 apply, 3 launches)",
+                  "achieved": 11 * 4 * ntot / t32 / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": 11 * 4 * ntot / t32 / 1e9 / hbm,
+                  "algorithmic_bytes": "11 words/DOF over the three axis passes"}
+
+    # ---- CPU baseline (oracle on the host cores, bounded sample)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        its64 = fp64["iterations"] if fp64 else [i["iterations"] for i in infos]
+        est, per_it = oracle_estimate(levels, args.contrast, its64, reps=1)
+        cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": ("one timed oracle GMRES iteration (dense Kronecker apply + constant-K "
+                          f"preconditioner) per level {levels}, "
+                          f"{', '.join(f'{p:.2f}' for p in per_it)} s each, times the GPU FP64 "
+                          f"iteration counts {its64}")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": per_step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+            "config": workload_config(levels, args.contrast),
+            "solves_per_s": world * args.steps / elapsed,
+            "iterations_per_level": [i["iterations"] for i in infos],
+            "refinements_per_level": [i["refinements"] for i in infos],
+            "rel_residual": infos[-1]["rel_residual"], "e_ref": eref,
+            "apply": apply, "fp64": fp64, "phase_ms_per_step": phase,
+            "roofline": roof, "apply_roofline": apply_roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -123,6 +123,106 @@ int cheb_adjoint_apply(cheb_plan plan, int prec, const void* K, const void* lam,
  * arrays (entries of unused axes ignored). */
 int cheb_rhs(cheb_plan plan, const double* f, const double* const face_vals[6], double* b);
 
+/* ------------------------------------------------------------------------
+ * Solves
+ * ------------------------------------------------------------------------ */
+
+/* Preconditioner of the Krylov solves.  The paper solves the collocation
+ * system with LGMRES and no preconditioner (CHEB_PRECOND_NONE).  FDM is
+ * the exact inverse of the constant-coefficient collocation operator with
+ * the same boundary rows (conductivity kref), applied by fast
+ * diagonalization; the solve runs on M^{-1} A u = M^{-1} b. */
+enum cheb_precond { CHEB_PRECOND_NONE = 0, CHEB_PRECOND_FDM = 2 };
+
+typedef struct cheb_solve_opts {
+  int mode;            /* CHEB_SOLVE_FP64 or CHEB_SOLVE_MIXED */
+  double rtol;         /* stop when ||M^{-1}(b - A u)|| <= rtol ||M^{-1} b|| (M = I
+                          without preconditioner) */
+  double atol;         /* ... or when ||M^{-1}(b - A u)|| <= atol */
+  int restart;         /* m: new Krylov directions per LGMRES cycle */
+  int augment;         /* k: error-approximation vectors carried between cycles;
+                          restart + augment + 1 <= 40 */
+  int maxiter;         /* cap on Arnoldi steps (all precisions) */
+  double inner_rtol;   /* MIXED: relative tolerance of each FP32 inner solve */
+  int inner_maxiter;   /* MIXED: cap on Arnoldi steps of one inner solve */
+  int max_refinements; /* MIXED: cap on FP64 refinement steps */
+  int reorth;          /* 1: Gram-Schmidt twice per Arnoldi step */
+  int precond;         /* CHEB_PRECOND_* */
+  double kref;         /* FDM conductivity; <= 0: geometric mean of K */
+  int verbose;         /* 1: progress lines on stderr */
+} cheb_solve_opts;
+
+typedef struct cheb_solve_info {
+  int status;              /* return code of the solve */
+  int iterations;          /* Arnoldi steps, all precisions */
+  int cycles;              /* LGMRES restart cycles */
+  int refinements;         /* MIXED: FP64 refinement steps taken */
+  int applies_fp64;        /* operator applications in FP64 */
+  int applies_fp32;        /* operator applications in FP32 */
+  double rel_residual;     /* final ||M^{-1}(b - A u)|| / ||M^{-1} b|| */
+  double rel_residual_inner; /* MIXED: last inner relative residual */
+  double seconds;          /* wall time of the call */
+  double kref;             /* FDM conductivity used */
+} cheb_solve_info;
+
+/* Defaults: MIXED, rtol 1e-12, restart 30, augment 3, maxiter 2000,
+ * inner_rtol 1e-5, inner_maxiter 400, max_refinements 30, FDM, kref auto. */
+void cheb_solve_opts_default(cheb_solve_opts* opts);
+
+/* Solve A u = b (Alg. 2 with the Krylov solver LGMRES; boundary rows as in
+ * cheb_apply).  K, b: FP64 device fields; u: FP64 device field, in: initial
+ * guess (e.g. a prolonged coarse solution, Alg. 4), out: solution.  opts may
+ * be NULL (defaults); info may be NULL.  Returns CHEB_OK,
+ * CHEB_ERR_NOT_CONVERGED (u holds the last iterate) or an error.  The plan
+ * allocates its Krylov workspace at the first solve (about
+ * (restart + 2 augment + 5) fields of the working precision) and keeps it.
+ * Synchronises the plan's stream once per Arnoldi step. */
+int cheb_solve(cheb_plan plan, const double* K, const double* b, double* u,
+               const cheb_solve_opts* opts, cheb_solve_info* info);
+
+/* Modal prolongation (Sec. 2.3.3, Alg. 4): per axis, coarse nodal values
+ * -> Chebyshev coefficients (DCT-I), zero-padded to the fine degree, ->
+ * fine nodal values (inverse DCT-I).  The fine plan must have N_f = 2 N on
+ * every active axis (powers of two, N_f <= 512) and the same box.  u_c:
+ * coarse device field, u_f: fine device field, both of type prec.  Uses two
+ * scratch arrays owned by the fine plan (allocated at the first call). */
+int cheb_prolong(cheb_plan coarse, cheb_plan fine, int prec, const void* u_c, void* u_f);
+
+/* out = ||a - b||_2 / ||a||_2 for FP64 device fields on the plan's grid (the
+ * refinement indicator e_ref of Sec. 2.3.3 with a the fine solution and b
+ * the prolonged coarse solution).  Synchronises. */
+int cheb_rel_diff(cheb_plan plan, const double* a, const double* b, double* out);
+
+/* Hierarchical refinement (Alg. 4) over `levels` plans of doubling N:
+ * solve level 0 from the guess in u[0]; for each further level prolong the
+ * previous solution into u[l] as the initial guess, solve, and report
+ * e_ref[l] = ||u_l - P u_{l-1}|| / ||u_l|| (e_ref[0] = 0).  K[l], b[l], u[l]:
+ * FP64 device fields of level l.  infos, e_ref: arrays of `levels` entries
+ * (may be NULL).  Returns the last level's status. */
+int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const* K,
+                         const double* const* b, double* const* u, const cheb_solve_opts* opts,
+                         cheb_solve_info* infos, double* e_ref);
+
+/* z = M^{-1} r for the FDM preconditioner with conductivity kref > 0
+ * (device fields of type prec). */
+int cheb_precond_apply(cheb_plan plan, int prec, double kref, const void* r, void* z);
+
+/* ------------------------------------------------------------------------
+ * Instrumentation
+ * ------------------------------------------------------------------------ */
+
+/* Number of kernels this library has launched in the process. */
+long long cheb_launch_count(void);
+
+/* Per-phase device timing with CUDA events recorded on the plan streams:
+ * enable (on = 1) or disable, resetting the totals.  Phases: 0 FP64 operator
+ * applies, 1 FP32 applies, 2 FP64 preconditioner, 3 FP32 preconditioner,
+ * 4 FP64 Gram-Schmidt, 5 FP32 Gram-Schmidt, 6 prolongation, 7 other. */
+int cheb_profile_enable(int on);
+/* Totals since enabling: ms[8] milliseconds and counts[8] timed intervals
+ * (either may be NULL).  Waits for the recorded events. */
+int cheb_profile_read(double* ms, long long* counts);
+
 /* Human-readable text of a status code, and the message of the last failed
  * call on the calling thread. */
 const char* cheb_status_str(int status);

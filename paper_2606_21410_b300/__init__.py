@@ -21,6 +21,18 @@ DIRICHLET, NEUMANN = 0, 1
 FP64, FP32 = 0, 1
 SOLVE_FP64, SOLVE_MIXED = 0, 1
 ROUTE_AUTO, ROUTE_TRANSFORM, ROUTE_DENSE = -1, 0, 1
+PRECOND_NONE, PRECOND_FDM = 0, 2
+
+
+def solve_opts(**kw) -> SolveOpts:
+    """``cheb_solve_opts`` with the library defaults, fields overridden by kw."""
+    o = SolveOpts()
+    lib.cheb_solve_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown solve option {k}")
+        setattr(o, k, v)
+    return o
 
 _PREC = {torch.float64: FP64, torch.float32: FP32}
 
@@ -159,6 +171,80 @@ class Plan:
         return out
 
 
+    def solve(self, K: torch.Tensor, b: torch.Tensor, u: torch.Tensor | None = None,
+              check_status: bool = True, **opts):
+        """Solve A u = b (``cheb_solve``); u (FP64) holds the initial guess and
+        receives the solution.  Returns (u, info dict)."""
+        K = self._field(K, "K", torch.float64)
+        b = self._field(b, "b", torch.float64)
+        if u is None:
+            u = torch.zeros(self.shape, dtype=torch.float64, device=b.device)
+        u = self._field(u, "u", torch.float64)
+        o = solve_opts(**opts)
+        info = SolveInfo()
+        self._sync_stream()
+        st = lib.cheb_solve(self._h, _vp(K), _vp(b), _vp(u), C.byref(o), C.byref(info))
+        check(st, "cheb_solve")
+        d = info.as_dict()
+        if check_status and st != 0:
+            raise ChebError(st, "cheb_solve")
+        return u, d
+
+    def precond_apply(self, r: torch.Tensor, kref: float, out=None) -> torch.Tensor:
+        """z = M^{-1} r for the fast-diagonalization preconditioner (``cheb_precond_apply``)."""
+        r = self._field(r, "r")
+        out = self._out(out, r)
+        self._sync_stream()
+        check(lib.cheb_precond_apply(self._h, _PREC[r.dtype], float(kref), _vp(r), _vp(out)),
+              "cheb_precond_apply")
+        return out
+
+
+def prolong(coarse: Plan, fine: Plan, u_c: torch.Tensor, out=None) -> torch.Tensor:
+    """Modal prolongation of u_c onto the fine plan's grid (``cheb_prolong``)."""
+    u_c = coarse._field(u_c, "u_c")
+    out = fine._out(out, u_c)
+    fine._sync_stream()
+    check(lib.cheb_prolong(coarse.handle, fine.handle, _PREC[u_c.dtype], _vp(u_c), _vp(out)),
+          "cheb_prolong")
+    return out
+
+
+def rel_diff(plan: Plan, a: torch.Tensor, b: torch.Tensor) -> float:
+    """||a - b|| / ||a|| (``cheb_rel_diff``), FP64 fields."""
+    a = plan._field(a, "a", torch.float64)
+    b = plan._field(b, "b", torch.float64)
+    out = C.c_double()
+    plan._sync_stream()
+    check(lib.cheb_rel_diff(plan.handle, _vp(a), _vp(b), C.byref(out)), "cheb_rel_diff")
+    return out.value
+
+
+def solve_hierarchy(plans, K, b, u0=None, check_status: bool = True, **opts):
+    """Hierarchical refinement (``cheb_solve_hierarchy``): plans of doubling N,
+    per-level FP64 K and b.  Returns (list of per-level solutions, infos, e_ref)."""
+    L = len(plans)
+    us = [torch.zeros(p.shape, dtype=torch.float64, device="cuda") for p in plans]
+    if u0 is not None:
+        us[0].copy_(u0)
+    for i, p in enumerate(plans):
+        p._field(K[i], "K", torch.float64)
+        p._field(b[i], "b", torch.float64)
+        p._sync_stream()
+    hp = (C.c_void_p * L)(*[p.handle.value for p in plans])
+    Kp = (C.c_void_p * L)(*[t.data_ptr() for t in K])
+    bp = (C.c_void_p * L)(*[t.data_ptr() for t in b])
+    up = (C.c_void_p * L)(*[t.data_ptr() for t in us])
+    infos = (SolveInfo * L)()
+    eref = (C.c_double * L)()
+    o = solve_opts(**opts)
+    st = lib.cheb_solve_hierarchy(L, hp, Kp, bp, up, C.byref(o), infos, eref)
+    check(st, "cheb_solve_hierarchy")
+    if check_status and st != 0:
+        raise ChebError(st, "cheb_solve_hierarchy")
+    return us, [i.as_dict() for i in infos], list(eref)
+
+
 # thin same-name wrappers of the C entry points -------------------------------
 
 def cheb_apply(plan: Plan, K, u, Au):
@@ -175,3 +261,11 @@ def cheb_deriv(plan: Plan, axis: int, u, du):
 
 def cheb_rhs(plan: Plan, f, faces, b):
     return plan.rhs(f, faces, b)
+
+
+def cheb_solve(plan: Plan, K, b, u, **opts):
+    return plan.solve(K, b, u, **opts)
+
+
+def cheb_prolong(coarse: Plan, fine: Plan, u_c, u_f):
+    return prolong(coarse, fine, u_c, u_f)

@@ -25,7 +25,7 @@ i32p = C.POINTER(C.c_int)
 
 
 class SolveOpts(C.Structure):
-    """Mirror of ``cheb_solve_opts``."""
+    """Mirror of ``cheb_solve_opts`` (include/cheb.h)."""
     _fields_ = [
         ("mode", i32),
         ("rtol", C.c_double),
@@ -37,9 +37,8 @@ class SolveOpts(C.Structure):
         ("inner_maxiter", i32),
         ("max_refinements", i32),
         ("reorth", i32),
-        ("row_scaling", i32),
         ("precond", i32),
-        ("use_graph", i32),
+        ("kref", C.c_double),
         ("verbose", i32),
     ]
 
@@ -56,8 +55,11 @@ class SolveInfo(C.Structure):
         ("rel_residual", C.c_double),
         ("rel_residual_inner", C.c_double),
         ("seconds", C.c_double),
-        ("e_ref", C.c_double),
+        ("kref", C.c_double),
     ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _SIGS = {
@@ -73,6 +75,16 @@ _SIGS = {
     "cheb_apply": (i32, [vp, i32, vp, vp, vp]),
     "cheb_adjoint_apply": (i32, [vp, i32, vp, vp, vp]),
     "cheb_rhs": (i32, [vp, vp, C.POINTER(vp), vp]),
+    "cheb_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
+    "cheb_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+    "cheb_precond_apply": (i32, [vp, i32, C.c_double, vp, vp]),
+    "cheb_prolong": (i32, [vp, vp, i32, vp, vp]),
+    "cheb_rel_diff": (i32, [vp, vp, vp, f64p]),
+    "cheb_solve_hierarchy": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                   C.POINTER(SolveOpts), C.POINTER(SolveInfo), f64p]),
+    "cheb_launch_count": (C.c_longlong, []),
+    "cheb_profile_enable": (i32, [i32]),
+    "cheb_profile_read": (i32, [f64p, C.POINTER(C.c_longlong)]),
     "cheb_status_str": (C.c_char_p, [i32]),
     "cheb_last_error": (C.c_char_p, []),
 }

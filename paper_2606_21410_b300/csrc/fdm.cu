@@ -1,0 +1,424 @@
+// Fast-diagonalization preconditioner M^{-1} for the collocation system
+// (the paper solves without one; see the design notes).  M is the exact
+// collocation operator with a constant conductivity kref and the same
+// boundary rows.  Its block structure makes M^{-1} r exact:
+//  - interior + single-face nodes: every face row of an interior a-line
+//    couples only that line, so the two end values are eliminated per line
+//    (u_b = G u_int + Binv g, the boundary elimination of Sec. 2.3.1), and
+//    the reduced interior operator is the Kronecker sum kref (A_x + A_y + A_z)
+//    of 1-D operators A_a = S_a Lambda_a S_a^{-1}; it is inverted by three
+//    dense contractions with S^{-1}, a pointwise division by
+//    kref (lx + ly + lz), and three contractions with S;
+//  - edge / corner nodes: their boundary rows do not involve K; each is
+//    solved on its owner axis' line (1x1 or 2x2) once the line interior is
+//    known, edges before corners.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device.cuh"
+#include "fdm.h"
+#include "gemm.h"
+#include "hostmath.h"
+
+namespace cheb {
+
+// ---------------------------------------------------------------------------
+// host set-up
+// ---------------------------------------------------------------------------
+template <typename T>
+static int upload(T** dst, const std::vector<double>& src) {
+  std::vector<T> tmp(src.size());
+  for (size_t i = 0; i < src.size(); ++i) tmp[i] = (T)src[i];
+  CHEB_CUDA(cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, tmp.size())));
+  if (!tmp.empty()) CHEB_CUDA(cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+  return CHEB_OK;
+}
+
+static std::vector<double> transpose(const std::vector<double>& A, int r, int c) {
+  std::vector<double> B((size_t)r * c);
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < c; ++j) B[(size_t)j * r + i] = A[(size_t)i * c + j];
+  return B;
+}
+
+template <typename T>
+static int upload_axis(FdmAxisDev<T>& d, const FdmAxisHost& h) {
+  int st;
+  if ((st = upload(&d.S, h.S))) return st;
+  if ((st = upload(&d.Sinv, h.Sinv))) return st;
+  if ((st = upload(&d.ST, transpose(h.S, h.m, h.m)))) return st;
+  if ((st = upload(&d.SinvT, transpose(h.Sinv, h.m, h.m)))) return st;
+  if ((st = upload(&d.lam, h.lam))) return st;
+  if ((st = upload(&d.G, h.G))) return st;
+  if ((st = upload(&d.Binv, h.Binv))) return st;
+  if ((st = upload(&d.Lh, h.Lh))) return st;
+  if ((st = upload(&d.Drow, h.Drow))) return st;
+  return CHEB_OK;
+}
+
+template <typename T>
+static void free_axis(FdmAxisDev<T>& d) {
+  cudaFree(d.S); cudaFree(d.Sinv); cudaFree(d.ST); cudaFree(d.SinvT); cudaFree(d.lam);
+  cudaFree(d.G); cudaFree(d.Binv); cudaFree(d.Lh); cudaFree(d.Drow);
+  d = FdmAxisDev<T>();
+}
+
+// 1-D tables of axis a: end rows of the boundary conditions, elimination
+// map, reduced interior operator and its eigen-decomposition.
+static int build_axis_host(const cheb_plan_s* p, int a, FdmAxisHost& h) {
+  const int n = p->n[a], N = n - 1, m = N - 1;
+  h.n = n;
+  h.m = m;
+  const double scale = 2.0 / (p->hi[a] - p->lo[a]);
+  std::vector<double> D = dense_deriv_matrix(N, scale);
+  auto Dat = [&](int i, int j) { return D[(size_t)i * n + j]; };
+  // end rows: index 0 is the hi face (2a+1, outward +), index N the lo face (2a, outward -)
+  double B[4] = {0, 0, 0, 0};
+  std::vector<double> Cm((size_t)2 * m, 0.0);
+  if (p->bc[2 * a + 1] == CHEB_DIRICHLET) B[0] = 1.0;
+  else {
+    B[0] = Dat(0, 0); B[1] = Dat(0, N);
+    for (int l = 0; l < m; ++l) Cm[l] = Dat(0, l + 1);
+  }
+  if (p->bc[2 * a] == CHEB_DIRICHLET) B[3] = 1.0;
+  else {
+    B[2] = -Dat(N, 0); B[3] = -Dat(N, N);
+    for (int l = 0; l < m; ++l) Cm[m + l] = -Dat(N, l + 1);
+  }
+  const double det = B[0] * B[3] - B[1] * B[2];
+  if (!(std::fabs(det) > 0)) { set_error("singular end-row block"); return CHEB_ERR_SINGULAR_BC; }
+  h.Binv = {B[3] / det, -B[1] / det, -B[2] / det, B[0] / det};
+  h.G.assign((size_t)2 * m, 0.0);
+  for (int r = 0; r < 2; ++r)
+    for (int l = 0; l < m; ++l)
+      h.G[(size_t)r * m + l] = -(h.Binv[r * 2 + 0] * Cm[l] + h.Binv[r * 2 + 1] * Cm[m + l]);
+  std::vector<double> D2 = matmul(D, D, n, n, n);
+  // reduced operator A = -(D2_II + D2_IB G), lifting Lh = D2_IB Binv
+  std::vector<double> Ared((size_t)m * m);
+  h.Lh.assign((size_t)m * 2, 0.0);
+  for (int i = 0; i < m; ++i) {
+    const double b0 = D2[(size_t)(i + 1) * n + 0], bN = D2[(size_t)(i + 1) * n + N];
+    for (int l = 0; l < m; ++l)
+      Ared[(size_t)i * m + l] = -(D2[(size_t)(i + 1) * n + l + 1] + b0 * h.G[l] + bN * h.G[(size_t)m + l]);
+    h.Lh[(size_t)i * 2 + 0] = b0 * h.Binv[0] + bN * h.Binv[2];
+    h.Lh[(size_t)i * 2 + 1] = b0 * h.Binv[1] + bN * h.Binv[3];
+  }
+  if (!eig_real(Ared, m, h.lam, h.S)) {
+    set_error("eigen-decomposition of the 1-D reduced operator failed");
+    return CHEB_ERR_UNSUPPORTED;
+  }
+  h.Sinv = h.S;
+  if (!invert(h.Sinv, m)) { set_error("singular eigenvector matrix"); return CHEB_ERR_UNSUPPORTED; }
+  h.Drow.assign((size_t)2 * n, 0.0);
+  for (int l = 0; l < n; ++l) {
+    h.Drow[l] = Dat(0, l);
+    h.Drow[(size_t)n + l] = Dat(N, l);
+  }
+  return CHEB_OK;
+}
+
+int fdm_setup(const cheb_plan_s* p, Fdm& f) {
+  if (f.ready) return CHEB_OK;
+  for (int a = 0; a < p->dim; ++a) {
+    int st = build_axis_host(p, a, f.host[a]);
+    if (st) return st;
+    if ((st = upload_axis<double>(f.d64[a], f.host[a]))) return st;
+    if ((st = upload_axis<float>(f.d32[a], f.host[a]))) return st;
+  }
+  for (int a = 0; a < 3; ++a) f.m[a] = a < p->dim ? p->n[a] - 2 : 1;
+  f.ready = true;
+  return CHEB_OK;
+}
+
+void fdm_free(Fdm& f) {
+  for (int a = 0; a < 3; ++a) { free_axis(f.d64[a]); free_axis(f.d32[a]); }
+  cudaFree(f.U64[0]); cudaFree(f.U64[1]); cudaFree(f.U32[0]); cudaFree(f.U32[1]);
+  f.U64[0] = f.U64[1] = nullptr;
+  f.U32[0] = f.U32[1] = nullptr;
+  f.ready = false;
+}
+
+// ---------------------------------------------------------------------------
+// device kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FdmK {
+  int m[3], off[3];
+  const T* Lh[3];
+  const T* lam[3];
+  const T* G[3];
+  const T* Binv[3];
+  const T* Drow[3];
+};
+
+__device__ __forceinline__ size_t gidx3(const Geom& g, int i, int j, int k) {
+  return ((size_t)k * g.n[1] + j) * g.n[0] + i;
+}
+
+// U (compact interior) = r_I + kref sum_a Lh_a (r at the two ends of the a-line)
+template <typename T>
+__global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__ r, T* __restrict__ U) {
+  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(c % t.m[0]);
+    const int cj = (int)((c / t.m[0]) % t.m[1]);
+    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
+    const int idx[3] = {ci + t.off[0], cj + t.off[1], ck + t.off[2]};
+    T v = r[gidx3(g, idx[0], idx[1], idx[2])];
+    const int cl[3] = {ci, cj, ck};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= g.dim) break;
+      int e0[3] = {idx[0], idx[1], idx[2]}, eN[3] = {idx[0], idx[1], idx[2]};
+      e0[a] = 0;
+      eN[a] = g.n[a] - 1;
+      const T r0 = r[gidx3(g, e0[0], e0[1], e0[2])], rN = r[gidx3(g, eN[0], eN[1], eN[2])];
+      v += kref * (t.Lh[a][cl[a] * 2 + 0] * r0 + t.Lh[a][cl[a] * 2 + 1] * rN);
+    }
+    U[c] = v;
+  }
+}
+
+template <typename T>
+__global__ void fdm_scale_kernel(FdmK<T> t, int dim, T kref, T* __restrict__ U) {
+  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(c % t.m[0]);
+    const int cj = (int)((c / t.m[0]) % t.m[1]);
+    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
+    T l = t.lam[0][ci];
+    if (dim > 1) l += t.lam[1][cj];
+    if (dim > 2) l += t.lam[2][ck];
+    U[c] = U[c] / (kref * l);
+  }
+}
+
+template <typename T>
+__global__ void fdm_scatter_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, T* __restrict__ x) {
+  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(c % t.m[0]);
+    const int cj = (int)((c / t.m[0]) % t.m[1]);
+    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
+    x[gidx3(g, ci + t.off[0], cj + t.off[1], ck + t.off[2])] = U[c];
+  }
+}
+
+// End values of every interior a-line: [x0; xN] = G u_int(line) + Binv [r0; rN].
+// One thread per line; for a > 0 consecutive threads take x-adjacent lines.
+template <typename T>
+__global__ void fdm_faces_kernel(Geom g, FdmK<T> t, int a, const T* __restrict__ U,
+                                 const T* __restrict__ r, T* __restrict__ x) {
+  const int ma = t.m[a];
+  // the two other compact axes
+  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  const size_t lines = (size_t)t.m[b] * t.m[c];
+  const size_t sx = 1, sy = t.m[0], sz = (size_t)t.m[0] * t.m[1];
+  const size_t str[3] = {sx, sy, sz};
+  const T* G0 = t.G[a];
+  const T* GN = t.G[a] + ma;
+  const T* Bi = t.Binv[a];
+  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < lines; L += (size_t)gridDim.x * blockDim.x) {
+    const int cb = (int)(L % t.m[b]), cc = (int)(L / t.m[b]);
+    int cidx[3];
+    cidx[a] = 0; cidx[b] = cb; cidx[c] = cc;
+    const size_t base = cidx[0] * str[0] + cidx[1] * str[1] + cidx[2] * str[2];
+    T s0 = 0, sN = 0;
+    for (int l = 0; l < ma; ++l) {
+      const T v = U[base + (size_t)l * str[a]];
+      s0 += G0[l] * v;
+      sN += GN[l] * v;
+    }
+    int idx[3] = {cidx[0] + t.off[0], cidx[1] + t.off[1], cidx[2] + t.off[2]};
+    idx[a] = 0;
+    const size_t p0 = gidx3(g, idx[0], idx[1], idx[2]);
+    idx[a] = g.n[a] - 1;
+    const size_t pN = gidx3(g, idx[0], idx[1], idx[2]);
+    const T r0 = r[p0], rN = r[pN];
+    x[p0] = s0 + Bi[0] * r0 + Bi[1] * rN;
+    x[pN] = sN + Bi[2] * r0 + Bi[3] * rN;
+  }
+}
+
+// Boundary-row solve on a-lines that lie in one face (kind 1: the third
+// index interior) or in two faces (kind 2).  End nodes owned by a Neumann
+// face of axis a are solved from their rows s (D x)_e = r_e with the line
+// interior known; Dirichlet-owned ends copy r; other ends belong to another
+// axis' line and are left alone.
+template <typename T>
+__global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __restrict__ r,
+                                 T* __restrict__ x) {
+  const int nb_axes = g.dim - 1;  // other active axes
+  int others[2], no = 0;
+  for (int q = 0; q < g.dim; ++q)
+    if (q != a) others[no++] = q;
+  // enumerate lines
+  int total;
+  if (kind == 1) {
+    // (which other axis is on its face, side, interior index of the remaining axis)
+    const int rem = (nb_axes == 2) ? 1 : 0;
+    int cnt = 0;
+    for (int q = 0; q < nb_axes; ++q) {
+      const int cax = rem ? others[1 - q] : -1;
+      cnt += 2 * (cax >= 0 ? g.n[cax] - 2 : 1);
+    }
+    total = cnt;
+  } else {
+    total = (nb_axes == 2) ? 4 : 0;
+  }
+  const int n = g.n[a], N = n - 1;
+  const T* D0 = t.Drow[a];
+  const T* DN = t.Drow[a] + n;
+  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < total; L += gridDim.x * blockDim.x) {
+    int idx[3] = {0, 0, 0};
+    if (kind == 1) {
+      int rest = L, q = 0;
+      for (; q < nb_axes; ++q) {
+        const int cax = (nb_axes == 2) ? others[1 - q] : -1;
+        const int span = 2 * (cax >= 0 ? g.n[cax] - 2 : 1);
+        if (rest < span) break;
+        rest -= span;
+      }
+      const int bax = others[q];
+      const int cax = (nb_axes == 2) ? others[1 - q] : -1;
+      const int side = rest & 1, tt = rest >> 1;
+      idx[bax] = side ? 0 : g.n[bax] - 1;  // side 1 (hi) is index 0
+      if (cax >= 0) idx[cax] = 1 + tt;
+    } else {
+      idx[others[0]] = (L & 1) ? 0 : g.n[others[0]] - 1;
+      idx[others[1]] = (L & 2) ? 0 : g.n[others[1]] - 1;
+    }
+    int e[3] = {idx[0], idx[1], idx[2]};
+    e[a] = 0;
+    const size_t p0 = gidx3(g, e[0], e[1], e[2]);
+    const int o0 = owner_face(g, e[0], e[1], e[2]);
+    e[a] = N;
+    const size_t pN = gidx3(g, e[0], e[1], e[2]);
+    const int oN = owner_face(g, e[0], e[1], e[2]);
+    const bool dir0 = g.bc[o0] == CHEB_DIRICHLET, dirN = g.bc[oN] == CHEB_DIRICHLET;
+    const bool neu0 = (o0 == 2 * a + 1) && !dir0;
+    const bool neuN = (oN == 2 * a) && !dirN;
+    const T r0 = r[p0], rN = r[pN];
+    if (dir0) x[p0] = r0;
+    if (dirN) x[pN] = rN;
+    if (!neu0 && !neuN) continue;
+    T s0 = 0, sN = 0;
+    for (int l = 1; l < N; ++l) {
+      e[a] = l;
+      const T v = x[gidx3(g, e[0], e[1], e[2])];
+      s0 += D0[l] * v;
+      sN += DN[l] * v;
+    }
+    // rows: +(D00 x0 + D0N xN + s0) = r0 ; -(DN0 x0 + DNN xN + sN) = rN
+    const T a00 = D0[0], a01 = D0[N], a10 = DN[0], a11 = DN[N];
+    const T b0 = r0 - s0, b1 = -rN - sN;
+    if (neu0 && neuN) {
+      const T det = a00 * a11 - a01 * a10;
+      x[p0] = (b0 * a11 - a01 * b1) / det;
+      x[pN] = (a00 * b1 - a10 * b0) / det;
+    } else if (neu0) {
+      const T xN = dirN ? rN : x[pN];
+      x[p0] = (b0 - a01 * xN) / a00;
+    } else {
+      const T x0 = dir0 ? r0 : x[p0];
+      x[pN] = (b1 - a10 * x0) / a11;
+    }
+  }
+}
+
+template <typename T> static FdmK<T> make_k(const Fdm& f, int dim);
+template <> FdmK<double> make_k<double>(const Fdm& f, int dim) {
+  FdmK<double> k;
+  for (int a = 0; a < 3; ++a) {
+    k.m[a] = f.m[a];
+    k.off[a] = a < dim ? 1 : 0;
+    k.Lh[a] = f.d64[a].Lh; k.lam[a] = f.d64[a].lam; k.G[a] = f.d64[a].G;
+    k.Binv[a] = f.d64[a].Binv; k.Drow[a] = f.d64[a].Drow;
+  }
+  return k;
+}
+template <> FdmK<float> make_k<float>(const Fdm& f, int dim) {
+  FdmK<float> k;
+  for (int a = 0; a < 3; ++a) {
+    k.m[a] = f.m[a];
+    k.off[a] = a < dim ? 1 : 0;
+    k.Lh[a] = f.d32[a].Lh; k.lam[a] = f.d32[a].lam; k.G[a] = f.d32[a].G;
+    k.Binv[a] = f.d32[a].Binv; k.Drow[a] = f.d32[a].Drow;
+  }
+  return k;
+}
+
+template <typename T> static T** ubuf(Fdm& f);
+template <> double** ubuf<double>(Fdm& f) { return f.U64; }
+template <> float** ubuf<float>(Fdm& f) { return f.U32; }
+template <typename T> static const FdmAxisDev<T>& axdev(const Fdm& f, int a);
+template <> const FdmAxisDev<double>& axdev<double>(const Fdm& f, int a) { return f.d64[a]; }
+template <> const FdmAxisDev<float>& axdev<float>(const Fdm& f, int a) { return f.d32[a]; }
+
+static int grid_for(size_t n) {
+  return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+}
+
+template <typename T>
+int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaStream_t s) {
+  const Geom g = p->geom();
+  const FdmK<T> k = make_k<T>(f, p->dim);
+  const size_t tot = (size_t)f.m[0] * f.m[1] * f.m[2];
+  T** U = ubuf<T>(f);
+  if (!U[0]) {
+    CHEB_CUDA(cudaMalloc(&U[0], sizeof(T) * tot));
+    CHEB_CUDA(cudaMalloc(&U[1], sizeof(T) * tot));
+  }
+  const int mx = f.m[0], my = f.m[1], mz = f.m[2];
+  fdm_lift_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, (T)kref, r, U[0]);
+  CHEB_LAUNCH_CHECK("fdm_lift_kernel");
+  int cur = 0;
+  auto contract = [&](int a, bool inverse) -> int {
+    const FdmAxisDev<T>& d = axdev<T>(f, a);
+    const int o = 1 - cur;
+    int st;
+    if (a == 0) {
+      st = k_gemm<T>(my * mz, mx, mx, U[cur], mx, 0, inverse ? d.SinvT : d.ST, mx, 0, U[o], mx, 0, 1, s);
+    } else if (a == 1) {
+      st = k_gemm<T>(my, mx, my, inverse ? d.Sinv : d.S, my, 0, U[cur], mx, (long long)my * mx, U[o], mx,
+                     (long long)my * mx, mz, s);
+    } else {
+      st = k_gemm<T>(mz, my * mx, mz, inverse ? d.Sinv : d.S, mz, 0, U[cur], my * mx, 0, U[o], my * mx, 0, 1, s);
+    }
+    cur = o;
+    return st;
+  };
+  int st;
+  for (int a = 0; a < p->dim; ++a)
+    if ((st = contract(a, true))) return st;
+  fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+  CHEB_LAUNCH_CHECK("fdm_scale_kernel");
+  for (int a = p->dim - 1; a >= 0; --a)
+    if ((st = contract(a, false))) return st;
+  fdm_scatter_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, U[cur], x);
+  CHEB_LAUNCH_CHECK("fdm_scatter_kernel");
+  for (int a = 0; a < p->dim; ++a) {
+    const size_t lines = tot / f.m[a];
+    fdm_faces_kernel<T><<<grid_for(lines), 256, 0, s>>>(g, k, a, U[cur], r, x);
+    CHEB_LAUNCH_CHECK("fdm_faces_kernel");
+  }
+  if (p->dim >= 2) {
+    for (int a = 0; a < p->dim; ++a) {
+      fdm_bline_kernel<T><<<8, 128, 0, s>>>(g, k, a, 1, r, x);
+      CHEB_LAUNCH_CHECK("fdm_bline_kernel");
+    }
+  }
+  if (p->dim == 3) {
+    for (int a = 0; a < 3; ++a) {
+      fdm_bline_kernel<T><<<1, 32, 0, s>>>(g, k, a, 2, r, x);
+      CHEB_LAUNCH_CHECK("fdm_bline_kernel");
+    }
+  }
+  return CHEB_OK;
+}
+
+template int fdm_apply<double>(const cheb_plan_s*, Fdm&, double, const double*, double*, cudaStream_t);
+template int fdm_apply<float>(const cheb_plan_s*, Fdm&, double, const float*, float*, cudaStream_t);
+
+}  // namespace cheb

@@ -1,0 +1,39 @@
+// Fast-diagonalization preconditioner (fdm.cu).
+#pragma once
+
+#include <vector>
+
+#include "internal.h"
+
+namespace cheb {
+
+struct FdmAxisHost {
+  int n = 0, m = 0;                  // points, interior points (n - 2)
+  std::vector<double> S, Sinv, lam;  // reduced 1-D operator = S diag(lam) S^{-1}
+  std::vector<double> G, Binv, Lh;   // end elimination: u_b = G u_int + Binv g; lifting D2_IB Binv
+  std::vector<double> Drow;          // rows 0 and N of D (2 x n)
+};
+
+template <typename T>
+struct FdmAxisDev {
+  T *S = nullptr, *Sinv = nullptr, *ST = nullptr, *SinvT = nullptr, *lam = nullptr;
+  T *G = nullptr, *Binv = nullptr, *Lh = nullptr, *Drow = nullptr;
+};
+
+struct Fdm {
+  bool ready = false;
+  int m[3] = {1, 1, 1};
+  FdmAxisHost host[3];
+  FdmAxisDev<double> d64[3];
+  FdmAxisDev<float> d32[3];
+  double* U64[2] = {nullptr, nullptr};  // compact interior work buffers
+  float* U32[2] = {nullptr, nullptr};
+};
+
+int fdm_setup(const cheb_plan_s* p, Fdm& f);
+void fdm_free(Fdm& f);
+// x = M^{-1} r with M the constant-kref collocation operator (same boundary rows).
+template <typename T>
+int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaStream_t s);
+
+}  // namespace cheb

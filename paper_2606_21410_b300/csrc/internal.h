@@ -74,11 +74,22 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::cheb::cuda_fail(_e, #call); \
   } while (0)
 
+void count_launch();
+
 #define CHEB_LAUNCH_CHECK(what)                           \
   do {                                                    \
+    ::cheb::count_launch();                               \
     cudaError_t _e = cudaGetLastError();                  \
     if (_e != cudaSuccess) return ::cheb::cuda_fail(_e, what); \
   } while (0)
+
+// Per-phase device timing with CUDA events (off unless cheb_profile_enable).
+enum ProfCat {
+  kProfApply64 = 0, kProfApply32, kProfPrec64, kProfPrec32, kProfOrth64, kProfOrth32,
+  kProfProlong, kProfOther, kProfNCat
+};
+void prof_begin(int cat, cudaStream_t s);
+void prof_end(int cat, cudaStream_t s);
 
 // Line-pass kinds (apply.cu).
 enum PassKind {

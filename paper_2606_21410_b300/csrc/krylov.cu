@@ -1,0 +1,285 @@
+// Vector kernels of the LGMRES Arnoldi process and the refinement loop:
+// fused multi-dot products (one read of w for all basis vectors), fused
+// multi-axpy with the norm of the result, scaling, casts and the FP64
+// residual update.  Reductions are deterministic: per-CTA partials in a
+// fixed order, the last CTA to finish sums the partials in index order.
+#include <algorithm>
+
+#include "krylov.h"
+
+namespace cheb {
+
+constexpr int kRedThreads = 256;
+
+static int red_blocks(size_t n) {
+  // enough CTAs to fill the GPU (148 SMs), never more than the work needs
+  size_t b = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
+  return (int)std::max<size_t>(1, std::min<size_t>(b, kRedBlocks));
+}
+
+template <typename T>
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// Block-reduce per-thread values and store the block's sums to
+// part[o * gridDim.x + blockIdx.x]: slot i < cnt goes to output o = i and,
+// when `extra`, the last slot MAXV-1 goes to output o = cnt.  Then the last
+// CTA sums the partials (fixed order, FP64) into out[o].  The slot loop is
+// unrolled so acc stays in registers.
+template <typename T, int MAXV>
+__device__ void block_reduce_store(T (&acc)[MAXV], int cnt, bool extra, double* part,
+                                   unsigned* counter, double* out) {
+  __shared__ double sred[kRedThreads / 32][MAXV];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nout = cnt + (extra ? 1 : 0);
+#pragma unroll
+  for (int i = 0; i < MAXV; ++i) {
+    const bool active = (i < cnt) || (extra && i == MAXV - 1);
+    if (active) {
+      const int o = (i < cnt) ? i : cnt;
+      T v = warp_sum_t<T>(acc[i]);
+      if (lane == 0) sred[wid][o] = (double)v;
+    }
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) s += sred[w][o];
+    part[(size_t)o * gridDim.x + blockIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // one warp per output value, lanes stride the partials, fixed tree order
+  for (int o = wid; o < nout; o += kRedThreads / 32) {
+    double s = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)o * gridDim.x + b);
+    s = warp_sum<double>(s);
+    if (lane == 0) out[o] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
+}
+
+// out[i] = <src_i, w>, i < cnt (cnt <= kMaxVecs); optionally also <w, w>
+// stored at out[cnt].
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+mdot_kernel(VecList<T> src, int cnt, const T* __restrict__ w, size_t n, int with_self,
+            double* part, unsigned* counter, double* out) {
+  T acc[kMaxVecs + 1];
+#pragma unroll
+  for (int i = 0; i <= kMaxVecs; ++i) acc[i] = (T)0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+    const T wv = w[e];
+#pragma unroll
+    for (int i = 0; i < kMaxVecs; ++i)
+      if (i < cnt) acc[i] += src.p[i][e] * wv;
+    if (with_self) acc[kMaxVecs] += wv * wv;
+  }
+  block_reduce_store<T, kMaxVecs + 1>(acc, cnt, with_self != 0, part, counter, out);
+}
+
+// y = beta * y + sum_i c_i src_i (cnt <= kMaxVecs); optionally ||y||^2 -> out[0].
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+maxpy_kernel(VecList<T> src, CoefList coef, const double* __restrict__ cdev, double csign, int cnt,
+             double beta, T* __restrict__ y, size_t n, int want_norm, double* part,
+             unsigned* counter, double* out) {
+  T c[kMaxVecs];
+#pragma unroll
+  for (int i = 0; i < kMaxVecs; ++i)
+    c[i] = (T)(cdev ? (i < cnt ? csign * cdev[i] : 0.0) : coef.c[i]);
+  T acc[1] = {(T)0};
+  const T b = (T)beta;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+    T v = (beta == 0.0) ? (T)0 : b * y[e];
+#pragma unroll
+    for (int i = 0; i < kMaxVecs; ++i)
+      if (i < cnt) v += c[i] * src.p[i][e];
+    y[e] = v;
+    acc[0] += v * v;
+  }
+  if (want_norm) block_reduce_store<T, 1>(acc, 1, false, part, counter, out);
+}
+
+template <typename T>
+__global__ void scale_kernel(T* __restrict__ y, const T* __restrict__ x, double s, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const T sv = (T)s;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) y[e] = sv * x[e];
+}
+
+// y (To) = s * x (Ti)
+template <typename To, typename Ti>
+__global__ void cast_scale_kernel(To* __restrict__ y, const Ti* __restrict__ x, double s, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride)
+    y[e] = (To)(s * (double)x[e]);
+}
+
+// y (FP64) += s * x (Ti)
+template <typename Ti>
+__global__ void axpy64_kernel(double* __restrict__ y, const Ti* __restrict__ x, double s, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride)
+    y[e] += s * (double)x[e];
+}
+
+// r = b - r  (r holds A x on entry)
+template <typename T>
+__global__ void residual_kernel(T* __restrict__ r, const T* __restrict__ b, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) r[e] = b[e] - r[e];
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int elem_blocks(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, 148 * 8));
+}
+
+template <typename T>
+int k_mdot(const ReduceScratch& rs, const T* const* src, int cnt, const T* w, size_t n,
+           bool with_self, double* out_dev, cudaStream_t s) {
+  if (cnt > kMaxVecs) { set_error("too many vectors in multi-dot"); return CHEB_ERR_ARG; }
+  VecList<T> L;
+  for (int i = 0; i < kMaxVecs; ++i) L.p[i] = i < cnt ? src[i] : nullptr;
+  const int nb = red_blocks(n);
+  mdot_kernel<T><<<nb, kRedThreads, 0, s>>>(L, cnt, w, n, with_self ? 1 : 0, rs.part, rs.counter,
+                                            out_dev);
+  CHEB_LAUNCH_CHECK("mdot_kernel");
+  return CHEB_OK;
+}
+
+template <typename T>
+int k_maxpy(const ReduceScratch& rs, const T* const* src, const double* coef, int cnt, double beta,
+            T* y, size_t n, double* norm2_dev, cudaStream_t s) {
+  if (cnt > kMaxVecs) { set_error("too many vectors in multi-axpy"); return CHEB_ERR_ARG; }
+  VecList<T> L;
+  CoefList C;
+  for (int i = 0; i < kMaxVecs; ++i) {
+    L.p[i] = i < cnt ? src[i] : nullptr;
+    C.c[i] = i < cnt ? coef[i] : 0.0;
+  }
+  const int nb = red_blocks(n);
+  maxpy_kernel<T><<<nb, kRedThreads, 0, s>>>(L, C, nullptr, 0.0, cnt, beta, y, n, norm2_dev ? 1 : 0,
+                                             rs.part, rs.counter, norm2_dev);
+  CHEB_LAUNCH_CHECK("maxpy_kernel");
+  return CHEB_OK;
+}
+
+template <typename T>
+int k_maxpy_dev(const ReduceScratch& rs, const T* const* src, const double* coef_dev, double sign,
+                int cnt, double beta, T* y, size_t n, double* norm2_dev, cudaStream_t s) {
+  if (cnt > kMaxVecs) { set_error("too many vectors in multi-axpy"); return CHEB_ERR_ARG; }
+  VecList<T> L;
+  CoefList C;
+  for (int i = 0; i < kMaxVecs; ++i) {
+    L.p[i] = i < cnt ? src[i] : nullptr;
+    C.c[i] = 0.0;
+  }
+  const int nb = red_blocks(n);
+  maxpy_kernel<T><<<nb, kRedThreads, 0, s>>>(L, C, coef_dev, sign, cnt, beta, y, n, norm2_dev ? 1 : 0,
+                                             rs.part, rs.counter, norm2_dev);
+  CHEB_LAUNCH_CHECK("maxpy_kernel");
+  return CHEB_OK;
+}
+
+// y *= 1 / sqrt(*norm2) (when positive)
+template <typename T>
+__global__ void scale_inv_norm_kernel(T* __restrict__ y, const double* __restrict__ norm2, size_t n) {
+  const double nv = *norm2;
+  if (!(nv > 0.0)) return;
+  const T sv = (T)(1.0 / sqrt(nv));
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) y[e] *= sv;
+}
+
+template <typename T>
+int k_scale_inv_norm(T* y, const double* norm2_dev, size_t n, cudaStream_t s) {
+  scale_inv_norm_kernel<T><<<elem_blocks(n), 256, 0, s>>>(y, norm2_dev, n);
+  CHEB_LAUNCH_CHECK("scale_inv_norm_kernel");
+  return CHEB_OK;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+sum_log_kernel(const double* __restrict__ K, size_t n, double* part, unsigned* counter, double* out) {
+  double acc[1] = {0.0};
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) acc[0] += log(K[e]);
+  block_reduce_store<double, 1>(acc, 1, false, part, counter, out);
+}
+
+int k_sum_log(const ReduceScratch& rs, const double* K, size_t n, double* out_dev, cudaStream_t s) {
+  sum_log_kernel<<<red_blocks(n), kRedThreads, 0, s>>>(K, n, rs.part, rs.counter, out_dev);
+  CHEB_LAUNCH_CHECK("sum_log_kernel");
+  return CHEB_OK;
+}
+
+template <typename T>
+int k_scale(T* y, const T* x, double sc, size_t n, cudaStream_t s) {
+  scale_kernel<T><<<elem_blocks(n), 256, 0, s>>>(y, x, sc, n);
+  CHEB_LAUNCH_CHECK("scale_kernel");
+  return CHEB_OK;
+}
+
+template <typename To, typename Ti>
+int k_cast_scale(To* y, const Ti* x, double sc, size_t n, cudaStream_t s) {
+  cast_scale_kernel<To, Ti><<<elem_blocks(n), 256, 0, s>>>(y, x, sc, n);
+  CHEB_LAUNCH_CHECK("cast_scale_kernel");
+  return CHEB_OK;
+}
+
+template <typename Ti>
+int k_axpy64(double* y, const Ti* x, double sc, size_t n, cudaStream_t s) {
+  axpy64_kernel<Ti><<<elem_blocks(n), 256, 0, s>>>(y, x, sc, n);
+  CHEB_LAUNCH_CHECK("axpy64_kernel");
+  return CHEB_OK;
+}
+
+template <typename T>
+int k_residual(T* r, const T* b, size_t n, cudaStream_t s) {
+  residual_kernel<T><<<elem_blocks(n), 256, 0, s>>>(r, b, n);
+  CHEB_LAUNCH_CHECK("residual_kernel");
+  return CHEB_OK;
+}
+
+template int k_mdot<double>(const ReduceScratch&, const double* const*, int, const double*, size_t, bool, double*, cudaStream_t);
+template int k_mdot<float>(const ReduceScratch&, const float* const*, int, const float*, size_t, bool, double*, cudaStream_t);
+template int k_maxpy<double>(const ReduceScratch&, const double* const*, const double*, int, double, double*, size_t, double*, cudaStream_t);
+template int k_maxpy<float>(const ReduceScratch&, const float* const*, const double*, int, double, float*, size_t, double*, cudaStream_t);
+template int k_maxpy_dev<double>(const ReduceScratch&, const double* const*, const double*, double, int, double, double*, size_t, double*, cudaStream_t);
+template int k_maxpy_dev<float>(const ReduceScratch&, const float* const*, const double*, double, int, double, float*, size_t, double*, cudaStream_t);
+template int k_scale_inv_norm<double>(double*, const double*, size_t, cudaStream_t);
+template int k_scale_inv_norm<float>(float*, const double*, size_t, cudaStream_t);
+template int k_scale<double>(double*, const double*, double, size_t, cudaStream_t);
+template int k_scale<float>(float*, const float*, double, size_t, cudaStream_t);
+template int k_cast_scale<float, double>(float*, const double*, double, size_t, cudaStream_t);
+template int k_cast_scale<double, float>(double*, const float*, double, size_t, cudaStream_t);
+template int k_cast_scale<double, double>(double*, const double*, double, size_t, cudaStream_t);
+template int k_axpy64<float>(double*, const float*, double, size_t, cudaStream_t);
+template int k_axpy64<double>(double*, const double*, double, size_t, cudaStream_t);
+template int k_residual<double>(double*, const double*, size_t, cudaStream_t);
+template int k_residual<float>(float*, const float*, size_t, cudaStream_t);
+
+}  // namespace cheb

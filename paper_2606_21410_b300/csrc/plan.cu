@@ -1,10 +1,13 @@
 // Plan creation and the plain entry points: nodes, routes, derivative line
 // passes, operator apply (forward and transposed), right-hand side.
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
+#include "hostmath.h"
 #include "internal.h"
 
 namespace cheb {
@@ -22,41 +25,68 @@ int launch_rhs(const cheb_plan_s* p, const double* f, const double* const face_v
                cudaStream_t s);
 void free_workspace(cheb_plan_s* p);
 
+// ---------------------------------------------------------------------------
+// launch counter and phase profiler
+// ---------------------------------------------------------------------------
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+struct ProfRec { int cat; cudaEvent_t a, b; };
+struct ProfState {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<ProfRec> recs;
+  cudaEvent_t open[kProfNCat] = {};
+  double ms[kProfNCat] = {};
+  long long cnt[kProfNCat] = {};
+};
+ProfState g_prof;
+std::mutex g_prof_mu;
+cudaEvent_t take_event() {
+  if (!g_prof.pool.empty()) { cudaEvent_t e = g_prof.pool.back(); g_prof.pool.pop_back(); return e; }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+void collect_locked() {
+  for (auto& r : g_prof.recs) {
+    cudaEventSynchronize(r.b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    g_prof.ms[r.cat] += t;
+    g_prof.cnt[r.cat] += 1;
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.recs.clear();
+}
+}  // namespace
+
+void prof_begin(int cat, cudaStream_t s) {
+  if (!g_prof.on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, s);
+  g_prof.open[cat] = e;
+}
+
+void prof_end(int cat, cudaStream_t s) {
+  if (!g_prof.on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof.open[cat]) return;
+  cudaEvent_t e = take_event();
+  cudaEventRecord(e, s);
+  g_prof.recs.push_back({cat, g_prof.open[cat], e});
+  g_prof.open[cat] = nullptr;
+  if (g_prof.recs.size() > 4096) collect_locked();
+}
+
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 // Reference CGL coordinate x_j = cos(pi j / N), evaluated as
 // sin(pi (N - 2j) / (2N)) (same value; exactly antisymmetric).
 static double cgl_ref(int j, int N) { return std::sin(M_PI * (double)(N - 2 * j) / (2.0 * N)); }
-
-// Dense derivative matrix on [lo, hi], built column by column from the
-// transform-route definition (DCT-I, closed-form recurrence, DCT-I) with
-// direct cosine sums in FP64.  Row-major: D[i * n + j] = d(l_j)/dt at t_i.
-static std::vector<double> dense_from_transform(int N, double scale) {
-  const int n = N + 1;
-  std::vector<double> cosv(2 * N);
-  for (int t = 0; t < 2 * N; ++t) cosv[t] = std::cos(M_PI * t / N);
-  auto m = [&](int k) { return (k == 0 || k == N) ? 1.0 : 2.0; };
-  std::vector<double> D((size_t)n * n), G(n), beta(n);
-  for (int col = 0; col < n; ++col) {
-    // F_k = sum_n m_n cos(pi k n / N) e_col[n] = m_col cos(pi k col / N)
-    for (int k = 0; k < n; ++k) {
-      const double F = m(col) * cosv[(k * col) % (2 * N)];
-      const double ck = (k == N) ? 0.5 : 1.0;
-      G[k] = k * ck * scale / N * F;
-    }
-    for (int k = 0; k < n; ++k) {
-      double s = 0.0;
-      for (int j = k + 1; j <= N; j += 2) s += G[j];
-      beta[k] = (k == N) ? 0.0 : s;
-    }
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int k = 0; k < n; ++k) s += m(k) * cosv[(k * i) % (2 * N)] * beta[k];
-      D[(size_t)i * n + col] = s;
-    }
-  }
-  return D;
-}
 
 static int build_axis(cheb_plan_s* p, int a) {
   AxisTables& t = p->ax[a];
@@ -81,7 +111,7 @@ static int build_axis(cheb_plan_s* p, int a) {
     CHEB_CUDA(cudaMemcpy(t.tw32, tw32.data(), sizeof(float2) * t.P, cudaMemcpyHostToDevice));
   }
   if (t.dense_ok) {
-    std::vector<double> D = dense_from_transform(t.N, t.scale);
+    std::vector<double> D = dense_deriv_matrix(t.N, t.scale);
     std::vector<float> D32(D.size());
     for (size_t i = 0; i < D.size(); ++i) D32[i] = (float)D[i];
     CHEB_CUDA(cudaMalloc(&t.D64, sizeof(double) * D.size()));
@@ -108,6 +138,26 @@ using namespace cheb;
 extern "C" {
 
 const char* cheb_last_error(void) { return g_last_error.c_str(); }
+
+long long cheb_launch_count(void) { return g_launches.load(); }
+
+int cheb_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  collect_locked();
+  for (int c = 0; c < kProfNCat; ++c) { g_prof.ms[c] = 0.0; g_prof.cnt[c] = 0; g_prof.open[c] = nullptr; }
+  g_prof.on = on != 0;
+  return CHEB_OK;
+}
+
+int cheb_profile_read(double* ms, long long* counts) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  collect_locked();
+  for (int c = 0; c < kProfNCat; ++c) {
+    if (ms) ms[c] = g_prof.ms[c];
+    if (counts) counts[c] = g_prof.cnt[c];
+  }
+  return CHEB_OK;
+}
 
 const char* cheb_status_str(int status) {
   switch (status) {

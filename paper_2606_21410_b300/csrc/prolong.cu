@@ -1,0 +1,204 @@
+// Modal prolongation N -> 2N (Sec. 2.3.3, Alg. 4): per axis and per line,
+// coarse nodal values -> Chebyshev coefficients a_k = c_k DCT-I(f)_k / N,
+// zero-padding to degree 2N, and evaluation at the fine CGL nodes
+// f_fine(x_n) = sum_{k<=N} a_k cos(pi k n / 2N) = DCT-I_{2N}(beta)_n with
+// beta_0 = a_0, beta_k = a_k / 2 (1 <= k <= N, k = N is an interior mode of
+// the fine transform), beta_k = 0 beyond.  Both transforms are warp FFTs of
+// the even extensions (lengths P = 2N and 2P), two lines per complex FFT.
+// Three axis passes, x then y then z, through two scratch arrays.
+#include <algorithm>
+#include <cmath>
+
+#include "device.cuh"
+#include "fdm.h"
+#include "krylov.h"
+#include "prolong.h"
+
+namespace cheb {
+
+__host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <typename T>
+static size_t prolong_smem(int nc, int PC) {
+  const int nf = 2 * (nc - 1) + 1;
+  const int ldx = nf | 1;
+  return al16(sizeof(T) * kTileL * ldx) + al16(2 * sizeof(T) * (size_t)(kTileL / 2) * 2 * PC) +
+         al16(2 * sizeof(T) * (size_t)2 * PC);
+}
+
+// dims: extents of the input array (axis a has nc points); the output has
+// 2(nc-1)+1 points along a.
+template <typename T, int PC>
+__global__ void __launch_bounds__(kThreads)
+prolong_pass_kernel(int a, int nx, int ny, int nz, const typename C2<T>::t* __restrict__ twc,
+                    const typename C2<T>::t* __restrict__ twf, const T* __restrict__ in,
+                    T* __restrict__ out) {
+  typedef typename C2<T>::t C;
+  constexpr int NC = PC / 2;         // coarse N
+  constexpr int PF = 2 * PC;         // fine FFT length
+  constexpr int NF = 2 * NC;         // fine N
+  const int nc = NC + 1, nf = NF + 1;
+  const int ldx = nf | 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* p = smem_raw;
+  T* X = (T*)p;      p += al16(sizeof(T) * kTileL * ldx);
+  C* Cb = (C*)p;     p += al16(2 * sizeof(T) * (size_t)(kTileL / 2) * PF);
+  C* tw = (C*)p;     // fine twiddles; coarse twiddles are every other one
+  for (int t = threadIdx.x; t < PF; t += blockDim.x) tw[t] = twf[t];
+  (void)twc;
+  // tile geometry: lines are indexed by the two other axes
+  const int dims_in[3] = {nx, ny, nz};
+  int dims_out[3] = {nx, ny, nz};
+  dims_out[a] = nf;
+  int line0 = 0, i0 = 0, outer = 0;
+  if (a == 0) line0 = blockIdx.x * kTileL;
+  else {
+    const int nbx = (nx + kTileL - 1) / kTileL;
+    i0 = (blockIdx.x % nbx) * kTileL;
+    outer = blockIdx.x / nbx;
+  }
+  auto gidx = [&](const int* dims, int l, int pt, size_t& g) -> bool {
+    if (a == 0) {
+      const int line = line0 + l;
+      if (line >= dims[1] * dims[2]) return false;
+      g = (size_t)line * dims[0] + pt;
+    } else {
+      const int i = i0 + l;
+      if (i >= dims[0]) return false;
+      int j, k;
+      if (a == 1) { j = pt; k = outer; } else { j = outer; k = pt; }
+      g = ((size_t)k * dims[1] + j) * dims[0] + i;
+    }
+    return true;
+  };
+  for (int e = threadIdx.x; e < kTileL * nc; e += blockDim.x) {
+    int l, pt;
+    if (a == 0) { l = e / nc; pt = e - l * nc; } else { pt = e / kTileL; l = e - pt * kTileL; }
+    size_t g;
+    X[l * ldx + pt] = gidx(dims_in, l, pt, g) ? in[g] : (T)0;
+  }
+  __syncthreads();
+  {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* xa = X + (2 * w) * ldx;
+    T* xb = X + (2 * w + 1) * ldx;
+    C* buf = Cb + (size_t)w * PF;
+    // coarse DCT-I with the length-PC FFT (twiddle stride 2 in the fine table:
+    // exp(-2 pi i t / PC) = exp(-2 pi i 2t / PF)); use a compacted copy in buf's tail
+    C* twc_s = buf + PC;  // PC entries, free until the fine FFT
+    for (int t = lane; t < PC; t += 32) twc_s[t] = tw[2 * t];
+    for (int j = lane; j < PC; j += 32) {
+      const int jj = j <= NC ? j : PC - j;
+      C v; v.x = xa[jj]; v.y = xb[jj];
+      buf[j] = v;
+    }
+    __syncwarp();
+    warp_fft<T, PC>(buf, twc_s, lane);
+    // beta_k = F_k / (2 NC) for k < NC, F_NC / (4 NC); zero for k > NC
+    const T s = (T)1 / (T)(2 * NC);
+    for (int k = lane; k <= NF; k += 32) {
+      T ba = 0, bb = 0;
+      if (k <= NC) {
+        const C F = buf[k];
+        const T wk = (k == NC) ? (T)0.5 * s : s;
+        ba = wk * F.x;
+        bb = wk * F.y;
+      }
+      xa[k] = ba;
+      xb[k] = bb;
+    }
+    __syncwarp();
+    for (int j = lane; j < PF; j += 32) {
+      const int jj = j <= NF ? j : PF - j;
+      C v; v.x = xa[jj]; v.y = xb[jj];
+      buf[j] = v;
+    }
+    __syncwarp();
+    warp_fft<T, PF>(buf, tw, lane);
+    for (int k = lane; k <= NF; k += 32) {
+      const C F = buf[k];
+      xa[k] = F.x;
+      xb[k] = F.y;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kTileL * nf; e += blockDim.x) {
+    int l, pt;
+    if (a == 0) { l = e / nf; pt = e - l * nf; } else { pt = e / kTileL; l = e - pt * kTileL; }
+    size_t g;
+    if (gidx(dims_out, l, pt, g)) out[g] = X[l * ldx + pt];
+  }
+}
+
+template <typename T, int PC>
+static int launch_prolong_pass(int a, const int dims[3], const typename C2<T>::t* twf, const T* in,
+                               T* out, cudaStream_t s) {
+  auto kern = prolong_pass_kernel<T, PC>;
+  const size_t smem = prolong_smem<T>(PC / 2 + 1, PC);
+  static size_t configured = 0;
+  if (smem > configured) {
+    CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = smem;
+  }
+  int nblocks;
+  if (a == 0) nblocks = (dims[1] * dims[2] + kTileL - 1) / kTileL;
+  else nblocks = ((dims[0] + kTileL - 1) / kTileL) * (a == 1 ? dims[2] : dims[1]);
+  kern<<<nblocks, kThreads, smem, s>>>(a, dims[0], dims[1], dims[2], nullptr, twf, in, out);
+  CHEB_LAUNCH_CHECK("prolong_pass_kernel");
+  return CHEB_OK;
+}
+
+template <typename T> static const typename C2<T>::t* twf_of(const AxisTables& t);
+template <> const double2* twf_of<double>(const AxisTables& t) { return t.tw64; }
+template <> const float2* twf_of<float>(const AxisTables& t) { return t.tw32; }
+
+template <typename T>
+static int prolong_pass(int a, int PC, const int dims[3], const typename C2<T>::t* twf, const T* in,
+                        T* out, cudaStream_t s) {
+  switch (PC) {
+    case 8: return launch_prolong_pass<T, 8>(a, dims, twf, in, out, s);
+    case 16: return launch_prolong_pass<T, 16>(a, dims, twf, in, out, s);
+    case 32: return launch_prolong_pass<T, 32>(a, dims, twf, in, out, s);
+    case 64: return launch_prolong_pass<T, 64>(a, dims, twf, in, out, s);
+    case 128: return launch_prolong_pass<T, 128>(a, dims, twf, in, out, s);
+    case 256: return launch_prolong_pass<T, 256>(a, dims, twf, in, out, s);
+    case 512: return launch_prolong_pass<T, 512>(a, dims, twf, in, out, s);
+    default:
+      set_error("prolongation needs coarse N a power of two in [4, 256]");
+      return CHEB_ERR_UNSUPPORTED;
+  }
+}
+
+int check_prolong_pair(const cheb_plan_s* c, const cheb_plan_s* f) {
+  if (!c || !f || c->dim != f->dim) { set_error("plans must have the same dimension"); return CHEB_ERR_ARG; }
+  for (int a = 0; a < c->dim; ++a) {
+    if (f->n[a] - 1 != 2 * (c->n[a] - 1)) { set_error("fine N must be twice the coarse N"); return CHEB_ERR_ARG; }
+    if (c->lo[a] != f->lo[a] || c->hi[a] != f->hi[a]) { set_error("plans must share the box"); return CHEB_ERR_ARG; }
+    if (!f->ax[a].transform_ok || !c->ax[a].transform_ok) {
+      set_error("prolongation needs coarse and fine N powers of two (4 <= N, fine N <= 512)");
+      return CHEB_ERR_UNSUPPORTED;
+    }
+  }
+  return CHEB_OK;
+}
+
+template <typename T>
+int launch_prolong(const cheb_plan_s* c, const cheb_plan_s* f, const T* uc, T* uf, T* s1, T* s2,
+                   cudaStream_t s) {
+  int dims[3] = {c->n[0], c->n[1], c->n[2]};
+  const T* src = uc;
+  int st;
+  for (int a = 0; a < c->dim; ++a) {
+    T* dst = (a == c->dim - 1) ? uf : (a % 2 == 0 ? s1 : s2);
+    if ((st = prolong_pass<T>(a, 2 * (c->n[a] - 1), dims, twf_of<T>(f->ax[a]), src, dst, s))) return st;
+    dims[a] = f->n[a];
+    src = dst;
+  }
+  return CHEB_OK;
+}
+
+template int launch_prolong<double>(const cheb_plan_s*, const cheb_plan_s*, const double*, double*, double*, double*, cudaStream_t);
+template int launch_prolong<float>(const cheb_plan_s*, const cheb_plan_s*, const float*, float*, float*, float*, cudaStream_t);
+
+}  // namespace cheb

@@ -1,15 +1,559 @@
-// Krylov workspace and solver drivers.
-#include "internal.h"
+// Solver drivers: LGMRES(m, k) on the left-preconditioned collocation system
+// (the Krylov solver named in Alg. 2; Baker, Jessup & Manteuffel 2005: m new
+// Krylov directions plus k error-approximation vectors carried between
+// restart cycles), and the mixed-precision form: FP32 inner LGMRES cycles
+// inside an FP64 iterative-refinement loop.
+//
+// Arnoldi step j (classical Gram-Schmidt, optionally twice):
+//   w = M^{-1} A v_j           (line passes + preconditioner)
+//   h = V_j^T w                (one fused multi-dot kernel, deterministic)
+//   w -= V_j h, ||w||          (one fused multi-axpy kernel with the norm)
+//   v_{j+1} = w / ||w||
+// The Hessenberg least-squares problem (Givens rotations) is solved on the
+// host in FP64 after one stream synchronisation per step.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fdm.h"
+#include "krylov.h"
+#include "prolong.h"
 
 namespace cheb {
 
-struct Workspace {
-  int dummy = 0;
+template <typename T>
+struct KrylovBufs {
+  int nvec = 0;        // allocated basis vectors
+  int kaug = 0;        // allocated augmentation pairs
+  T* V = nullptr;      // nvec x n
+  T* Z = nullptr;      // kaug x n  (error approximations)
+  T* BZ = nullptr;     // kaug x n  (M^{-1} A z)
+  T* tmp = nullptr;    // n
+  T* x = nullptr;      // n (inner solution)
+  T* c = nullptr;      // n (inner right-hand side)
+  T* K = nullptr;      // n (conductivity in this precision)
 };
 
+struct Workspace {
+  size_t n = 0;
+  ReduceScratch rs;
+  double* dscal = nullptr;    // device scalars (dots, norms): kMaxVecs + 8
+  double* hscal = nullptr;    // pinned host mirror
+  KrylovBufs<double> k64;
+  KrylovBufs<float> k32;
+  double* r64 = nullptr;      // FP64 residual
+  double* pro[3] = {nullptr, nullptr, nullptr};  // prolongation scratch (2) + prolonged copy
+  Fdm fdm;
+};
+
+template <typename T> static KrylovBufs<T>& bufs(Workspace& w);
+template <> KrylovBufs<double>& bufs<double>(Workspace& w) { return w.k64; }
+template <> KrylovBufs<float>& bufs<float>(Workspace& w) { return w.k32; }
+
+template <typename T>
+static void free_bufs(KrylovBufs<T>& b) {
+  cudaFree(b.V); cudaFree(b.Z); cudaFree(b.BZ); cudaFree(b.tmp); cudaFree(b.x); cudaFree(b.c); cudaFree(b.K);
+  b = KrylovBufs<T>();
+}
+
 void free_workspace(cheb_plan_s* p) {
-  delete p->ws;
+  if (!p->ws) return;
+  Workspace* w = p->ws;
+  cudaFree(w->rs.part); cudaFree(w->rs.counter); cudaFree(w->dscal); cudaFreeHost(w->hscal);
+  free_bufs(w->k64); free_bufs(w->k32);
+  cudaFree(w->r64);
+  for (int i = 0; i < 3; ++i) cudaFree(w->pro[i]);
+  fdm_free(w->fdm);
+  delete w;
   p->ws = nullptr;
 }
 
+static int ensure_ws(cheb_plan_s* p) {
+  if (p->ws) return CHEB_OK;
+  Workspace* w = new Workspace();
+  p->ws = w;
+  w->n = p->size();
+  CHEB_CUDA(cudaMalloc(&w->rs.part, sizeof(double) * (kMaxVecs + 1) * kRedBlocks));
+  CHEB_CUDA(cudaMalloc(&w->rs.counter, sizeof(unsigned)));
+  CHEB_CUDA(cudaMemset(w->rs.counter, 0, sizeof(unsigned)));
+  CHEB_CUDA(cudaMalloc(&w->dscal, sizeof(double) * (kMaxVecs + 8)));
+  CHEB_CUDA(cudaMallocHost(&w->hscal, sizeof(double) * (kMaxVecs + 8)));
+  return CHEB_OK;
+}
+
+template <typename T>
+static int ensure_bufs(Workspace& w, int nvec, int kaug) {
+  KrylovBufs<T>& b = bufs<T>(w);
+  const size_t n = w.n;
+  if (b.nvec < nvec) {
+    cudaFree(b.V);
+    b.V = nullptr;
+    CHEB_CUDA(cudaMalloc(&b.V, sizeof(T) * n * nvec));
+    b.nvec = nvec;
+  }
+  if (b.kaug < kaug) {
+    cudaFree(b.Z); cudaFree(b.BZ);
+    b.Z = b.BZ = nullptr;
+    CHEB_CUDA(cudaMalloc(&b.Z, sizeof(T) * n * kaug));
+    CHEB_CUDA(cudaMalloc(&b.BZ, sizeof(T) * n * kaug));
+    b.kaug = kaug;
+  }
+  if (!b.tmp) {
+    CHEB_CUDA(cudaMalloc(&b.tmp, sizeof(T) * n));
+    CHEB_CUDA(cudaMalloc(&b.x, sizeof(T) * n));
+    CHEB_CUDA(cudaMalloc(&b.c, sizeof(T) * n));
+    CHEB_CUDA(cudaMalloc(&b.K, sizeof(T) * n));
+  }
+  return CHEB_OK;
+}
+
+static int sync_read(Workspace& w, int cnt, cudaStream_t s) {
+  CHEB_CUDA(cudaMemcpyAsync(w.hscal, w.dscal, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s));
+  CHEB_CUDA(cudaStreamSynchronize(s));
+  return CHEB_OK;
+}
+
+// Settings of one LGMRES run.
+struct LgOpts {
+  int m = 30, k = 3, maxiter = 1000;
+  bool reorth = false;
+  int precond = CHEB_PRECOND_FDM;
+  double kref = 1.0;
+  double tol_abs = 0.0;  // stop when ||c - B x|| <= tol_abs
+};
+
+struct LgStats {
+  int iterations = 0, cycles = 0, applies = 0;
+  double resid = 0.0;  // last true preconditioned residual norm
+  bool converged = false;
+};
+
+// out = B v = M^{-1} A v (tmp holds A v)
+template <typename T> struct Cat;
+template <> struct Cat<double> { static constexpr int apply = kProfApply64, prec = kProfPrec64, orth = kProfOrth64; };
+template <> struct Cat<float> { static constexpr int apply = kProfApply32, prec = kProfPrec32, orth = kProfOrth32; };
+
+template <typename T>
+static int op_B(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, const T* v, T* out, T* tmp,
+                cudaStream_t s) {
+  int st;
+  prof_begin(Cat<T>::apply, s);
+  st = launch_apply<T>(p, K, v, o.precond == CHEB_PRECOND_FDM ? tmp : out, s);
+  prof_end(Cat<T>::apply, s);
+  if (st || o.precond != CHEB_PRECOND_FDM) return st;
+  prof_begin(Cat<T>::prec, s);
+  st = fdm_apply<T>(p, w.fdm, o.kref, tmp, out, s);
+  prof_end(Cat<T>::prec, s);
+  return st;
+}
+
+// LGMRES on B x = c (B = M^{-1} A), x in/out.  Returns CHEB_OK when
+// converged, CHEB_ERR_NOT_CONVERGED at maxiter, or an error.
+template <typename T>
+static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, const T* c, T* x,
+                  bool x_is_zero, LgStats& stt, cudaStream_t s) {
+  const size_t n = w.n;
+  const int m = o.m, kk = o.k;
+  const int nbasis = m + kk + 1;
+  int st;
+  if ((st = ensure_bufs<T>(w, nbasis, std::max(1, kk)))) return st;
+  KrylovBufs<T>& B = bufs<T>(w);
+  auto Vp = [&](int i) { return B.V + (size_t)i * n; };
+  auto Zp = [&](int i) { return B.Z + (size_t)i * n; };
+  auto BZp = [&](int i) { return B.BZ + (size_t)i * n; };
+  int naug = 0, next_slot = 0;
+  std::vector<double> H((size_t)(nbasis + 1) * nbasis), Hr((size_t)(nbasis + 1) * nbasis);
+  std::vector<double> cs(nbasis), sn(nbasis), g(nbasis + 1), y(nbasis);
+  double* dv = w.dscal;
+  double* hv = w.hscal;
+  bool zero = x_is_zero;
+  stt = LgStats();
+  while (true) {
+    // ---- residual r = c - B x into V[0]
+    if (zero) {
+      if ((st = k_scale<T>(Vp(0), c, 1.0, n, s))) return st;
+    } else {
+      if ((st = op_B<T>(p, w, o, K, x, Vp(0), B.tmp, s))) return st;
+      stt.applies++;
+      if ((st = k_residual<T>(Vp(0), c, n, s))) return st;
+    }
+    const T* v0 = Vp(0);
+    if ((st = k_mdot<T>(w.rs, &v0, 0, Vp(0), n, true, dv, s))) return st;
+    if ((st = sync_read(w, 1, s))) return st;
+    const double beta = std::sqrt(hv[0]);
+    stt.resid = beta;
+    if (!std::isfinite(beta)) { set_error("non-finite residual"); return CHEB_ERR_NONFINITE; }
+    if (beta <= o.tol_abs) { stt.converged = true; return CHEB_OK; }
+    if (stt.iterations >= o.maxiter) return CHEB_ERR_NOT_CONVERGED;
+    if ((st = k_scale<T>(Vp(0), Vp(0), 1.0 / beta, n, s))) return st;
+    stt.cycles++;
+    // ---- Arnoldi: first m_eff Krylov directions, then the augmentation vectors
+    const int m_eff = m + (kk - naug);
+    const int steps_max = m_eff + naug;
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int steps = 0;
+    for (int j = 0; j < steps_max; ++j) {
+      T* wv = Vp(j + 1);
+      if (j < m_eff) {
+        if ((st = op_B<T>(p, w, o, K, Vp(j), wv, B.tmp, s))) return st;
+        stt.applies++;
+      } else {
+        const int a = (next_slot - naug + (j - m_eff) + 4 * kk) % kk;  // oldest first
+        if ((st = k_scale<T>(wv, BZp(a), 1.0, n, s))) return st;
+      }
+      const T* src[kMaxVecs];
+      for (int i = 0; i <= j; ++i) src[i] = Vp(i);
+      // classical Gram-Schmidt (twice if requested): h = V^T w, w -= V h, |w|^2;
+      // the axpy reads h on the device, one synchronisation per pass
+      for (int pass = 0; pass < (o.reorth ? 2 : 1); ++pass) {
+        prof_begin(Cat<T>::orth, s);
+        if ((st = k_mdot<T>(w.rs, src, j + 1, wv, n, false, dv, s))) return st;
+        if ((st = k_maxpy_dev<T>(w.rs, src, dv, -1.0, j + 1, 1.0, wv, n, dv + kMaxVecs + 1, s))) return st;
+        prof_end(Cat<T>::orth, s);
+        if ((st = sync_read(w, kMaxVecs + 2, s))) return st;
+        for (int i = 0; i <= j; ++i) {
+          if (pass == 0) H[(size_t)i * nbasis + j] = hv[i];
+          else H[(size_t)i * nbasis + j] += hv[i];
+        }
+      }
+      const double hn = std::sqrt(std::max(0.0, hv[kMaxVecs + 1]));
+      if (!std::isfinite(hn)) { set_error("non-finite Arnoldi norm"); return CHEB_ERR_NONFINITE; }
+      H[(size_t)(j + 1) * nbasis + j] = hn;
+      if (hn > 0) {
+        if ((st = k_scale_inv_norm<T>(wv, dv + kMaxVecs + 1, n, s))) return st;
+      }
+      // Givens: copy the column, apply previous rotations, make a new one
+      for (int i = 0; i <= j + 1; ++i) Hr[(size_t)i * nbasis + j] = H[(size_t)i * nbasis + j];
+      for (int i = 0; i < j; ++i) {
+        const double a = Hr[(size_t)i * nbasis + j], b = Hr[(size_t)(i + 1) * nbasis + j];
+        Hr[(size_t)i * nbasis + j] = cs[i] * a + sn[i] * b;
+        Hr[(size_t)(i + 1) * nbasis + j] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = Hr[(size_t)j * nbasis + j], b = Hr[(size_t)(j + 1) * nbasis + j];
+      const double den = std::hypot(a, b);
+      cs[j] = den > 0 ? a / den : 1.0;
+      sn[j] = den > 0 ? b / den : 0.0;
+      Hr[(size_t)j * nbasis + j] = den;
+      Hr[(size_t)(j + 1) * nbasis + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      steps = j + 1;
+      stt.iterations++;
+      if (std::fabs(g[j + 1]) <= o.tol_abs || hn == 0.0 || stt.iterations >= o.maxiter) break;
+    }
+    // ---- least squares: R y = g
+    for (int i = steps - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int l = i + 1; l < steps; ++l) t -= Hr[(size_t)i * nbasis + l] * y[l];
+      y[i] = Hr[(size_t)i * nbasis + i] != 0.0 ? t / Hr[(size_t)i * nbasis + i] : 0.0;
+    }
+    // ---- dx = W y into tmp (with its norm), x += dx
+    {
+      const T* src[kMaxVecs];
+      double coef[kMaxVecs];
+      for (int i = 0; i < steps; ++i) {
+        if (i < m_eff) src[i] = Vp(i);
+        else src[i] = Zp((next_slot - naug + (i - m_eff) + 4 * kk) % kk);
+        coef[i] = y[i];
+      }
+      if ((st = k_maxpy<T>(w.rs, src, coef, steps, 0.0, B.tmp, n, dv + kMaxVecs + 1, s))) return st;
+      const T* one[1] = {B.tmp};
+      double cone[1] = {1.0};
+      if (zero) {
+        if ((st = k_scale<T>(x, B.tmp, 1.0, n, s))) return st;
+      } else {
+        if ((st = k_maxpy<T>(w.rs, one, cone, 1, 1.0, x, n, nullptr, s))) return st;
+      }
+      zero = false;
+      if (kk > 0) {
+        if ((st = sync_read(w, kMaxVecs + 2, s))) return st;
+        const double dxn = std::sqrt(std::max(0.0, hv[kMaxVecs + 1]));
+        if (dxn > 0) {
+          // store z = dx/|dx| and B z = V Hbar y / |dx| (linearity: B W = V Hbar)
+          const int slot = next_slot;
+          if ((st = k_scale<T>(Zp(slot), B.tmp, 1.0 / dxn, n, s))) return st;
+          double hy[kMaxVecs];
+          const T* vs[kMaxVecs];
+          for (int i = 0; i <= steps; ++i) {
+            double t = 0.0;
+            for (int l = 0; l < steps; ++l)
+              if (i <= l + 1) t += H[(size_t)i * nbasis + l] * y[l];
+            hy[i] = t / dxn;
+            vs[i] = Vp(i);
+          }
+          if ((st = k_maxpy<T>(w.rs, vs, hy, steps + 1, 0.0, BZp(slot), n, nullptr, s))) return st;
+          next_slot = (next_slot + 1) % kk;
+          naug = std::min(naug + 1, kk);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// drivers
+// ---------------------------------------------------------------------------
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void default_opts(cheb_solve_opts& o) {
+  std::memset(&o, 0, sizeof(o));
+  o.mode = CHEB_SOLVE_MIXED;
+  o.rtol = 1e-12;
+  o.restart = 30;
+  o.augment = 3;
+  o.maxiter = 2000;
+  o.inner_rtol = 1e-5;
+  o.inner_maxiter = 400;
+  o.max_refinements = 30;
+  o.reorth = 0;
+  o.precond = CHEB_PRECOND_FDM;
+  o.kref = 0.0;
+}
+
+static double norm2_dev(Workspace& w, const double* x, cudaStream_t s, int* st) {
+  const double* src[1] = {x};
+  *st = k_mdot<double>(w.rs, src, 0, x, w.n, true, w.dscal, s);
+  if (*st) return 0;
+  *st = sync_read(w, 1, s);
+  return std::sqrt(w.hscal[0]);
+}
+
+template <typename T>
+static double norm2_t(Workspace& w, const T* x, cudaStream_t s, int* st) {
+  const T* src[1] = {x};
+  *st = k_mdot<T>(w.rs, src, 0, x, w.n, true, w.dscal, s);
+  if (*st) return 0;
+  *st = sync_read(w, 1, s);
+  return std::sqrt(w.hscal[0]);
+}
+
+static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* u,
+                      const cheb_solve_opts& o, cheb_solve_info& info) {
+  const double t0 = now_s();
+  cudaStream_t s = p->stream;
+  int st;
+  bool has_dir = false;
+  for (int f = 0; f < 2 * p->dim; ++f) has_dir |= p->bc[f] == CHEB_DIRICHLET;
+  if (!has_dir) { set_error("every face is Neumann: the system is singular"); return CHEB_ERR_SINGULAR_BC; }
+  if (o.restart < 1 || o.augment < 0 || o.restart + o.augment + 1 > kMaxVecs) {
+    set_error("need restart >= 1, augment >= 0, restart + augment < 40"); return CHEB_ERR_ARG;
+  }
+  if ((st = ensure_ws(p))) return st;
+  Workspace& w = *p->ws;
+  const size_t n = w.n;
+  LgOpts lo;
+  lo.m = o.restart;
+  lo.k = o.augment;
+  lo.reorth = o.reorth != 0;
+  lo.precond = o.precond;
+  if (o.precond == CHEB_PRECOND_FDM) {
+    if ((st = fdm_setup(p, w.fdm))) return st;
+    if (o.kref > 0) lo.kref = o.kref;
+    else {
+      if ((st = k_sum_log(w.rs, K, n, w.dscal, s))) return st;
+      if ((st = sync_read(w, 1, s))) return st;
+      lo.kref = std::exp(w.hscal[0] / (double)n);
+    }
+  }
+  info.kref = lo.kref;
+  // ||M^{-1} b||
+  double nb;
+  if (o.mode == CHEB_SOLVE_FP64) {
+    if ((st = ensure_bufs<double>(w, lo.m + lo.k + 1, std::max(1, lo.k)))) return st;
+    KrylovBufs<double>& B = w.k64;
+    if (o.precond == CHEB_PRECOND_FDM) {
+      if ((st = fdm_apply<double>(p, w.fdm, lo.kref, b, B.c, s))) return st;
+    } else if ((st = k_scale<double>(B.c, b, 1.0, n, s))) return st;
+    nb = norm2_dev(w, B.c, s, &st);
+    if (st) return st;
+    if (nb == 0.0) {
+      CHEB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
+      CHEB_CUDA(cudaStreamSynchronize(s));
+      info.status = CHEB_OK;
+      return CHEB_OK;
+    }
+    lo.tol_abs = std::max(o.rtol * nb, o.atol);
+    lo.maxiter = o.maxiter;
+    LgStats stt;
+    int rc = lgmres<double>(p, w, lo, K, B.c, u, false, stt, s);
+    info.iterations = stt.iterations;
+    info.cycles = stt.cycles;
+    info.applies_fp64 = stt.applies;
+    info.rel_residual = stt.resid / nb;
+    info.seconds = now_s() - t0;
+    info.status = rc;
+    return rc;
+  }
+  // ---- mixed: FP32 inner LGMRES inside FP64 iterative refinement
+  if ((st = ensure_bufs<float>(w, lo.m + lo.k + 1, std::max(1, lo.k)))) return st;
+  KrylovBufs<float>& B = w.k32;
+  if (!w.r64) CHEB_CUDA(cudaMalloc(&w.r64, sizeof(double) * n));
+  if ((st = k_cast_scale<float, double>(B.K, K, 1.0, n, s))) return st;
+  {
+    const double sb = norm2_dev(w, b, s, &st);
+    if (st) return st;
+    if (sb == 0.0) {
+      CHEB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
+      CHEB_CUDA(cudaStreamSynchronize(s));
+      info.status = CHEB_OK;
+      return CHEB_OK;
+    }
+    if ((st = k_cast_scale<float, double>(B.tmp, b, 1.0 / sb, n, s))) return st;
+    if (o.precond == CHEB_PRECOND_FDM) {
+      if ((st = fdm_apply<float>(p, w.fdm, lo.kref, B.tmp, B.c, s))) return st;
+    } else if ((st = k_scale<float>(B.c, B.tmp, 1.0, n, s))) return st;
+    nb = sb * norm2_t<float>(w, B.c, s, &st);
+    if (st) return st;
+  }
+  int rc = CHEB_ERR_NOT_CONVERGED;
+  double eta = 1.0;
+  for (int it = 0; it <= o.max_refinements; ++it) {
+    // r64 = b - A u (FP64)
+    if ((st = launch_apply<double>(p, K, u, w.r64, s))) return st;
+    info.applies_fp64++;
+    if ((st = k_residual<double>(w.r64, b, n, s))) return st;
+    const double sr = norm2_dev(w, w.r64, s, &st);
+    if (st) return st;
+    if (!std::isfinite(sr)) { set_error("non-finite residual"); return CHEB_ERR_NONFINITE; }
+    if (sr == 0.0) { eta = 0.0; rc = CHEB_OK; break; }
+    if ((st = k_cast_scale<float, double>(B.tmp, w.r64, 1.0 / sr, n, s))) return st;
+    if (o.precond == CHEB_PRECOND_FDM) {
+      if ((st = fdm_apply<float>(p, w.fdm, lo.kref, B.tmp, B.c, s))) return st;
+    } else if ((st = k_scale<float>(B.c, B.tmp, 1.0, n, s))) return st;
+    const double cn = norm2_t<float>(w, B.c, s, &st);
+    if (st) return st;
+    eta = sr * cn / nb;
+    if (o.verbose) fprintf(stderr, "[cheb] refinement %d: eta = %.3e\n", it, eta);
+    if (eta <= o.rtol || sr * cn <= o.atol) { rc = CHEB_OK; break; }
+    if (it == o.max_refinements || info.iterations >= o.maxiter) break;
+    LgOpts li = lo;
+    li.tol_abs = o.inner_rtol * cn;
+    li.maxiter = std::min(o.inner_maxiter, o.maxiter - info.iterations);
+    LgStats stt;
+    int r2 = lgmres<float>(p, w, li, B.K, B.c, B.x, true, stt, s);
+    if (r2 < 0) return r2;
+    info.iterations += stt.iterations;
+    info.cycles += stt.cycles;
+    info.applies_fp32 += stt.applies;
+    info.refinements++;
+    info.rel_residual_inner = stt.resid / cn;
+    if ((st = k_axpy64<float>(u, B.x, sr, n, s))) return st;
+  }
+  CHEB_CUDA(cudaStreamSynchronize(s));
+  info.rel_residual = eta;
+  info.seconds = now_s() - t0;
+  info.status = rc;
+  return rc;
+}
+
 }  // namespace cheb
+
+using namespace cheb;
+
+extern "C" {
+
+void cheb_solve_opts_default(cheb_solve_opts* o) {
+  if (o) default_opts(*o);
+}
+
+int cheb_solve(cheb_plan p, const double* K, const double* b, double* u, const cheb_solve_opts* opts,
+               cheb_solve_info* info) {
+  if (!p || !K || !b || !u) { set_error("null argument"); return CHEB_ERR_ARG; }
+  cheb_solve_opts o;
+  if (opts) o = *opts;
+  else default_opts(o);
+  if (o.mode != CHEB_SOLVE_FP64 && o.mode != CHEB_SOLVE_MIXED) { set_error("bad mode"); return CHEB_ERR_ARG; }
+  if (o.precond != CHEB_PRECOND_NONE && o.precond != CHEB_PRECOND_FDM) {
+    set_error("bad preconditioner"); return CHEB_ERR_ARG;
+  }
+  cheb_solve_info tmp;
+  std::memset(&tmp, 0, sizeof(tmp));
+  int rc = solve_impl(p, K, b, u, o, tmp);
+  if (info) *info = tmp;
+  return rc;
+}
+
+int cheb_prolong(cheb_plan coarse, cheb_plan fine, int prec, const void* uc, void* uf) {
+  if (!uc || !uf) { set_error("null argument"); return CHEB_ERR_ARG; }
+  int st;
+  if ((st = check_prolong_pair(coarse, fine))) return st;
+  if ((st = ensure_ws(fine))) return st;
+  Workspace& w = *fine->ws;
+  if (!w.pro[0]) {
+    CHEB_CUDA(cudaMalloc(&w.pro[0], sizeof(double) * (w.n / 2 + 1)));
+    CHEB_CUDA(cudaMalloc(&w.pro[1], sizeof(double) * (w.n / 2 + 1)));
+  }
+  if (prec == CHEB_FP64) {
+    prof_begin(kProfProlong, fine->stream);
+    st = launch_prolong<double>(coarse, fine, (const double*)uc, (double*)uf, w.pro[0], w.pro[1],
+                                fine->stream);
+    prof_end(kProfProlong, fine->stream);
+    return st;
+  }
+  if (prec == CHEB_FP32)
+    return launch_prolong<float>(coarse, fine, (const float*)uc, (float*)uf, (float*)w.pro[0],
+                                 (float*)w.pro[1], fine->stream);
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+int cheb_rel_diff(cheb_plan p, const double* a, const double* b, double* out) {
+  if (!p || !a || !b || !out) { set_error("null argument"); return CHEB_ERR_ARG; }
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  Workspace& w = *p->ws;
+  const double* src[1] = {b};
+  // |a|^2, <a, b>, |b|^2 -> |a - b|^2 = |a|^2 - 2<a,b> + |b|^2 loses digits; use a difference vector
+  if (!w.r64) CHEB_CUDA(cudaMalloc(&w.r64, sizeof(double) * w.n));
+  const double* one[1] = {a};
+  double cf[2] = {1.0, -1.0};
+  const double* two[2] = {a, b};
+  if ((st = k_maxpy<double>(w.rs, two, cf, 2, 0.0, w.r64, w.n, w.dscal + 1, p->stream))) return st;
+  if ((st = k_mdot<double>(w.rs, one, 0, a, w.n, true, w.dscal, p->stream))) return st;
+  (void)src;
+  if ((st = sync_read(w, 2, p->stream))) return st;
+  *out = w.hscal[0] > 0 ? std::sqrt(w.hscal[1] / w.hscal[0]) : 0.0;
+  return CHEB_OK;
+}
+
+int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const* K,
+                         const double* const* b, double* const* u, const cheb_solve_opts* opts,
+                         cheb_solve_info* infos, double* e_ref) {
+  if (levels < 1 || !plans || !K || !b || !u) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  int rc = CHEB_OK, st;
+  for (int l = 0; l < levels; ++l) {
+    cheb_plan p = plans[l];
+    if (l > 0) {
+      if ((st = cheb_prolong(plans[l - 1], p, CHEB_FP64, u[l - 1], u[l]))) return st;
+      Workspace& w = *p->ws;
+      if (!w.pro[2]) CHEB_CUDA(cudaMalloc(&w.pro[2], sizeof(double) * w.n));
+      CHEB_CUDA(cudaMemcpyAsync(w.pro[2], u[l], sizeof(double) * w.n, cudaMemcpyDeviceToDevice, p->stream));
+    }
+    cheb_solve_info info;
+    rc = cheb_solve(p, K[l], b[l], u[l], opts, &info);
+    if (infos) infos[l] = info;
+    if (rc < 0) return rc;
+    if (e_ref) {
+      e_ref[l] = 0.0;
+      if (l > 0 && (st = cheb_rel_diff(p, u[l], p->ws->pro[2], &e_ref[l]))) return st;
+    }
+  }
+  return rc;
+}
+
+int cheb_precond_apply(cheb_plan p, int prec, double kref, const void* r, void* z) {
+  if (!p || !r || !z || !(kref > 0)) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  if ((st = fdm_setup(p, p->ws->fdm))) return st;
+  if (prec == CHEB_FP64) return fdm_apply<double>(p, p->ws->fdm, kref, (const double*)r, (double*)z, p->stream);
+  if (prec == CHEB_FP32) return fdm_apply<float>(p, p->ws->fdm, kref, (const float*)r, (float*)z, p->stream);
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+}  // extern "C"

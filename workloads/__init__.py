@@ -210,10 +210,26 @@ def sphere_packing(seed: int = 0, rmin: float = 0.08, rmax: float = 0.15,
 
 
 def two_phase_conductivity(X, Y, Z, spheres: np.ndarray, k_matrix: float, k_incl: float) -> np.ndarray:
-    """k = k_incl at points inside (inclusive) any sphere, else k_matrix."""
+    """k = k_incl at points inside (inclusive) any sphere, else k_matrix.
+
+    X, Y, Z are (nz, ny, nx) tensor-grid coordinates; each sphere is tested
+    only on the sub-block of grid lines that its bounding box covers."""
+    x, y, z = X[0, 0, :], Y[0, :, 0], Z[:, 0, 0]
     inside = np.zeros(X.shape, dtype=bool)
+
+    def span(c, r, t):
+        idx = np.nonzero((t >= c - r) & (t <= c + r))[0]
+        return (idx.min(), idx.max() + 1) if idx.size else (0, 0)
+
     for cx, cy, cz, r in spheres:
-        inside |= (X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2 <= r * r
+        i0, i1 = span(cx, r, x)
+        j0, j1 = span(cy, r, y)
+        k0, k1 = span(cz, r, z)
+        if i1 <= i0 or j1 <= j0 or k1 <= k0:
+            continue
+        d2 = ((x[i0:i1] - cx) ** 2)[None, None, :] + ((y[j0:j1] - cy) ** 2)[None, :, None] \
+            + ((z[k0:k1] - cz) ** 2)[:, None, None]
+        inside[k0:k1, j0:j1, i0:i1] |= d2 <= r * r
     return np.where(inside, k_incl, k_matrix).astype(float)
 
 
