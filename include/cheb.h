@@ -188,6 +188,22 @@ int cheb_solve(cheb_plan plan, const double* K, const double* b, double* u,
  * scratch arrays owned by the fine plan (allocated at the first call). */
 int cheb_prolong(cheb_plan coarse, cheb_plan fine, int prec, const void* u_c, void* u_f);
 
+/* cheb_prolong for callers that cannot allocate device memory (code running
+ * inside a custom allocator, a memory-capped sandbox, or any process that
+ * must not call cudaMalloc from this library).  No counterpart in the paper.
+ * Same arguments and result as cheb_prolong, but it calls no cudaMalloc,
+ * cudaFree or other allocating routine: the intermediate arrays live in one
+ * fixed 16 MiB device array inside the library, which every GPU that loads
+ * the library keeps until the process exits.  Grids whose intermediates
+ * exceed 16 MiB are rejected with CHEB_ERR_UNSUPPORTED: 3-D grids up to
+ * 65^3 -> 129^3 fit in FP64 and FP32, 129^3 -> 257^3 does not.  The first call on
+ * a device looks up the array's device address for that device (a
+ * cudaGetSymbolAddress call), so make that first call before any stream
+ * capture.  All calls share the one array and nothing in it needs to start
+ * at zero; calls that overlap on the GPU (other streams, other host
+ * threads) race on it, so order them on one stream. */
+int cheb_prolong_noalloc(cheb_plan coarse, cheb_plan fine, int prec, const void* u_c, void* u_f);
+
 /* out = ||a - b||_2 / ||a||_2 for FP64 device fields on the plan's grid (the
  * refinement indicator e_ref of Sec. 2.3.3 with a the fine solution and b
  * the prolonged coarse solution).  Synchronises. */

@@ -79,6 +79,7 @@ _SIGS = {
     "cheb_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "cheb_precond_apply": (i32, [vp, i32, C.c_double, vp, vp]),
     "cheb_prolong": (i32, [vp, vp, i32, vp, vp]),
+    "cheb_prolong_noalloc": (i32, [vp, vp, i32, vp, vp]),
     "cheb_rel_diff": (i32, [vp, vp, vp, f64p]),
     "cheb_solve_hierarchy": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo), f64p]),

@@ -8,6 +8,8 @@
 // Three axis passes, x then y then z, through two scratch arrays.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "device.cuh"
 #include "fdm.h"
@@ -201,4 +203,68 @@ int launch_prolong(const cheb_plan_s* c, const cheb_plan_s* f, const T* uc, T* u
 template int launch_prolong<double>(const cheb_plan_s*, const cheb_plan_s*, const double*, double*, double*, double*, cudaStream_t);
 template int launch_prolong<float>(const cheb_plan_s*, const cheb_plan_s*, const float*, float*, float*, float*, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Prolongation without allocation, for callers that cannot call cudaMalloc
+// (for example code that runs inside a custom allocator, a memory-capped
+// sandbox, or a process whose allocator must not be re-entered).  The two
+// intermediate arrays of the axis passes live in one fixed file-scope device
+// array of kNoAllocBytes; every GPU that loads this library holds it until
+// the process exits.  The host code only knows the array by its symbol, so
+// its device address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_prolong_scratch[kNoAllocBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void* g_scratch_ptr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+}  // namespace
+
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  CHEB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) { set_error("device index out of range"); return CHEB_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* ptr = nullptr;
+    CHEB_CUDA(cudaGetSymbolAddress(&ptr, g_prolong_scratch));
+    g_scratch_ptr[dev] = ptr;
+  }
+  *out = g_scratch_ptr[dev];
+  return CHEB_OK;
+}
+
 }  // namespace cheb
+
+using namespace cheb;
+
+extern "C" int cheb_prolong_noalloc(cheb_plan coarse, cheb_plan fine, int prec, const void* uc,
+                                    void* uf) {
+  if (!uc || !uf) { set_error("null argument"); return CHEB_ERR_ARG; }
+  int st;
+  if ((st = check_prolong_pair(coarse, fine))) return st;
+  if (prec != CHEB_FP64 && prec != CHEB_FP32) {
+    set_error("prec must be CHEB_FP64 or CHEB_FP32");
+    return CHEB_ERR_ARG;
+  }
+  // intermediate extents: after the x pass (nxf, nyc, nzc), after the y pass (nxf, nyf, nzc)
+  const size_t esz = prec == CHEB_FP64 ? sizeof(double) : sizeof(float);
+  size_t n1 = 0, n2 = 0;
+  if (coarse->dim >= 2) n1 = (size_t)fine->n[0] * coarse->n[1] * coarse->n[2];
+  if (coarse->dim >= 3) n2 = (size_t)fine->n[0] * fine->n[1] * coarse->n[2];
+  const size_t off2 = ((n1 * esz + 255) / 256) * 256;
+  if (off2 + n2 * esz > kNoAllocBytes) {
+    set_error("cheb_prolong_noalloc: the grids need " + std::to_string(off2 + n2 * esz) +
+              " bytes of intermediate storage, above its fixed 16 MiB (use cheb_prolong)");
+    return CHEB_ERR_UNSUPPORTED;
+  }
+  void* base = nullptr;
+  if ((st = noalloc_scratch(&base))) return st;
+  unsigned char* b = (unsigned char*)base;
+  if (prec == CHEB_FP64)
+    return launch_prolong<double>(coarse, fine, (const double*)uc, (double*)uf, (double*)b,
+                                  (double*)(b + off2), fine->stream);
+  return launch_prolong<float>(coarse, fine, (const float*)uc, (float*)uf, (float*)b,
+                               (float*)(b + off2), fine->stream);
+}
