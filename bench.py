@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--contrast", type=float, default=100.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--reorth", type=int, default=0, help="Gram-Schmidt twice per Arnoldi step")
+    ap.add_argument("--inner-rtol", type=float, default=1e-5)
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--apply-only", type=int, default=0, metavar="BITS",
+                    help="only time cheb_apply at the finest level in FP32 (32) or FP64 (64); "
+                         "for profiling")
     return ap.parse_args()
 
 
@@ -218,6 +224,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def apply_only(args, n):
+    """Time cheb_apply alone (profiling helper): u smooth, K the sphere field."""
+    import torch
+    import paper_2606_21410_b300 as P
+    import workloads as W
+    dt = torch.float32 if args.apply_only == 32 else torch.float64
+    p = P.Plan((n, n, n), bc=BC)
+    X, Y, Z = p.mesh()
+    K = torch.from_numpy(W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0,
+                                                  args.contrast)).to("cuda", dt)
+    u = torch.from_numpy(np.sin(X + 2 * Y) * np.cos(Z)).to("cuda", dt)
+    out = torch.empty_like(u)
+    for _ in range(max(3, args.warmup)):
+        p.apply(K, u, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        p.apply(K, u, out)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    wb = 4 if dt == torch.float32 else 8
+    print(json.dumps({"apply_only": args.apply_only, "n": n, "ms": t * 1e3, "gdofs": n ** 3 / t / 1e9,
+                      "gbs_11words": 11 * wb * n ** 3 / t / 1e9}), flush=True)
+
+
 def workload_config(levels, contrast):
     return {"workload": f"two-phase spheres, hierarchical {'->'.join(f'{n}^3' for n in levels)}, "
                         f"K_incl/K_matrix={contrast:g}, mixed FP32/FP64, rtol 1e-12",
@@ -243,8 +276,12 @@ def main():
     import paper_2606_21410_b300 as P
     lib = P.lib
     levels = [int(v) for v in args.levels.split(",")]
+    if args.apply_only:
+        apply_only(args, levels[-1])
+        return
     plans, Ks, bs, hostK, hostb = setup_gpu(levels, args.contrast)
-    opts = dict(mode=1, rtol=1e-12)
+    opts = dict(mode=1, rtol=1e-12, reorth=args.reorth, inner_rtol=args.inner_rtol,
+                restart=args.restart)
     stream = torch.cuda.current_stream()
 
     def step():

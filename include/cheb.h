@@ -71,7 +71,7 @@ enum cheb_status {
 /* Create a plan for one grid.
  *   dim      1, 2 or 3 (the first dim axes are active)
  *   n        points per axis, n[a] >= 3 for a < dim, n[a] = 1 otherwise
- *            (route TRANSFORM needs n - 1 a power of two, 4 <= n - 1 <= 512;
+ *            (route TRANSFORM needs n - 1 a power of two, 4 <= n - 1 <= 256;
  *             route DENSE needs n <= 129; every axis needs one of them)
  *   lo, hi   interval of each axis (hi > lo); entries of unused axes ignored
  *   bc_type  six CHEB_DIRICHLET / CHEB_NEUMANN values, faces x-,x+,y-,y+,z-,z+
@@ -180,10 +180,22 @@ void cheb_solve_opts_default(cheb_solve_opts* opts);
 int cheb_solve(cheb_plan plan, const double* K, const double* b, double* u,
                const cheb_solve_opts* opts, cheb_solve_info* info);
 
+/* Discrete adjoint solve: lambda = A^{-T} dJdu with A = A(K) as in
+ * cheb_apply (LGMRES on A^T, preconditioned by M^{-T}; same options and
+ * modes as cheb_solve).  lambda: FP64 device field, in: initial guess, out:
+ * solution.  When dJdK is not NULL it is incremented by
+ * sum_a (D_a^T P_int lambda) * (D_a u), the gradient of J(u(K)) with respect
+ * to nodal K for the forward solution u (P_int zeroes boundary rows; K enters
+ * A only through the interior rows).  The gradient with respect to b is
+ * lambda itself (f on interior rows, boundary data on boundary rows). */
+int cheb_adjoint_solve(cheb_plan plan, const double* K, const double* u, const double* dJdu,
+                       const cheb_solve_opts* opts, double* lambda, double* dJdK,
+                       cheb_solve_info* info);
+
 /* Modal prolongation (Sec. 2.3.3, Alg. 4): per axis, coarse nodal values
  * -> Chebyshev coefficients (DCT-I), zero-padded to the fine degree, ->
  * fine nodal values (inverse DCT-I).  The fine plan must have N_f = 2 N on
- * every active axis (powers of two, N_f <= 512) and the same box.  u_c:
+ * every active axis (powers of two, N_f <= 256) and the same box.  u_c:
  * coarse device field, u_f: fine device field, both of type prec.  Uses two
  * scratch arrays owned by the fine plan (allocated at the first call). */
 int cheb_prolong(cheb_plan coarse, cheb_plan fine, int prec, const void* u_c, void* u_f);
@@ -218,6 +230,9 @@ int cheb_rel_diff(cheb_plan plan, const double* a, const double* b, double* out)
 int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const* K,
                          const double* const* b, double* const* u, const cheb_solve_opts* opts,
                          cheb_solve_info* infos, double* e_ref);
+
+/* z = M^{-T} y (transposed FDM preconditioner, used by the adjoint solve). */
+int cheb_precond_apply_t(cheb_plan plan, int prec, double kref, const void* y, void* z);
 
 /* z = M^{-1} r for the FDM preconditioner with conductivity kref > 0
  * (device fields of type prec). */

@@ -190,6 +190,41 @@ class Plan:
             raise ChebError(st, "cheb_solve")
         return u, d
 
+    def adjoint_solve(self, K: torch.Tensor, dJdu: torch.Tensor, u: torch.Tensor | None = None,
+                      lam: torch.Tensor | None = None, dJdK: torch.Tensor | None = None,
+                      check_status: bool = True, **opts):
+        """lam = A^{-T} dJdu (``cheb_adjoint_solve``); when dJdK is given it is
+        incremented by the K-gradient for the forward solution u.  Returns
+        (lam, dJdK, info)."""
+        K = self._field(K, "K", torch.float64)
+        dJdu = self._field(dJdu, "dJdu", torch.float64)
+        if lam is None:
+            lam = torch.zeros(self.shape, dtype=torch.float64, device=K.device)
+        lam = self._field(lam, "lam", torch.float64)
+        up = None
+        if dJdK is not None:
+            dJdK = self._field(dJdK, "dJdK", torch.float64)
+            u = self._field(u, "u", torch.float64)
+            up = _vp(u)
+        o = solve_opts(**opts)
+        info = SolveInfo()
+        self._sync_stream()
+        st = lib.cheb_adjoint_solve(self._h, _vp(K), up, _vp(dJdu), C.byref(o), _vp(lam),
+                                    _vp(dJdK) if dJdK is not None else None, C.byref(info))
+        check(st, "cheb_adjoint_solve")
+        if check_status and st != 0:
+            raise ChebError(st, "cheb_adjoint_solve")
+        return lam, dJdK, info.as_dict()
+
+    def precond_apply_t(self, y: torch.Tensor, kref: float, out=None) -> torch.Tensor:
+        """z = M^{-T} y (``cheb_precond_apply_t``)."""
+        y = self._field(y, "y")
+        out = self._out(out, y)
+        self._sync_stream()
+        check(lib.cheb_precond_apply_t(self._h, _PREC[y.dtype], float(kref), _vp(y), _vp(out)),
+              "cheb_precond_apply_t")
+        return out
+
     def precond_apply(self, r: torch.Tensor, kref: float, out=None) -> torch.Tensor:
         """z = M^{-1} r for the fast-diagonalization preconditioner (``cheb_precond_apply``)."""
         r = self._field(r, "r")

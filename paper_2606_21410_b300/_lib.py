@@ -78,6 +78,8 @@ _SIGS = {
     "cheb_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
     "cheb_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "cheb_precond_apply": (i32, [vp, i32, C.c_double, vp, vp]),
+    "cheb_precond_apply_t": (i32, [vp, i32, C.c_double, vp, vp]),
+    "cheb_adjoint_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveInfo)]),
     "cheb_prolong": (i32, [vp, vp, i32, vp, vp]),
     "cheb_prolong_noalloc": (i32, [vp, vp, i32, vp, vp]),
     "cheb_rel_diff": (i32, [vp, vp, vp, f64p]),

@@ -30,7 +30,7 @@ struct AxisK {
   const T* D;                   // n x n row-major (dense route)
 };
 
-__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Shared-memory layout of a line pass: X (tile), ends (2 x kTileL x 2),
 // then the route's buffers.
@@ -92,7 +92,7 @@ __device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* 
       v.x = xa[jj];
       v.y = xb[jj];
       if (divide_m && jj != 0 && jj != N) { v.x *= (T)0.5; v.y *= (T)0.5; }
-      buf[j] = v;
+      buf[fpad(j)] = v;
     }
     __syncwarp();
   };
@@ -105,7 +105,7 @@ __device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* 
     warp_fft<T, P>(buf, tw, lane);
     for (int k = lane; k <= N; k += 32) {
       const T wk = weight(k);
-      const C F = buf[k];
+      const C F = buf[fpad(k)];
       xa[k] = wk * F.x;
       xb[k] = wk * F.y;
     }
@@ -115,7 +115,7 @@ __device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* 
     pack(false);
     warp_fft<T, P>(buf, tw, lane);
     for (int k = lane; k <= N; k += 32) {
-      const C F = buf[k];
+      const C F = buf[fpad(k)];
       xa[k] = F.x;
       xb[k] = F.y;
     }
@@ -127,7 +127,7 @@ __device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* 
     warp_fft<T, P>(buf, tw, lane);
     for (int k = lane; k <= N; k += 32) {
       const T mk = (k == 0 || k == N) ? (T)1 : (T)2;
-      const C F = buf[k];
+      const C F = buf[fpad(k)];
       xa[k] = mk * F.x;
       xb[k] = mk * F.y;
     }
@@ -144,7 +144,7 @@ __device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* 
     warp_fft<T, P>(buf, tw, lane);
     for (int k = lane; k <= N; k += 32) {
       const T mk = (k == 0 || k == N) ? (T)1 : (T)2;
-      const C F = buf[k];
+      const C F = buf[fpad(k)];
       xa[k] = mk * F.x;
       xb[k] = mk * F.y;
     }
@@ -340,6 +340,229 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// transform-route pass with compile-time N: tiles staged by cp.async (u, then
+// K, then the accumulated output) so the loads overlap the warp FFTs
+// ---------------------------------------------------------------------------
+template <int B>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  if constexpr (B == 4) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int NW>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW) : "memory"); }
+
+template <typename T, int P>
+__host__ __device__ constexpr size_t tf_smem_bytes() {
+  return align16(sizeof(T) * kTileL * (P / 2 + 1)) * 2 + align16(sizeof(T) * kTileL * 4) +
+         align16(2 * sizeof(T) * (size_t)(kTileL / 2) * FftBuf<P>::len) + align16(2 * sizeof(T) * (size_t)P);
+}
+
+template <typename T, int P, int CM>
+__global__ void __launch_bounds__(kThreads, 2)
+tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
+               const T* __restrict__ u, T* __restrict__ out) {
+  typedef typename C2<T>::t C;
+  constexpr int N = P / 2, n = N + 1, ldx = n;  // n is odd
+  constexpr int TE = kTileL * n;
+  constexpr int BL = FftBuf<P>::len;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* p = smem_raw;
+  T* X = (T*)p;    p += align16(sizeof(T) * kTileL * ldx);
+  T* KO = (T*)p;   p += align16(sizeof(T) * kTileL * ldx);
+  T* ends = (T*)p; p += align16(sizeof(T) * kTileL * 4);
+  C* Cb = (C*)p;   p += align16(2 * sizeof(T) * (size_t)(kTileL / 2) * BL);
+  C* tw = (C*)p;
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const bool adj = (kind == kAdjFirst || kind == kAdjAcc);
+  const bool is_acc = (kind == kApplyAcc || kind == kAdjAcc);
+  const bool first = (kind == kApplyFirst || kind == kAdjFirst);
+  const bool needK = !(kind == kDeriv || kind == kDerivT);
+  // tile geometry
+  int line0 = 0, i0 = 0, outer = 0;
+  size_t base = 0, pstride = 1;
+  if (axis == 0) {
+    line0 = blockIdx.x * kTileL;
+  } else {
+    const int nbx = (nx + kTileL - 1) / kTileL;
+    i0 = (blockIdx.x % nbx) * kTileL;
+    outer = blockIdx.x / nbx;
+    if (axis == 1) { base = (size_t)outer * ny * nx + i0; pstride = nx; }
+    else { base = (size_t)outer * nx + i0; pstride = (size_t)nx * ny; }
+  }
+  const int nlines = ny * nz;
+  auto elem = [&](int e, int& l, int& pt, size_t& gi) -> bool {
+    if (axis == 0) {
+      l = e / n;
+      pt = e - l * n;
+      gi = (size_t)line0 * n + e;
+      return line0 + l < nlines;
+    }
+    l = e & (kTileL - 1);
+    pt = e >> 4;
+    gi = base + (size_t)pt * pstride + l;
+    return i0 + l < nx;
+  };
+  auto node = [&](int l, int pt, int& i, int& j, int& k) {
+    if (axis == 0) { const int line = line0 + l; i = pt; j = line % ny; k = line / ny; }
+    else if (axis == 1) { i = i0 + l; j = pt; k = outer; }
+    else { i = i0 + l; j = outer; k = pt; }
+  };
+  auto on_bnd = [&](int i, int j, int k) -> bool {
+    bool b = (i == 0 || i == nx - 1);
+    if (g.dim > 1) b = b || j == 0 || j == ny - 1;
+    if (g.dim > 2) b = b || k == 0 || k == nz - 1;
+    return b;
+  };
+  // ---- stage twiddles and launch the tile copies
+  for (int t = threadIdx.x; t < P; t += kThreads) tw[t] = ax.tw[t];
+  for (int e = threadIdx.x; e < TE; e += kThreads) {
+    int l, pt; size_t gi;
+    if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&X[l * ldx + pt], u + gi);
+    else X[l * ldx + pt] = (T)0;
+  }
+  cp_commit();
+  if (needK) {
+    for (int e = threadIdx.x; e < TE; e += kThreads) {
+      int l, pt; size_t gi;
+      if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&KO[l * ldx + pt], K + gi);
+      else KO[l * ldx + pt] = (T)0;
+    }
+  }
+  cp_commit();
+  cp_wait<1>();
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  C* buf = Cb + (size_t)w * BL;
+
+  if (kind == kDeriv || kind == kDerivT) {
+    if (kind == kDeriv) warp_deriv_tf<T, P, CM, false>(X, ldx, buf, tw, N, ax.scale, w, lane);
+    else warp_deriv_tf<T, P, CM, true>(X, ldx, buf, tw, N, ax.scale, w, lane);
+    __syncthreads();
+    for (int e = threadIdx.x; e < TE; e += kThreads) {
+      int l, pt; size_t gi;
+      if (elem(e, l, pt, gi)) out[gi] = X[l * ldx + pt];
+    }
+    return;
+  }
+
+  if (!adj) {
+    warp_deriv_tf<T, P, CM, false>(X, ldx, buf, tw, N, ax.scale, w, lane);
+    __syncthreads();
+    if (threadIdx.x < kTileL) {
+      ends[threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
+      ends[threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
+    }
+    cp_wait<0>();
+    __syncthreads();
+    for (int e = threadIdx.x; e < TE; e += kThreads) {
+      const int l = e / n, pt = e - (e / n) * n;
+      X[l * ldx + pt] *= KO[l * ldx + pt];
+    }
+    __syncthreads();
+    if (is_acc) {  // prefetch the output being accumulated into the free K tile
+      for (int e = threadIdx.x; e < TE; e += kThreads) {
+        int l, pt; size_t gi;
+        if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&KO[l * ldx + pt], out + gi);
+      }
+      cp_commit();
+    }
+    warp_deriv_tf<T, P, CM, false>(X, ldx, buf, tw, N, ax.scale, w, lane);
+    cp_wait<0>();
+    __syncthreads();
+    for (int e = threadIdx.x; e < TE; e += kThreads) {
+      int l, pt; size_t gi;
+      if (!elem(e, l, pt, gi)) continue;
+      int i, j, k;
+      node(l, pt, i, j, k);
+      const T v = -X[l * ldx + pt];
+      if (!on_bnd(i, j, k)) {
+        out[gi] = first ? v : KO[l * ldx + pt] + v;
+        continue;
+      }
+      const int o = owner_face(g, i, j, k);
+      if (g.bc[o] == CHEB_DIRICHLET) {
+        if (first) out[gi] = u[gi];
+      } else if ((o >> 1) == axis) {
+        // hi face (side 1) is line point 0, lo face (side 0) is point N
+        out[gi] = (o & 1) ? ends[l * 2 + 0] : -ends[l * 2 + 1];
+      } else if (first) {
+        out[gi] = (T)0;  // Neumann row of a later axis: written by that pass
+      }
+    }
+    return;
+  }
+
+  // ---- A^T lam for this axis: D_a^T (S_a lam - K * D_a^T (P_int lam))
+  if (threadIdx.x < kTileL) {
+    const int l = threadIdx.x;
+    T s0 = (T)0, sN = (T)0;
+    int e0l, e0p; size_t gi;
+    if (elem(l * (axis == 0 ? n : 1), e0l, e0p, gi)) {
+      int i, j, k;
+      node(l, 0, i, j, k);
+      const int o = owner_face(g, i, j, k);
+      if (o == 2 * axis + 1 && g.bc[o] == CHEB_NEUMANN) s0 = X[l * ldx + 0];
+      node(l, N, i, j, k);
+      const int o2 = owner_face(g, i, j, k);
+      if (o2 == 2 * axis && g.bc[o2] == CHEB_NEUMANN) sN = -X[l * ldx + N];
+    }
+    ends[l * 2 + 0] = s0;
+    ends[l * 2 + 1] = sN;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TE; e += kThreads) {
+    int l, pt; size_t gi;
+    if (!elem(e, l, pt, gi)) continue;
+    int i, j, k;
+    node(l, pt, i, j, k);
+    if (on_bnd(i, j, k)) X[l * ldx + pt] = (T)0;
+  }
+  __syncthreads();
+  warp_deriv_tf<T, P, CM, true>(X, ldx, buf, tw, N, ax.scale, w, lane);
+  cp_wait<0>();
+  __syncthreads();
+  for (int e = threadIdx.x; e < TE; e += kThreads) {
+    const int l = e / n, pt = e - (e / n) * n;
+    T v = -KO[l * ldx + pt] * X[l * ldx + pt];
+    if (pt == 0) v += ends[l * 2 + 0];
+    if (pt == N) v += ends[l * 2 + 1];
+    X[l * ldx + pt] = v;
+  }
+  __syncthreads();
+  if (is_acc) {
+    for (int e = threadIdx.x; e < TE; e += kThreads) {
+      int l, pt; size_t gi;
+      if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&KO[l * ldx + pt], out + gi);
+    }
+    cp_commit();
+  }
+  warp_deriv_tf<T, P, CM, true>(X, ldx, buf, tw, N, ax.scale, w, lane);
+  cp_wait<0>();
+  __syncthreads();
+  for (int e = threadIdx.x; e < TE; e += kThreads) {
+    int l, pt; size_t gi;
+    if (!elem(e, l, pt, gi)) continue;
+    T v = X[l * ldx + pt];
+    if (first) {
+      int i, j, k;
+      node(l, pt, i, j, k);
+      if (on_bnd(i, j, k)) {
+        const int o = owner_face(g, i, j, k);
+        if (g.bc[o] == CHEB_DIRICHLET) v += u[gi];
+      }
+      out[gi] = v;
+    } else {
+      out[gi] = KO[l * ldx + pt] + v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host dispatch
 // ---------------------------------------------------------------------------
 template <typename T> static AxisK<T> axis_k(const AxisTables& t);
@@ -353,15 +576,26 @@ template <> AxisK<float> axis_k<float>(const AxisTables& t) {
 template <typename T, int ROUTE, int P, int CM>
 static int launch_kernel(const Geom& g, int axis, int kind, const AxisK<T>& ak, const T* K,
                          const T* u, T* out, cudaStream_t s, int nblocks) {
-  auto kern = line_pass_kernel<T, ROUTE, P, CM>;
-  const size_t smem = pass_smem_bytes<T>(ROUTE, ak.n, P);
   static size_t configured = 0;  // per instantiation
-  if (smem > configured) {
-    CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
+  if constexpr (ROUTE == CHEB_ROUTE_TRANSFORM) {
+    auto kern = tf_pass_kernel<T, P, CM>;
+    constexpr size_t smem = tf_smem_bytes<T, P>();
+    if (smem > configured) {
+      CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      configured = smem;
+    }
+    kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
+    CHEB_LAUNCH_CHECK("tf_pass_kernel");
+  } else {
+    auto kern = line_pass_kernel<T, ROUTE, P, CM>;
+    const size_t smem = pass_smem_bytes<T>(ROUTE, ak.n, P);
+    if (smem > configured) {
+      CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      configured = smem;
+    }
+    kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
+    CHEB_LAUNCH_CHECK("line_pass_kernel");
   }
-  kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
-  CHEB_LAUNCH_CHECK("line_pass_kernel");
   return CHEB_OK;
 }
 
@@ -388,9 +622,8 @@ int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u
     case 128: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 128, 2>(g, axis, kind, ak, K, u, out, s, nblocks);
     case 256: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 256, 3>(g, axis, kind, ak, K, u, out, s, nblocks);
     case 512: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 512, 5>(g, axis, kind, ak, K, u, out, s, nblocks);
-    case 1024: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 1024, 9>(g, axis, kind, ak, K, u, out, s, nblocks);
     default:
-      set_error("transform route needs 2N a power of two in [8, 1024]");
+      set_error("transform route needs 2N a power of two in [8, 512]");
       return CHEB_ERR_UNSUPPORTED;
   }
 }

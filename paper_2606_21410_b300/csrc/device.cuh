@@ -105,10 +105,16 @@ template <typename T> struct Dft<T, 8> {
   }
 };
 
+// Padded position of element idx of a warp FFT buffer: one spare slot every
+// 8 complex values keeps the strided Stockham stores free of bank conflicts.
+__host__ __device__ __forceinline__ int fpad(int idx) { return idx + (idx >> 3); }
+template <int P> struct FftBuf { static constexpr int len = P + P / 8; };
+
 // One Stockham stage of radix R on a length-P sequence held in shared
 // memory by one warp (in place: every lane reads its butterflies into
 // registers, the warp synchronises, then every lane writes).  Ns is the
-// product of the radices of the earlier stages.  tw[t] = exp(-2 pi i t / P).
+// product of the radices of the earlier stages.  Stage twiddles are stored
+// contiguously: tw[(Ns - 1) + (r - 1) Ns + k] = exp(-2 pi i r k / (Ns R)).
 template <typename T, int P, int R, int Ns>
 __device__ __forceinline__ void warp_stage(typename C2<T>::t* buf, const typename C2<T>::t* tw,
                                            int lane) {
@@ -121,12 +127,11 @@ __device__ __forceinline__ void warp_stage(typename C2<T>::t* buf, const typenam
     const int j = lane + 32 * it;
     if (NB % 32 == 0 || j < NB) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[it][r] = buf[j + r * NB];
+      for (int r = 0; r < R; ++r) v[it][r] = buf[fpad(j + r * NB)];
       if (Ns > 1) {
         const int k = j & (Ns - 1);
-        constexpr int step = P / (Ns * R);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], tw[r * k * step]);
+        for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], tw[(Ns - 1) + (r - 1) * Ns + k]);
       }
       Dft<T, R>::run(v[it]);
     }
@@ -139,7 +144,7 @@ __device__ __forceinline__ void warp_stage(typename C2<T>::t* buf, const typenam
       const int k = j & (Ns - 1);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[it][r];
+      for (int r = 0; r < R; ++r) buf[fpad(base + r * Ns)] = v[it][r];
     }
   }
   __syncwarp();
@@ -161,6 +166,7 @@ struct WarpFft {
   }
 };
 
+// Forward DFT of length P (power of two, 8..1024) of buf (padded layout).
 template <typename T, int P>
 __device__ __forceinline__ void warp_fft(typename C2<T>::t* buf, const typename C2<T>::t* tw,
                                          int lane) {

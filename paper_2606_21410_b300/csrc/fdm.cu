@@ -134,8 +134,11 @@ int fdm_setup(const cheb_plan_s* p, Fdm& f) {
 void fdm_free(Fdm& f) {
   for (int a = 0; a < 3; ++a) { free_axis(f.d64[a]); free_axis(f.d32[a]); }
   cudaFree(f.U64[0]); cudaFree(f.U64[1]); cudaFree(f.U32[0]); cudaFree(f.U32[1]);
+  cudaFree(f.Y64); cudaFree(f.Y32);
   f.U64[0] = f.U64[1] = nullptr;
   f.U32[0] = f.U32[1] = nullptr;
+  f.Y64 = nullptr;
+  f.Y32 = nullptr;
   f.ready = false;
 }
 
@@ -327,6 +330,170 @@ __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __
   }
 }
 
+// ---------------------------------------------------------------------------
+// transposed preconditioner M^{-T} (for the adjoint solve): the steps of
+// M^{-1} in reverse order, each transposed.  Y is a work copy of the input
+// that collects the adjoints of intermediate values; z is the output.
+// ---------------------------------------------------------------------------
+
+// Transposed end-row solves on boundary lines (kind 1 or 2, as in
+// fdm_bline_kernel): for every end solved from a Neumann row of axis a,
+// route its adjoint to z at the two ends and to Y along the line interior.
+template <typename T>
+__global__ void fdm_bline_t_kernel(Geom g, FdmK<T> t, int a, int kind, T* __restrict__ Y,
+                                   T* __restrict__ z) {
+  const int nb_axes = g.dim - 1;
+  int others[2], no = 0;
+  for (int q = 0; q < g.dim; ++q)
+    if (q != a) others[no++] = q;
+  int total;
+  if (kind == 1) {
+    int cnt = 0;
+    for (int q = 0; q < nb_axes; ++q) {
+      const int cax = (nb_axes == 2) ? others[1 - q] : -1;
+      cnt += 2 * (cax >= 0 ? g.n[cax] - 2 : 1);
+    }
+    total = cnt;
+  } else {
+    total = (nb_axes == 2) ? 4 : 0;
+  }
+  const int n = g.n[a], N = n - 1;
+  const T* D0 = t.Drow[a];
+  const T* DN = t.Drow[a] + n;
+  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < total; L += gridDim.x * blockDim.x) {
+    int idx[3] = {0, 0, 0};
+    if (kind == 1) {
+      int rest = L, q = 0;
+      for (; q < nb_axes; ++q) {
+        const int cax = (nb_axes == 2) ? others[1 - q] : -1;
+        const int span = 2 * (cax >= 0 ? g.n[cax] - 2 : 1);
+        if (rest < span) break;
+        rest -= span;
+      }
+      const int bax = others[q];
+      const int cax = (nb_axes == 2) ? others[1 - q] : -1;
+      const int side = rest & 1, tt = rest >> 1;
+      idx[bax] = side ? 0 : g.n[bax] - 1;
+      if (cax >= 0) idx[cax] = 1 + tt;
+    } else {
+      idx[others[0]] = (L & 1) ? 0 : g.n[others[0]] - 1;
+      idx[others[1]] = (L & 2) ? 0 : g.n[others[1]] - 1;
+    }
+    int e[3] = {idx[0], idx[1], idx[2]};
+    e[a] = 0;
+    const size_t p0 = gidx3(g, e[0], e[1], e[2]);
+    const int o0 = owner_face(g, e[0], e[1], e[2]);
+    e[a] = N;
+    const size_t pN = gidx3(g, e[0], e[1], e[2]);
+    const int oN = owner_face(g, e[0], e[1], e[2]);
+    const bool dir0 = g.bc[o0] == CHEB_DIRICHLET, dirN = g.bc[oN] == CHEB_DIRICHLET;
+    const bool neu0 = (o0 == 2 * a + 1) && !dir0;
+    const bool neuN = (oN == 2 * a) && !dirN;
+    if (!neu0 && !neuN) continue;
+    const T a00 = D0[0], a01 = D0[N], a10 = DN[0], a11 = DN[N];
+    // adjoints of the right-hand sides b0 = r0 - s0, b1 = -rN - sN
+    T bb0 = 0, bb1 = 0;
+    if (neu0 && neuN) {
+      const T y0 = Y[p0], yN = Y[pN];
+      const T det = a00 * a11 - a01 * a10;
+      // [b0; b1] = A^{-T} [y0; yN]
+      bb0 = (a11 * y0 - a10 * yN) / det;
+      bb1 = (-a01 * y0 + a00 * yN) / det;
+      z[p0] = bb0;
+      z[pN] = -bb1;
+    } else if (neu0) {
+      // x0 = (b0 - a01 rN) / a00 with rN the Dirichlet value of the other end:
+      // that end's adjoint gains -a01 bb0 (its own copy is added later)
+      bb0 = Y[p0] / a00;
+      z[p0] = bb0;
+      Y[pN] -= a01 * bb0;
+    } else {
+      bb1 = Y[pN] / a11;
+      z[pN] = -bb1;
+      Y[p0] -= a10 * bb1;
+    }
+    for (int l = 1; l < N; ++l) {
+      e[a] = l;
+      Y[gidx3(g, e[0], e[1], e[2])] -= bb0 * D0[l] + bb1 * DN[l];
+    }
+  }
+}
+
+// Dirichlet-owned edge / corner nodes: z = Y (the transposed copy x = r).
+template <typename T>
+__global__ void fdm_edge_dirichlet_t_kernel(Geom g, const T* __restrict__ Y, T* __restrict__ z) {
+  const size_t tot = (size_t)g.n[0] * g.n[1] * g.n[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((size_t)g.n[0] * g.n[1]));
+    const int idx[3] = {i, j, k};
+    int nf = 0;
+    for (int a = 0; a < g.dim; ++a) nf += (idx[a] == 0 || idx[a] == g.n[a] - 1);
+    if (nf < 2) continue;
+    const int o = owner_face(g, i, j, k);
+    if (g.bc[o] == CHEB_DIRICHLET) z[c] = Y[c];
+  }
+}
+
+// Transpose of the face step and the interior scatter:
+//   Ubar[c] = Y[I(c)] + sum_a (G_a[0][c_a] Y[e0_a(c)] + G_a[1][c_a] Y[eN_a(c)])
+template <typename T>
+__global__ void fdm_gather_t_kernel(Geom g, FdmK<T> t, const T* __restrict__ Y, T* __restrict__ U) {
+  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int ci = (int)(c % t.m[0]);
+    const int cj = (int)((c / t.m[0]) % t.m[1]);
+    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
+    const int idx[3] = {ci + t.off[0], cj + t.off[1], ck + t.off[2]};
+    const int cl[3] = {ci, cj, ck};
+    T v = Y[gidx3(g, idx[0], idx[1], idx[2])];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= g.dim) break;
+      int e0[3] = {idx[0], idx[1], idx[2]}, eN[3] = {idx[0], idx[1], idx[2]};
+      e0[a] = 0;
+      eN[a] = g.n[a] - 1;
+      const int ma = t.m[a];
+      v += t.G[a][cl[a]] * Y[gidx3(g, e0[0], e0[1], e0[2])] +
+           t.G[a][ma + cl[a]] * Y[gidx3(g, eN[0], eN[1], eN[2])];
+    }
+    U[c] = v;
+  }
+}
+
+// Per interior a-line: z[e0], z[eN] = Binv^T (Y[e0], Y[eN]) + kref (Lh^T Ubar(line)).
+template <typename T>
+__global__ void fdm_faces_t_kernel(Geom g, FdmK<T> t, int a, T kref, const T* __restrict__ U,
+                                   const T* __restrict__ Y, T* __restrict__ z) {
+  const int ma = t.m[a];
+  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  const size_t lines = (size_t)t.m[b] * t.m[c];
+  const size_t str[3] = {1, (size_t)t.m[0], (size_t)t.m[0] * t.m[1]};
+  const T* Lh = t.Lh[a];
+  const T* Bi = t.Binv[a];
+  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < lines; L += (size_t)gridDim.x * blockDim.x) {
+    const int cb = (int)(L % t.m[b]), cc = (int)(L / t.m[b]);
+    int cidx[3];
+    cidx[a] = 0; cidx[b] = cb; cidx[c] = cc;
+    const size_t base = cidx[0] * str[0] + cidx[1] * str[1] + cidx[2] * str[2];
+    T s0 = 0, sN = 0;
+    for (int l = 0; l < ma; ++l) {
+      const T v = U[base + (size_t)l * str[a]];
+      s0 += Lh[l * 2 + 0] * v;
+      sN += Lh[l * 2 + 1] * v;
+    }
+    int idx[3] = {cidx[0] + t.off[0], cidx[1] + t.off[1], cidx[2] + t.off[2]};
+    idx[a] = 0;
+    const size_t p0 = gidx3(g, idx[0], idx[1], idx[2]);
+    idx[a] = g.n[a] - 1;
+    const size_t pN = gidx3(g, idx[0], idx[1], idx[2]);
+    const T y0 = Y[p0], yN = Y[pN];
+    z[p0] = Bi[0] * y0 + Bi[2] * yN + kref * s0;
+    z[pN] = Bi[1] * y0 + Bi[3] * yN + kref * sN;
+  }
+}
+
 template <typename T> static FdmK<T> make_k(const Fdm& f, int dim);
 template <> FdmK<double> make_k<double>(const Fdm& f, int dim) {
   FdmK<double> k;
@@ -420,5 +587,84 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
 
 template int fdm_apply<double>(const cheb_plan_s*, Fdm&, double, const double*, double*, cudaStream_t);
 template int fdm_apply<float>(const cheb_plan_s*, Fdm&, double, const float*, float*, cudaStream_t);
+
+template <typename T> static T* ybuf(Fdm& f);
+template <> double* ybuf<double>(Fdm& f) { return f.Y64; }
+template <> float* ybuf<float>(Fdm& f) { return f.Y32; }
+
+template <typename T>
+int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cudaStream_t s) {
+  const Geom g = p->geom();
+  const FdmK<T> k = make_k<T>(f, p->dim);
+  const size_t tot = (size_t)f.m[0] * f.m[1] * f.m[2];
+  const size_t nfull = p->size();
+  T** U = ubuf<T>(f);
+  if (!U[0]) {
+    CHEB_CUDA(cudaMalloc(&U[0], sizeof(T) * tot));
+    CHEB_CUDA(cudaMalloc(&U[1], sizeof(T) * tot));
+  }
+  if (!ybuf<T>(f)) {
+    T* yb = nullptr;
+    CHEB_CUDA(cudaMalloc(&yb, sizeof(T) * nfull));
+    if constexpr (sizeof(T) == 8) f.Y64 = (double*)yb;
+    else f.Y32 = (float*)yb;
+  }
+  T* Y = ybuf<T>(f);
+  CHEB_CUDA(cudaMemcpyAsync(Y, y, sizeof(T) * nfull, cudaMemcpyDeviceToDevice, s));
+  if (p->dim == 3) {
+    for (int a = 2; a >= 0; --a) {
+      fdm_bline_t_kernel<T><<<1, 32, 0, s>>>(g, k, a, 2, Y, z);
+      CHEB_LAUNCH_CHECK("fdm_bline_t_kernel");
+    }
+  }
+  if (p->dim >= 2) {
+    for (int a = p->dim - 1; a >= 0; --a) {
+      fdm_bline_t_kernel<T><<<8, 128, 0, s>>>(g, k, a, 1, Y, z);
+      CHEB_LAUNCH_CHECK("fdm_bline_t_kernel");
+    }
+    fdm_edge_dirichlet_t_kernel<T><<<grid_for(nfull), 256, 0, s>>>(g, Y, z);
+    CHEB_LAUNCH_CHECK("fdm_edge_dirichlet_t_kernel");
+  }
+  fdm_gather_t_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, Y, U[0]);
+  CHEB_LAUNCH_CHECK("fdm_gather_t_kernel");
+  const int mx = f.m[0], my = f.m[1], mz = f.m[2];
+  int cur = 0;
+  // (S_z S_y S_x Lambda^{-1} Sinv_z Sinv_y Sinv_x)^T = Sinv^T ... Lambda^{-1} ... S^T
+  auto contract_t = [&](int a, bool inverse) -> int {
+    const FdmAxisDev<T>& d = axdev<T>(f, a);
+    const int o = 1 - cur;
+    int st;
+    // contracting with M^T along axis a: x axis uses (M^T)^T = M as the right factor
+    if (a == 0) {
+      st = k_gemm<T>(my * mz, mx, mx, U[cur], mx, 0, inverse ? d.Sinv : d.S, mx, 0, U[o], mx, 0, 1, s);
+    } else if (a == 1) {
+      st = k_gemm<T>(my, mx, my, inverse ? d.SinvT : d.ST, my, 0, U[cur], mx, (long long)my * mx, U[o], mx,
+                     (long long)my * mx, mz, s);
+    } else {
+      st = k_gemm<T>(mz, my * mx, mz, inverse ? d.SinvT : d.ST, mz, 0, U[cur], my * mx, 0, U[o], my * mx, 0,
+                     1, s);
+    }
+    cur = o;
+    return st;
+  };
+  int st;
+  for (int a = 0; a < p->dim; ++a)
+    if ((st = contract_t(a, false))) return st;
+  fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+  CHEB_LAUNCH_CHECK("fdm_scale_kernel");
+  for (int a = p->dim - 1; a >= 0; --a)
+    if ((st = contract_t(a, true))) return st;
+  fdm_scatter_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, U[cur], z);
+  CHEB_LAUNCH_CHECK("fdm_scatter_kernel");
+  for (int a = 0; a < p->dim; ++a) {
+    const size_t lines = tot / f.m[a];
+    fdm_faces_t_kernel<T><<<grid_for(lines), 256, 0, s>>>(g, k, a, (T)kref, U[cur], Y, z);
+    CHEB_LAUNCH_CHECK("fdm_faces_t_kernel");
+  }
+  return CHEB_OK;
+}
+
+template int fdm_apply_t<double>(const cheb_plan_s*, Fdm&, double, const double*, double*, cudaStream_t);
+template int fdm_apply_t<float>(const cheb_plan_s*, Fdm&, double, const float*, float*, cudaStream_t);
 
 }  // namespace cheb

@@ -28,6 +28,8 @@ struct Fdm {
   FdmAxisDev<float> d32[3];
   double* U64[2] = {nullptr, nullptr};  // compact interior work buffers
   float* U32[2] = {nullptr, nullptr};
+  double* Y64 = nullptr;                // transposed application: work copy of the input
+  float* Y32 = nullptr;
 };
 
 int fdm_setup(const cheb_plan_s* p, Fdm& f);
@@ -35,5 +37,8 @@ void fdm_free(Fdm& f);
 // x = M^{-1} r with M the constant-kref collocation operator (same boundary rows).
 template <typename T>
 int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaStream_t s);
+// z = M^{-T} y (for the adjoint solve).
+template <typename T>
+int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cudaStream_t s);
 
 }  // namespace cheb

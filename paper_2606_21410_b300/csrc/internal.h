@@ -14,7 +14,7 @@ namespace cheb {
 constexpr int kTileL = 16;      // lines per CTA in the line passes
 constexpr int kThreads = 256;   // threads per CTA in the line passes
 constexpr int kDenseMaxN = 129; // largest axis size of the dense route
-constexpr int kTransformMaxN = 512;
+constexpr int kTransformMaxN = 256;
 
 // Per-axis device tables.  The transform route needs the FFT twiddles
 // exp(-2 pi i t / P), t < P = 2N; the dense route the differentiation matrix.

@@ -98,12 +98,22 @@ static int build_axis(cheb_plan_s* p, int a) {
   t.route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
   if (t.transform_ok) {
     t.P = 2 * t.N;
-    std::vector<double2> tw64(t.P);
-    std::vector<float2> tw32(t.P);
-    for (int k = 0; k < t.P; ++k) {
-      const double ang = -2.0 * M_PI * (double)k / (double)t.P;
-      tw64[k] = make_double2(std::cos(ang), std::sin(ang));
-      tw32[k] = make_float2((float)tw64[k].x, (float)tw64[k].y);
+    // per-stage twiddles of the warp FFT (radix 8, then 4 or 2):
+    // stage with span Ns and radix R stores exp(-2 pi i r k / (Ns R)) at
+    // (Ns - 1) + (r - 1) Ns + k, r = 1..R-1, k < Ns
+    std::vector<double2> tw64(t.P, make_double2(1.0, 0.0));
+    std::vector<float2> tw32(t.P, make_float2(1.f, 0.f));
+    for (int Ns = 1, rem = t.P; rem > 1;) {
+      const int R = rem % 8 == 0 ? 8 : rem;
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          const double ang = -2.0 * M_PI * (double)(r * k) / (double)(Ns * R);
+          const int at = (Ns - 1) + (r - 1) * Ns + k;
+          tw64[at] = make_double2(std::cos(ang), std::sin(ang));
+          tw32[at] = make_float2((float)tw64[at].x, (float)tw64[at].y);
+        }
+      Ns *= R;
+      rem /= R;
     }
     CHEB_CUDA(cudaMalloc(&t.tw64, sizeof(double2) * t.P));
     CHEB_CUDA(cudaMalloc(&t.tw32, sizeof(float2) * t.P));
@@ -227,7 +237,7 @@ int cheb_plan_set_route(cheb_plan p, int axis, int route) {
   AxisTables& t = p->ax[axis];
   if (route == CHEB_ROUTE_AUTO) route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
   if (route == CHEB_ROUTE_TRANSFORM && !t.transform_ok) {
-    set_error("transform route needs n - 1 a power of two in [4, 512]"); return CHEB_ERR_UNSUPPORTED;
+    set_error("transform route needs n - 1 a power of two in [4, 256]"); return CHEB_ERR_UNSUPPORTED;
   }
   if (route == CHEB_ROUTE_DENSE && !t.dense_ok) {
     set_error("dense route needs n <= 129"); return CHEB_ERR_UNSUPPORTED;

@@ -20,12 +20,13 @@ namespace cheb {
 
 __host__ __device__ __forceinline__ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <typename T>
-static size_t prolong_smem(int nc, int PC) {
+template <typename T, int PC>
+static size_t prolong_smem() {
+  const int nc = PC / 2 + 1;
   const int nf = 2 * (nc - 1) + 1;
   const int ldx = nf | 1;
-  return al16(sizeof(T) * kTileL * ldx) + al16(2 * sizeof(T) * (size_t)(kTileL / 2) * 2 * PC) +
-         al16(2 * sizeof(T) * (size_t)2 * PC);
+  return al16(sizeof(T) * kTileL * ldx) + al16(2 * sizeof(T) * (size_t)(kTileL / 2) * FftBuf<2 * PC>::len) +
+         al16(2 * sizeof(T) * (size_t)3 * PC);
 }
 
 // dims: extents of the input array (axis a has nc points); the output has
@@ -42,12 +43,14 @@ prolong_pass_kernel(int a, int nx, int ny, int nz, const typename C2<T>::t* __re
   const int nc = NC + 1, nf = NF + 1;
   const int ldx = nf | 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BL = FftBuf<PF>::len;
   unsigned char* p = smem_raw;
   T* X = (T*)p;      p += al16(sizeof(T) * kTileL * ldx);
-  C* Cb = (C*)p;     p += al16(2 * sizeof(T) * (size_t)(kTileL / 2) * PF);
-  C* tw = (C*)p;     // fine twiddles; coarse twiddles are every other one
+  C* Cb = (C*)p;     p += al16(2 * sizeof(T) * (size_t)(kTileL / 2) * BL);
+  C* tw = (C*)p;     // fine-transform stage twiddles (PF), then coarse ones (PC)
+  C* twc_s = tw + PF;
   for (int t = threadIdx.x; t < PF; t += blockDim.x) tw[t] = twf[t];
-  (void)twc;
+  for (int t = threadIdx.x; t < PC; t += blockDim.x) twc_s[t] = twc[t];
   // tile geometry: lines are indexed by the two other axes
   const int dims_in[3] = {nx, ny, nz};
   int dims_out[3] = {nx, ny, nz};
@@ -84,15 +87,12 @@ prolong_pass_kernel(int a, int nx, int ny, int nz, const typename C2<T>::t* __re
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* xa = X + (2 * w) * ldx;
     T* xb = X + (2 * w + 1) * ldx;
-    C* buf = Cb + (size_t)w * PF;
-    // coarse DCT-I with the length-PC FFT (twiddle stride 2 in the fine table:
-    // exp(-2 pi i t / PC) = exp(-2 pi i 2t / PF)); use a compacted copy in buf's tail
-    C* twc_s = buf + PC;  // PC entries, free until the fine FFT
-    for (int t = lane; t < PC; t += 32) twc_s[t] = tw[2 * t];
+    C* buf = Cb + (size_t)w * BL;
+    // coarse DCT-I with the length-PC FFT
     for (int j = lane; j < PC; j += 32) {
       const int jj = j <= NC ? j : PC - j;
       C v; v.x = xa[jj]; v.y = xb[jj];
-      buf[j] = v;
+      buf[fpad(j)] = v;
     }
     __syncwarp();
     warp_fft<T, PC>(buf, twc_s, lane);
@@ -101,7 +101,7 @@ prolong_pass_kernel(int a, int nx, int ny, int nz, const typename C2<T>::t* __re
     for (int k = lane; k <= NF; k += 32) {
       T ba = 0, bb = 0;
       if (k <= NC) {
-        const C F = buf[k];
+        const C F = buf[fpad(k)];
         const T wk = (k == NC) ? (T)0.5 * s : s;
         ba = wk * F.x;
         bb = wk * F.y;
@@ -113,12 +113,12 @@ prolong_pass_kernel(int a, int nx, int ny, int nz, const typename C2<T>::t* __re
     for (int j = lane; j < PF; j += 32) {
       const int jj = j <= NF ? j : PF - j;
       C v; v.x = xa[jj]; v.y = xb[jj];
-      buf[j] = v;
+      buf[fpad(j)] = v;
     }
     __syncwarp();
     warp_fft<T, PF>(buf, tw, lane);
     for (int k = lane; k <= NF; k += 32) {
-      const C F = buf[k];
+      const C F = buf[fpad(k)];
       xa[k] = F.x;
       xb[k] = F.y;
     }
@@ -134,10 +134,10 @@ prolong_pass_kernel(int a, int nx, int ny, int nz, const typename C2<T>::t* __re
 }
 
 template <typename T, int PC>
-static int launch_prolong_pass(int a, const int dims[3], const typename C2<T>::t* twf, const T* in,
-                               T* out, cudaStream_t s) {
+static int launch_prolong_pass(int a, const int dims[3], const typename C2<T>::t* twc,
+                               const typename C2<T>::t* twf, const T* in, T* out, cudaStream_t s) {
   auto kern = prolong_pass_kernel<T, PC>;
-  const size_t smem = prolong_smem<T>(PC / 2 + 1, PC);
+  const size_t smem = prolong_smem<T, PC>();
   static size_t configured = 0;
   if (smem > configured) {
     CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -146,7 +146,7 @@ static int launch_prolong_pass(int a, const int dims[3], const typename C2<T>::t
   int nblocks;
   if (a == 0) nblocks = (dims[1] * dims[2] + kTileL - 1) / kTileL;
   else nblocks = ((dims[0] + kTileL - 1) / kTileL) * (a == 1 ? dims[2] : dims[1]);
-  kern<<<nblocks, kThreads, smem, s>>>(a, dims[0], dims[1], dims[2], nullptr, twf, in, out);
+  kern<<<nblocks, kThreads, smem, s>>>(a, dims[0], dims[1], dims[2], twc, twf, in, out);
   CHEB_LAUNCH_CHECK("prolong_pass_kernel");
   return CHEB_OK;
 }
@@ -156,18 +156,17 @@ template <> const double2* twf_of<double>(const AxisTables& t) { return t.tw64; 
 template <> const float2* twf_of<float>(const AxisTables& t) { return t.tw32; }
 
 template <typename T>
-static int prolong_pass(int a, int PC, const int dims[3], const typename C2<T>::t* twf, const T* in,
-                        T* out, cudaStream_t s) {
+static int prolong_pass(int a, int PC, const int dims[3], const typename C2<T>::t* twc,
+                        const typename C2<T>::t* twf, const T* in, T* out, cudaStream_t s) {
   switch (PC) {
-    case 8: return launch_prolong_pass<T, 8>(a, dims, twf, in, out, s);
-    case 16: return launch_prolong_pass<T, 16>(a, dims, twf, in, out, s);
-    case 32: return launch_prolong_pass<T, 32>(a, dims, twf, in, out, s);
-    case 64: return launch_prolong_pass<T, 64>(a, dims, twf, in, out, s);
-    case 128: return launch_prolong_pass<T, 128>(a, dims, twf, in, out, s);
-    case 256: return launch_prolong_pass<T, 256>(a, dims, twf, in, out, s);
-    case 512: return launch_prolong_pass<T, 512>(a, dims, twf, in, out, s);
+    case 8: return launch_prolong_pass<T, 8>(a, dims, twc, twf, in, out, s);
+    case 16: return launch_prolong_pass<T, 16>(a, dims, twc, twf, in, out, s);
+    case 32: return launch_prolong_pass<T, 32>(a, dims, twc, twf, in, out, s);
+    case 64: return launch_prolong_pass<T, 64>(a, dims, twc, twf, in, out, s);
+    case 128: return launch_prolong_pass<T, 128>(a, dims, twc, twf, in, out, s);
+    case 256: return launch_prolong_pass<T, 256>(a, dims, twc, twf, in, out, s);
     default:
-      set_error("prolongation needs coarse N a power of two in [4, 256]");
+      set_error("prolongation needs coarse N a power of two in [4, 128]");
       return CHEB_ERR_UNSUPPORTED;
   }
 }
@@ -178,7 +177,7 @@ int check_prolong_pair(const cheb_plan_s* c, const cheb_plan_s* f) {
     if (f->n[a] - 1 != 2 * (c->n[a] - 1)) { set_error("fine N must be twice the coarse N"); return CHEB_ERR_ARG; }
     if (c->lo[a] != f->lo[a] || c->hi[a] != f->hi[a]) { set_error("plans must share the box"); return CHEB_ERR_ARG; }
     if (!f->ax[a].transform_ok || !c->ax[a].transform_ok) {
-      set_error("prolongation needs coarse and fine N powers of two (4 <= N, fine N <= 512)");
+      set_error("prolongation needs coarse and fine N powers of two (4 <= N, fine N <= 256)");
       return CHEB_ERR_UNSUPPORTED;
     }
   }
@@ -193,7 +192,9 @@ int launch_prolong(const cheb_plan_s* c, const cheb_plan_s* f, const T* uc, T* u
   int st;
   for (int a = 0; a < c->dim; ++a) {
     T* dst = (a == c->dim - 1) ? uf : (a % 2 == 0 ? s1 : s2);
-    if ((st = prolong_pass<T>(a, 2 * (c->n[a] - 1), dims, twf_of<T>(f->ax[a]), src, dst, s))) return st;
+    if ((st = prolong_pass<T>(a, 2 * (c->n[a] - 1), dims, twf_of<T>(c->ax[a]), twf_of<T>(f->ax[a]), src,
+                              dst, s)))
+      return st;
     dims[a] = f->n[a];
     src = dst;
   }

@@ -11,6 +11,7 @@
 //   v_{j+1} = w / ||w||
 // The Hessenberg least-squares problem (Givens rotations) is solved on the
 // host in FP64 after one stream synchronisation per step.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -44,6 +45,7 @@ struct Workspace {
   KrylovBufs<float> k32;
   double* r64 = nullptr;      // FP64 residual
   double* pro[3] = {nullptr, nullptr, nullptr};  // prolongation scratch (2) + prolonged copy
+  double* adj[3] = {nullptr, nullptr, nullptr};  // gradient accumulation temporaries
   Fdm fdm;
 };
 
@@ -63,7 +65,7 @@ void free_workspace(cheb_plan_s* p) {
   cudaFree(w->rs.part); cudaFree(w->rs.counter); cudaFree(w->dscal); cudaFreeHost(w->hscal);
   free_bufs(w->k64); free_bufs(w->k32);
   cudaFree(w->r64);
-  for (int i = 0; i < 3; ++i) cudaFree(w->pro[i]);
+  for (int i = 0; i < 3; ++i) { cudaFree(w->pro[i]); cudaFree(w->adj[i]); }
   fdm_free(w->fdm);
   delete w;
   p->ws = nullptr;
@@ -118,6 +120,7 @@ static int sync_read(Workspace& w, int cnt, cudaStream_t s) {
 struct LgOpts {
   int m = 30, k = 3, maxiter = 1000;
   bool reorth = false;
+  bool transpose = false;  // solve with A^T and M^{-T} (adjoint)
   int precond = CHEB_PRECOND_FDM;
   double kref = 1.0;
   double tol_abs = 0.0;  // stop when ||c - B x|| <= tol_abs
@@ -139,11 +142,13 @@ static int op_B(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, const
                 cudaStream_t s) {
   int st;
   prof_begin(Cat<T>::apply, s);
-  st = launch_apply<T>(p, K, v, o.precond == CHEB_PRECOND_FDM ? tmp : out, s);
+  T* dst = o.precond == CHEB_PRECOND_FDM ? tmp : out;
+  st = o.transpose ? launch_adjoint_apply<T>(p, K, v, dst, s) : launch_apply<T>(p, K, v, dst, s);
   prof_end(Cat<T>::apply, s);
   if (st || o.precond != CHEB_PRECOND_FDM) return st;
   prof_begin(Cat<T>::prec, s);
-  st = fdm_apply<T>(p, w.fdm, o.kref, tmp, out, s);
+  st = o.transpose ? fdm_apply_t<T>(p, w.fdm, o.kref, tmp, out, s)
+                   : fdm_apply<T>(p, w.fdm, o.kref, tmp, out, s);
   prof_end(Cat<T>::prec, s);
   return st;
 }
@@ -331,8 +336,14 @@ static double norm2_t(Workspace& w, const T* x, cudaStream_t s, int* st) {
   return std::sqrt(w.hscal[0]);
 }
 
+template <typename T>
+static int precond(cheb_plan_s* p, Workspace& w, const LgOpts& lo, const T* r, T* z, cudaStream_t s) {
+  if (lo.precond != CHEB_PRECOND_FDM) return k_scale<T>(z, r, 1.0, w.n, s);
+  return lo.transpose ? fdm_apply_t<T>(p, w.fdm, lo.kref, r, z, s) : fdm_apply<T>(p, w.fdm, lo.kref, r, z, s);
+}
+
 static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* u,
-                      const cheb_solve_opts& o, cheb_solve_info& info) {
+                      const cheb_solve_opts& o, cheb_solve_info& info, bool transpose = false) {
   const double t0 = now_s();
   cudaStream_t s = p->stream;
   int st;
@@ -350,6 +361,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   lo.k = o.augment;
   lo.reorth = o.reorth != 0;
   lo.precond = o.precond;
+  lo.transpose = transpose;
   if (o.precond == CHEB_PRECOND_FDM) {
     if ((st = fdm_setup(p, w.fdm))) return st;
     if (o.kref > 0) lo.kref = o.kref;
@@ -365,9 +377,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   if (o.mode == CHEB_SOLVE_FP64) {
     if ((st = ensure_bufs<double>(w, lo.m + lo.k + 1, std::max(1, lo.k)))) return st;
     KrylovBufs<double>& B = w.k64;
-    if (o.precond == CHEB_PRECOND_FDM) {
-      if ((st = fdm_apply<double>(p, w.fdm, lo.kref, b, B.c, s))) return st;
-    } else if ((st = k_scale<double>(B.c, b, 1.0, n, s))) return st;
+    if ((st = precond<double>(p, w, lo, b, B.c, s))) return st;
     nb = norm2_dev(w, B.c, s, &st);
     if (st) return st;
     if (nb == 0.0) {
@@ -403,9 +413,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
       return CHEB_OK;
     }
     if ((st = k_cast_scale<float, double>(B.tmp, b, 1.0 / sb, n, s))) return st;
-    if (o.precond == CHEB_PRECOND_FDM) {
-      if ((st = fdm_apply<float>(p, w.fdm, lo.kref, B.tmp, B.c, s))) return st;
-    } else if ((st = k_scale<float>(B.c, B.tmp, 1.0, n, s))) return st;
+    if ((st = precond<float>(p, w, lo, B.tmp, B.c, s))) return st;
     nb = sb * norm2_t<float>(w, B.c, s, &st);
     if (st) return st;
   }
@@ -413,7 +421,9 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   double eta = 1.0;
   for (int it = 0; it <= o.max_refinements; ++it) {
     // r64 = b - A u (FP64)
-    if ((st = launch_apply<double>(p, K, u, w.r64, s))) return st;
+    if ((st = transpose ? launch_adjoint_apply<double>(p, K, u, w.r64, s)
+                        : launch_apply<double>(p, K, u, w.r64, s)))
+      return st;
     info.applies_fp64++;
     if ((st = k_residual<double>(w.r64, b, n, s))) return st;
     const double sr = norm2_dev(w, w.r64, s, &st);
@@ -421,9 +431,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     if (!std::isfinite(sr)) { set_error("non-finite residual"); return CHEB_ERR_NONFINITE; }
     if (sr == 0.0) { eta = 0.0; rc = CHEB_OK; break; }
     if ((st = k_cast_scale<float, double>(B.tmp, w.r64, 1.0 / sr, n, s))) return st;
-    if (o.precond == CHEB_PRECOND_FDM) {
-      if ((st = fdm_apply<float>(p, w.fdm, lo.kref, B.tmp, B.c, s))) return st;
-    } else if ((st = k_scale<float>(B.c, B.tmp, 1.0, n, s))) return st;
+    if ((st = precond<float>(p, w, lo, B.tmp, B.c, s))) return st;
     const double cn = norm2_t<float>(w, B.c, s, &st);
     if (st) return st;
     eta = sr * cn / nb;
@@ -448,6 +456,48 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   info.seconds = now_s() - t0;
   info.status = rc;
   return rc;
+}
+
+// dJdK += sum_a (D_a^T P_int lam) * (D_a u): the derivative of -lam^T A(K) u
+// with respect to K_p, since K enters A only through the interior rows
+// -sum_a D_a diag(K) D_a.
+__global__ void mask_interior_kernel(Geom g, const double* __restrict__ x, double* __restrict__ y) {
+  const size_t tot = (size_t)g.n[0] * g.n[1] * g.n[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((size_t)g.n[0] * g.n[1]));
+    bool b = (i == 0 || i == g.n[0] - 1);
+    if (g.dim > 1) b = b || j == 0 || j == g.n[1] - 1;
+    if (g.dim > 2) b = b || k == 0 || k == g.n[2] - 1;
+    y[c] = b ? 0.0 : x[c];
+  }
+}
+
+__global__ void fma_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ y,
+                           size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    y[c] += a[c] * b[c];
+}
+
+static int grad_K_accumulate(cheb_plan_s* p, const double* u, const double* lam, double* dJdK) {
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  Workspace& w = *p->ws;
+  const size_t n = w.n;
+  if (!w.adj[0])
+    for (int i = 0; i < 3; ++i) CHEB_CUDA(cudaMalloc(&w.adj[i], sizeof(double) * n));
+  cudaStream_t s = p->stream;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+  mask_interior_kernel<<<blocks, 256, 0, s>>>(p->geom(), lam, w.adj[0]);
+  CHEB_LAUNCH_CHECK("mask_interior_kernel");
+  for (int a = 0; a < p->dim; ++a) {
+    if ((st = launch_pass<double>(p, a, kDerivT, nullptr, w.adj[0], w.adj[1], s))) return st;
+    if ((st = launch_pass<double>(p, a, kDeriv, nullptr, u, w.adj[2], s))) return st;
+    fma_kernel<<<blocks, 256, 0, s>>>(w.adj[1], w.adj[2], dJdK, n);
+    CHEB_LAUNCH_CHECK("fma_kernel");
+  }
+  return CHEB_OK;
 }
 
 }  // namespace cheb
@@ -542,6 +592,35 @@ int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const
       if (l > 0 && (st = cheb_rel_diff(p, u[l], p->ws->pro[2], &e_ref[l]))) return st;
     }
   }
+  return rc;
+}
+
+int cheb_precond_apply_t(cheb_plan p, int prec, double kref, const void* y, void* z) {
+  if (!p || !y || !z || !(kref > 0)) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  if ((st = fdm_setup(p, p->ws->fdm))) return st;
+  if (prec == CHEB_FP64) return fdm_apply_t<double>(p, p->ws->fdm, kref, (const double*)y, (double*)z, p->stream);
+  if (prec == CHEB_FP32) return fdm_apply_t<float>(p, p->ws->fdm, kref, (const float*)y, (float*)z, p->stream);
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+int cheb_adjoint_solve(cheb_plan p, const double* K, const double* u, const double* dJdu,
+                       const cheb_solve_opts* opts, double* lambda, double* dJdK,
+                       cheb_solve_info* info) {
+  if (!p || !K || !dJdu || !lambda) { set_error("null argument"); return CHEB_ERR_ARG; }
+  if (dJdK && !u) { set_error("dJdK needs the forward solution u"); return CHEB_ERR_ARG; }
+  cheb_solve_opts o;
+  if (opts) o = *opts;
+  else default_opts(o);
+  cheb_solve_info tmp;
+  std::memset(&tmp, 0, sizeof(tmp));
+  int rc = solve_impl(p, K, dJdu, lambda, o, tmp, true);
+  if (info) *info = tmp;
+  if (rc < 0 || !dJdK) return rc;
+  int st;
+  if ((st = grad_K_accumulate(p, u, lambda, dJdK))) return st;
   return rc;
 }
 
