@@ -180,6 +180,32 @@ void cheb_solve_opts_default(cheb_solve_opts* opts);
 int cheb_solve(cheb_plan plan, const double* K, const double* b, double* u,
                const cheb_solve_opts* opts, cheb_solve_info* info);
 
+/* Picard iteration for K = K0 (1 + beta |grad u|^2) (Sec. 2.3, Picard:
+ * the nonlinearity is evaluated at the previous iterate): repeat
+ * K^m = K0 (1 + beta |grad u^m|^2) (gradients by line passes, FP64), solve
+ * A(K^m) u* = b warm-started from u^m (cheb_solve with opts) and relax
+ * u^{m+1} = omega u* + (1 - omega) u^m (0 < omega <= 1; omega = 1 is the
+ * plain iteration), until ||u^{m+1} - u^m|| / ||u^{m+1}|| <= tol or maxit.  u: FP64
+ * device field, in: initial guess, out: last iterate.  info sums the inner
+ * solves; picard_iters / picard_delta (nullable) receive the outer count and
+ * the last relative change.  Returns CHEB_ERR_NOT_CONVERGED at maxit. */
+int cheb_picard_solve(cheb_plan plan, const double* K0, const double* b, double* u, double beta,
+                      double omega, double tol, int maxit, const cheb_solve_opts* opts,
+                      cheb_solve_info* info, int* picard_iters, double* picard_delta);
+
+/* Batches of independent instances (each its own plan, any sizes), solved
+ * concurrently: one host thread per instance orders its work on its plan's
+ * stream (plans on the legacy NULL stream get a private stream for the
+ * call).  Arrays have `count` entries; infos / picard_iters may be NULL.
+ * Returns the most severe status; the first error message is kept. */
+int cheb_solve_batched(int count, const cheb_plan* plans, const double* const* K,
+                       const double* const* b, double* const* u, const cheb_solve_opts* opts,
+                       cheb_solve_info* infos);
+int cheb_picard_batched(int count, const cheb_plan* plans, const double* const* K0,
+                        const double* const* b, double* const* u, double beta, double omega,
+                        double tol, int maxit, const cheb_solve_opts* opts,
+                        cheb_solve_info* infos, int* picard_iters);
+
 /* Discrete adjoint solve: lambda = A^{-T} dJdu with A = A(K) as in
  * cheb_apply (LGMRES on A^T, preconditioned by M^{-T}; same options and
  * modes as cheb_solve).  lambda: FP64 device field, in: initial guess, out:

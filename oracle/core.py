@@ -459,15 +459,22 @@ def picard_conductivity(K0: np.ndarray, u: np.ndarray, grid: Grid, beta: float =
 
 
 def picard_solve(K0: np.ndarray, b: np.ndarray, grid: Grid, tol: float = 1e-11,
-                 maxit: int = 50, beta: float = 0.5, u0=None, lin_rtol: float = 1e-13):
-    """u^{m+1} solves A(K(u^m)) u^{m+1} = b (the nonlinearity is frozen at the
-    previous iterate, Sec. 2.3 Picard iteration); stops when
-    ||u^{m+1} - u^m|| / ||u^{m+1}|| <= tol."""
+                 maxit: int = 50, beta: float = 0.5, u0=None, lin_rtol: float = 1e-13,
+                 omega: float = 1.0):
+    """Picard iteration with the nonlinearity frozen at the previous iterate
+    (Sec. 2.3 Picard iteration): u* solves A(K(u^m)) u* = b and
+    u^{m+1} = (1 - omega) u^m + omega u* (omega = 1 is the plain iteration);
+    stops when ||u^{m+1} - u^m|| / ||u^{m+1}|| <= tol."""
     u = np.zeros(grid.shape) if u0 is None else np.array(u0, float)
     hist = []
     for it in range(1, maxit + 1):
         K = picard_conductivity(K0, u, grid, beta)
-        un, _ = solve(K, b, grid, x0=u, rtol=lin_rtol)
+        if grid.size <= 4096:
+            un, _ = solve(K, b, grid, x0=u, rtol=lin_rtol)
+        else:
+            from .precond import solve_preconditioned
+            un, _ = solve_preconditioned(K, b, grid, x0=u, rtol=lin_rtol)
+        un = (1.0 - omega) * u + omega * un
         d = np.linalg.norm(un - u) / max(np.linalg.norm(un), 1e-300)
         hist.append(d)
         u = un

@@ -190,6 +190,29 @@ class Plan:
             raise ChebError(st, "cheb_solve")
         return u, d
 
+    def picard_solve(self, K0: torch.Tensor, b: torch.Tensor, u: torch.Tensor | None = None,
+                     beta: float = 0.5, tol: float = 1e-9, maxit: int = 30, omega: float = 1.0,
+                     check_status: bool = True, **opts):
+        """Picard iteration for K = K0 (1 + beta |grad u|^2), relaxation omega
+        (``cheb_picard_solve``).
+        Returns (u, info, picard_iters, last relative change)."""
+        K0 = self._field(K0, "K0", torch.float64)
+        b = self._field(b, "b", torch.float64)
+        if u is None:
+            u = torch.zeros(self.shape, dtype=torch.float64, device=b.device)
+        u = self._field(u, "u", torch.float64)
+        o = solve_opts(**opts)
+        info = SolveInfo()
+        its, dlt = C.c_int(), C.c_double()
+        self._sync_stream()
+        st = lib.cheb_picard_solve(self._h, _vp(K0), _vp(b), _vp(u), float(beta), float(omega),
+                                   float(tol), int(maxit), C.byref(o), C.byref(info), C.byref(its),
+                                   C.byref(dlt))
+        check(st, "cheb_picard_solve")
+        if check_status and st != 0:
+            raise ChebError(st, "cheb_picard_solve")
+        return u, info.as_dict(), its.value, dlt.value
+
     def adjoint_solve(self, K: torch.Tensor, dJdu: torch.Tensor, u: torch.Tensor | None = None,
                       lam: torch.Tensor | None = None, dJdK: torch.Tensor | None = None,
                       check_status: bool = True, **opts):
@@ -278,6 +301,49 @@ def solve_hierarchy(plans, K, b, u0=None, check_status: bool = True, **opts):
     if check_status and st != 0:
         raise ChebError(st, "cheb_solve_hierarchy")
     return us, [i.as_dict() for i in infos], list(eref)
+
+
+def _batch_args(plans, A, b, u):
+    L = len(plans)
+    for i, p in enumerate(plans):
+        p._field(A[i], "K", torch.float64)
+        p._field(b[i], "b", torch.float64)
+    if u is None:
+        u = [torch.zeros(p.shape, dtype=torch.float64, device="cuda") for p in plans]
+    hp = (C.c_void_p * L)(*[p.handle.value for p in plans])
+    Ap = (C.c_void_p * L)(*[t.data_ptr() for t in A])
+    bp = (C.c_void_p * L)(*[t.data_ptr() for t in b])
+    up = (C.c_void_p * L)(*[t.data_ptr() for t in u])
+    return L, hp, Ap, bp, up, u
+
+
+def solve_batched(plans, K, b, u=None, check_status: bool = True, **opts):
+    """Independent solves run concurrently (``cheb_solve_batched``).
+    Returns (solutions, infos)."""
+    torch.cuda.synchronize()
+    L, hp, Kp, bp, up, u = _batch_args(plans, K, b, u)
+    infos = (SolveInfo * L)()
+    st = lib.cheb_solve_batched(L, hp, Kp, bp, up, C.byref(solve_opts(**opts)), infos)
+    check(st, "cheb_solve_batched")
+    if check_status and st != 0:
+        raise ChebError(st, "cheb_solve_batched")
+    return u, [i.as_dict() for i in infos]
+
+
+def picard_batched(plans, K0, b, u=None, beta: float = 0.5, tol: float = 1e-9, maxit: int = 30,
+                   omega: float = 1.0, check_status: bool = True, **opts):
+    """Independent Picard solves run concurrently (``cheb_picard_batched``).
+    Returns (solutions, infos, picard iteration counts)."""
+    torch.cuda.synchronize()
+    L, hp, Kp, bp, up, u = _batch_args(plans, K0, b, u)
+    infos = (SolveInfo * L)()
+    its = (C.c_int * L)()
+    st = lib.cheb_picard_batched(L, hp, Kp, bp, up, float(beta), float(omega), float(tol), int(maxit),
+                                 C.byref(solve_opts(**opts)), infos, its)
+    check(st, "cheb_picard_batched")
+    if check_status and st != 0:
+        raise ChebError(st, "cheb_picard_batched")
+    return u, [i.as_dict() for i in infos], list(its)
 
 
 # thin same-name wrappers of the C entry points -------------------------------

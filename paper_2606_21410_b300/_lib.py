@@ -78,6 +78,13 @@ _SIGS = {
     "cheb_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
     "cheb_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "cheb_precond_apply": (i32, [vp, i32, C.c_double, vp, vp]),
+    "cheb_picard_solve": (i32, [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, i32,
+                                C.POINTER(SolveOpts), C.POINTER(SolveInfo), i32p, f64p]),
+    "cheb_solve_batched": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                 C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
+    "cheb_picard_batched": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                  C.c_double, C.c_double, C.c_double, i32, C.POINTER(SolveOpts),
+                                  C.POINTER(SolveInfo), i32p]),
     "cheb_precond_apply_t": (i32, [vp, i32, C.c_double, vp, vp]),
     "cheb_adjoint_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), vp, vp, C.POINTER(SolveInfo)]),
     "cheb_prolong": (i32, [vp, vp, i32, vp, vp]),

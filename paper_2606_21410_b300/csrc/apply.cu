@@ -18,6 +18,8 @@
 // Dense route: f' = D f with D staged in shared memory.
 #include <cstdio>
 
+#include <atomic>
+
 #include "device.cuh"
 
 namespace cheb {
@@ -576,7 +578,7 @@ template <> AxisK<float> axis_k<float>(const AxisTables& t) {
 template <typename T, int ROUTE, int P, int CM>
 static int launch_kernel(const Geom& g, int axis, int kind, const AxisK<T>& ak, const T* K,
                          const T* u, T* out, cudaStream_t s, int nblocks) {
-  static size_t configured = 0;  // per instantiation
+  static std::atomic<size_t> configured{0};  // per instantiation
   if constexpr (ROUTE == CHEB_ROUTE_TRANSFORM) {
     auto kern = tf_pass_kernel<T, P, CM>;
     constexpr size_t smem = tf_smem_bytes<T, P>();

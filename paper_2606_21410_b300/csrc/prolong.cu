@@ -11,6 +11,8 @@
 #include <mutex>
 #include <string>
 
+#include <atomic>
+
 #include "device.cuh"
 #include "fdm.h"
 #include "krylov.h"
@@ -138,7 +140,7 @@ static int launch_prolong_pass(int a, const int dims[3], const typename C2<T>::t
                                const typename C2<T>::t* twf, const T* in, T* out, cudaStream_t s) {
   auto kern = prolong_pass_kernel<T, PC>;
   const size_t smem = prolong_smem<T, PC>();
-  static size_t configured = 0;
+  static std::atomic<size_t> configured{0};
   if (smem > configured) {
     CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;

@@ -15,6 +15,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "fdm.h"
@@ -45,7 +47,9 @@ struct Workspace {
   KrylovBufs<float> k32;
   double* r64 = nullptr;      // FP64 residual
   double* pro[3] = {nullptr, nullptr, nullptr};  // prolongation scratch (2) + prolonged copy
-  double* adj[3] = {nullptr, nullptr, nullptr};  // gradient accumulation temporaries
+  double* adj[3] = {nullptr, nullptr, nullptr};  // gradient accumulation / Picard temporaries
+  double* picK = nullptr;                         // Picard conductivity
+  double* picU = nullptr;                         // Picard previous iterate
   Fdm fdm;
 };
 
@@ -66,6 +70,8 @@ void free_workspace(cheb_plan_s* p) {
   free_bufs(w->k64); free_bufs(w->k32);
   cudaFree(w->r64);
   for (int i = 0; i < 3; ++i) { cudaFree(w->pro[i]); cudaFree(w->adj[i]); }
+  cudaFree(w->picK);
+  cudaFree(w->picU);
   fdm_free(w->fdm);
   delete w;
   p->ws = nullptr;
@@ -500,6 +506,91 @@ static int grad_K_accumulate(cheb_plan_s* p, const double* u, const double* lam,
   return CHEB_OK;
 }
 
+// K = K0 (1 + beta |grad u|^2) from the three gradient components g0, g1, g2
+__global__ void picard_k_kernel(const double* __restrict__ K0, const double* __restrict__ g0,
+                                const double* __restrict__ g1, const double* __restrict__ g2, int dim,
+                                double beta, double* __restrict__ K, size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    double s = g0[c] * g0[c];
+    if (dim > 1) s += g1[c] * g1[c];
+    if (dim > 2) s += g2[c] * g2[c];
+    K[c] = K0[c] * (1.0 + beta * s);
+  }
+}
+
+static int picard_conductivity(cheb_plan_s* p, const double* K0, const double* u, double beta, double* K) {
+  Workspace& w = *p->ws;
+  const size_t n = w.n;
+  int st;
+  for (int a = 0; a < p->dim; ++a)
+    if ((st = launch_pass<double>(p, a, kDeriv, nullptr, u, w.adj[a], p->stream))) return st;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+  picard_k_kernel<<<blocks, 256, 0, p->stream>>>(K0, w.adj[0], w.adj[1], w.adj[2], p->dim, beta, K, n);
+  CHEB_LAUNCH_CHECK("picard_k_kernel");
+  return CHEB_OK;
+}
+
+// Picard iteration (Sec. 2.3, Picard): the nonlinearity is frozen at the
+// previous iterate, K^m = K0 (1 + beta |grad u^m|^2), the linear system
+// A(K^m) u* = b is solved warm-started from u^m, and u^{m+1} = omega u* +
+// (1 - omega) u^m (omega = 1: the plain iteration); stop when
+// ||u^{m+1} - u^m|| / ||u^{m+1}|| <= tol or after maxit outer steps.
+__global__ void relax_kernel(double* __restrict__ u, const double* __restrict__ uprev, double omega,
+                             size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    u[c] = omega * u[c] + (1.0 - omega) * uprev[c];
+}
+
+static int picard_impl(cheb_plan_s* p, const double* K0, const double* b, double* u, double beta,
+                       double omega, double tol, int maxit, const cheb_solve_opts& o,
+                       cheb_solve_info& info, int* iters, double* delta) {
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  Workspace& w = *p->ws;
+  const size_t n = w.n;
+  if (!w.adj[0])
+    for (int i = 0; i < 3; ++i) CHEB_CUDA(cudaMalloc(&w.adj[i], sizeof(double) * n));
+  if (!w.picK) {
+    CHEB_CUDA(cudaMalloc(&w.picK, sizeof(double) * n));
+    CHEB_CUDA(cudaMalloc(&w.picU, sizeof(double) * n));
+  }
+  int rc = CHEB_ERR_NOT_CONVERGED;
+  double d = 1.0;
+  int m = 0;
+  cheb_solve_info tot;
+  std::memset(&tot, 0, sizeof(tot));
+  const double t0 = now_s();
+  for (m = 1; m <= maxit; ++m) {
+    if ((st = picard_conductivity(p, K0, u, beta, w.picK))) return st;
+    CHEB_CUDA(cudaMemcpyAsync(w.picU, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, p->stream));
+    cheb_solve_info li;
+    std::memset(&li, 0, sizeof(li));
+    int r = solve_impl(p, w.picK, b, u, o, li);
+    tot.iterations += li.iterations;
+    tot.cycles += li.cycles;
+    tot.refinements += li.refinements;
+    tot.applies_fp64 += li.applies_fp64;
+    tot.applies_fp32 += li.applies_fp32;
+    tot.rel_residual = li.rel_residual;
+    tot.kref = li.kref;
+    if (r < 0) return r;
+    if (omega != 1.0) {
+      const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+      relax_kernel<<<blocks, 256, 0, p->stream>>>(u, w.picU, omega, n);
+      CHEB_LAUNCH_CHECK("relax_kernel");
+    }
+    if ((st = cheb_rel_diff(p, u, w.picU, &d))) return st;
+    if (o.verbose) fprintf(stderr, "[cheb] picard %d: |du|/|u| = %.3e (%d its)\n", m, d, li.iterations);
+    if (d <= tol) { rc = CHEB_OK; break; }
+  }
+  tot.seconds = now_s() - t0;
+  tot.status = rc;
+  info = tot;
+  if (iters) *iters = std::min(m, maxit);
+  if (delta) *delta = d;
+  return rc;
+}
+
 }  // namespace cheb
 
 using namespace cheb;
@@ -622,6 +713,84 @@ int cheb_adjoint_solve(cheb_plan p, const double* K, const double* u, const doub
   int st;
   if ((st = grad_K_accumulate(p, u, lambda, dJdK))) return st;
   return rc;
+}
+
+int cheb_picard_solve(cheb_plan p, const double* K0, const double* b, double* u, double beta,
+                      double omega, double tol, int maxit, const cheb_solve_opts* opts,
+                      cheb_solve_info* info, int* picard_iters, double* picard_delta) {
+  if (!p || !K0 || !b || !u || maxit < 1 || !(tol > 0) || !(omega > 0 && omega <= 1)) {
+    set_error("bad argument (need maxit >= 1, tol > 0, 0 < omega <= 1)");
+    return CHEB_ERR_ARG;
+  }
+  cheb_solve_opts o;
+  if (opts) o = *opts;
+  else default_opts(o);
+  cheb_solve_info tmp;
+  std::memset(&tmp, 0, sizeof(tmp));
+  int rc = picard_impl(p, K0, b, u, beta, omega, tol, maxit, o, tmp, picard_iters, picard_delta);
+  if (info) *info = tmp;
+  return rc;
+}
+
+// Independent instances solved concurrently: one host thread per instance,
+// each ordering its work on its plan's stream (a private non-blocking
+// stream is created for plans on the legacy stream).  K0 and beta select the
+// Picard form (K0 != NULL), otherwise K is the fixed conductivity.
+static int batched(int count, const cheb_plan* plans, const double* const* K, const double* const* b,
+                   double* const* u, const cheb_solve_opts* opts, cheb_solve_info* infos, double beta,
+                   double omega, double tol, int maxit, int* iters, bool picard) {
+  if (count < 1 || !plans || !K || !b || !u) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  int dev = 0;
+  CHEB_CUDA(cudaGetDevice(&dev));
+  std::vector<int> rcs(count, CHEB_OK);
+  std::vector<std::string> errs(count);
+  std::vector<std::thread> th;
+  for (int i = 0; i < count; ++i) {
+    th.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      cheb_plan p = plans[i];
+      cudaStream_t own = nullptr, saved = p->stream;
+      if (!saved) {
+        cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking);
+        p->stream = own;
+      }
+      cheb_solve_info inf;
+      std::memset(&inf, 0, sizeof(inf));
+      int rc;
+      if (picard)
+        rc = cheb_picard_solve(p, K[i], b[i], u[i], beta, omega, tol, maxit, opts, &inf,
+                               iters ? &iters[i] : nullptr, nullptr);
+      else
+        rc = cheb_solve(p, K[i], b[i], u[i], opts, &inf);
+      if (rc < 0) errs[i] = cheb_last_error();
+      if (own) {
+        cudaStreamSynchronize(own);
+        p->stream = saved;
+        cudaStreamDestroy(own);
+      }
+      rcs[i] = rc;
+      if (infos) infos[i] = inf;
+    });
+  }
+  for (auto& t : th) t.join();
+  int worst = CHEB_OK;
+  for (int i = 0; i < count; ++i) {
+    if (rcs[i] < 0 && (worst >= 0 || rcs[i] < worst)) { worst = rcs[i]; set_error(errs[i]); }
+    else if (worst == CHEB_OK && rcs[i] > 0) worst = rcs[i];
+  }
+  return worst;
+}
+
+int cheb_solve_batched(int count, const cheb_plan* plans, const double* const* K, const double* const* b,
+                       double* const* u, const cheb_solve_opts* opts, cheb_solve_info* infos) {
+  return batched(count, plans, K, b, u, opts, infos, 0.0, 1.0, 1.0, 1, nullptr, false);
+}
+
+int cheb_picard_batched(int count, const cheb_plan* plans, const double* const* K0,
+                        const double* const* b, double* const* u, double beta, double omega,
+                        double tol, int maxit, const cheb_solve_opts* opts, cheb_solve_info* infos,
+                        int* picard_iters) {
+  return batched(count, plans, K0, b, u, opts, infos, beta, omega, tol, maxit, picard_iters, true);
 }
 
 int cheb_precond_apply(cheb_plan p, int prec, double kref, const void* r, void* z) {
