@@ -85,10 +85,21 @@ int cheb_plan_create(cheb_plan* out, int dim, const int n[3], const double lo[3]
 int cheb_plan_destroy(cheb_plan plan);
 int cheb_plan_set_stream(cheb_plan plan, void* stream);
 
-/* Force the line-derivative route of one axis (CHEB_ROUTE_*); fails with
- * CHEB_ERR_UNSUPPORTED when the axis size does not allow it. */
+/* Force the line-derivative route of one axis (CHEB_ROUTE_*), both
+ * precisions; fails with CHEB_ERR_UNSUPPORTED when the axis size does not
+ * allow it.  get_route reports the FP64 route. */
 int cheb_plan_set_route(cheb_plan plan, int axis, int route);
 int cheb_plan_get_route(cheb_plan plan, int axis, int* route);
+
+/* Autotuner: for every active axis whose size allows both routes, time
+ * the operator line pass with the transform route and with the dense route
+ * (FP64 and FP32 separately, on the plan's grid and stream) and keep the
+ * faster.  cache_path (nullable) names a text file of earlier decisions,
+ * one line per (GPU name, axis size, precision); hits skip the timing and
+ * new decisions are appended.  routes_out[6] (nullable) receives the FP64
+ * routes of axes x, y, z then the FP32 routes.  Allocates three temporary
+ * fields when timing; synchronises the plan's stream. */
+int cheb_autotune(cheb_plan plan, const char* cache_path, int routes_out[6]);
 
 /* Host copy of the CGL coordinates of one axis (n[axis] doubles, node 0 =
  * hi end).  Callers sample f, K and face data at these points. */
@@ -150,6 +161,10 @@ typedef struct cheb_solve_opts {
   int precond;         /* CHEB_PRECOND_* */
   double kref;         /* FDM conductivity; <= 0: geometric mean of K */
   int verbose;         /* 1: progress lines on stderr */
+  int use_graph;       /* 1: Arnoldi cycles after a full-length cycle run as captured
+                          CUDA graphs with the Hessenberg / Givens update on the
+                          device (one host synchronisation per cycle instead of
+                          per step); graphs are cached per operator and shape */
 } cheb_solve_opts;
 
 typedef struct cheb_solve_info {
@@ -163,10 +178,12 @@ typedef struct cheb_solve_info {
   double rel_residual_inner; /* MIXED: last inner relative residual */
   double seconds;          /* wall time of the call */
   double kref;             /* FDM conductivity used */
+  int graph_captures;      /* Arnoldi-cycle graphs captured (use_graph) */
 } cheb_solve_info;
 
 /* Defaults: MIXED, rtol 1e-12, restart 30, augment 3, maxiter 2000,
- * inner_rtol 1e-5, inner_maxiter 400, max_refinements 30, FDM, kref auto. */
+ * inner_rtol 1e-4, inner_maxiter 400, max_refinements 30, FDM, kref auto,
+ * use_graph 0. */
 void cheb_solve_opts_default(cheb_solve_opts* opts);
 
 /* Solve A u = b (Alg. 2 with the Krylov solver LGMRES; boundary rows as in

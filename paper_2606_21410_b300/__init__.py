@@ -98,6 +98,16 @@ class Plan:
     def set_route(self, axis: int, route: int):
         check(lib.cheb_plan_set_route(self._h, axis, route), "cheb_plan_set_route")
 
+    def autotune(self, cache: str | None = None) -> dict:
+        """Pick the faster line-derivative route per axis and precision
+        (``cheb_autotune``); cache: optional decision file."""
+        out = (C.c_int * 6)()
+        self._sync_stream()
+        check(lib.cheb_autotune(self._h, cache.encode() if cache else None, out), "cheb_autotune")
+        names = {0: "transform", 1: "dense"}
+        return {"fp64": [names[out[a]] for a in range(self.dim)],
+                "fp32": [names[out[3 + a]] for a in range(self.dim)]}
+
     def route(self, axis: int) -> int:
         r = C.c_int()
         check(lib.cheb_plan_get_route(self._h, axis, C.byref(r)), "cheb_plan_get_route")

@@ -40,6 +40,7 @@ class SolveOpts(C.Structure):
         ("precond", i32),
         ("kref", C.c_double),
         ("verbose", i32),
+        ("use_graph", i32),
     ]
 
 
@@ -56,6 +57,7 @@ class SolveInfo(C.Structure):
         ("rel_residual_inner", C.c_double),
         ("seconds", C.c_double),
         ("kref", C.c_double),
+        ("graph_captures", i32),
     ]
 
     def as_dict(self):
@@ -69,6 +71,7 @@ _SIGS = {
     "cheb_plan_set_route": (i32, [vp, i32, i32]),
     "cheb_plan_get_route": (i32, [vp, i32, i32p]),
     "cheb_nodes": (i32, [vp, i32, f64p]),
+    "cheb_autotune": (i32, [vp, C.c_char_p, i32p]),
     "cheb_plan_size": (C.c_size_t, [vp]),
     "cheb_deriv": (i32, [vp, i32, i32, vp, vp]),
     "cheb_deriv_t": (i32, [vp, i32, i32, vp, vp]),

@@ -614,7 +614,8 @@ int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u
     nblocks = nbx * (axis == 1 ? g.n[2] : g.n[1]);
   }
   if (nblocks == 0) return CHEB_OK;
-  if (t.route == CHEB_ROUTE_DENSE)
+  const int route = sizeof(T) == 4 ? t.route32 : t.route;
+  if (route == CHEB_ROUTE_DENSE)
     return launch_kernel<T, CHEB_ROUTE_DENSE, 0, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
   switch (t.P) {
     case 8: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 8, 1>(g, axis, kind, ak, K, u, out, s, nblocks);

@@ -23,7 +23,8 @@ struct AxisTables {
   int N = 0;           // n - 1
   int P = 0;           // FFT length 2N (transform route), 0 otherwise
   double scale = 1.0;  // 2 / (hi - lo)
-  int route = CHEB_ROUTE_TRANSFORM;
+  int route = CHEB_ROUTE_TRANSFORM;    // FP64 passes
+  int route32 = CHEB_ROUTE_TRANSFORM;  // FP32 passes
   bool transform_ok = false;
   bool dense_ok = false;
   double2* tw64 = nullptr;
@@ -75,6 +76,8 @@ int cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 void count_launch();
+void add_launches(long long k);
+long long thread_launches();  // launches issued by the calling thread
 
 #define CHEB_LAUNCH_CHECK(what)                           \
   do {                                                    \

@@ -29,7 +29,13 @@ void free_workspace(cheb_plan_s* p);
 // launch counter and phase profiler
 // ---------------------------------------------------------------------------
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void add_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long thread_launches() { return t_launches; }
 
 namespace {
 struct ProfRec { int cat; cudaEvent_t a, b; };
@@ -63,8 +69,13 @@ void collect_locked() {
 }
 }  // namespace
 
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 void prof_begin(int cat, cudaStream_t s) {
-  if (!g_prof.on) return;
+  if (!g_prof.on || capturing(s)) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   cudaEvent_t e = take_event();
   cudaEventRecord(e, s);
@@ -72,7 +83,7 @@ void prof_begin(int cat, cudaStream_t s) {
 }
 
 void prof_end(int cat, cudaStream_t s) {
-  if (!g_prof.on) return;
+  if (!g_prof.on || capturing(s)) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof.open[cat]) return;
   cudaEvent_t e = take_event();
@@ -96,6 +107,7 @@ static int build_axis(cheb_plan_s* p, int a) {
   t.transform_ok = is_pow2(t.N) && t.N >= 4 && t.N <= kTransformMaxN;
   t.dense_ok = t.n <= kDenseMaxN;
   t.route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  t.route32 = t.route;
   if (t.transform_ok) {
     t.P = 2 * t.N;
     // per-stage twiddles of the warp FFT (radix 8, then 4 or 2):
@@ -246,6 +258,7 @@ int cheb_plan_set_route(cheb_plan p, int axis, int route) {
     set_error("unknown route"); return CHEB_ERR_ARG;
   }
   t.route = route;
+  t.route32 = route;
   return CHEB_OK;
 }
 

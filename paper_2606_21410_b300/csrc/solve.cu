@@ -25,6 +25,16 @@
 
 namespace cheb {
 
+// Captured Arnoldi cycles, one per cycle shape (number of Krylov steps).
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long nkernels = 0;  // kernel launches captured in the graph
+  int m_eff = -1;
+  const void* K = nullptr;
+  double kref = 0.0;
+  int precond = -1, reorth = -1, transpose = -1, m = -1, k = -1;
+};
+
 template <typename T>
 struct KrylovBufs {
   int nvec = 0;        // allocated basis vectors
@@ -36,6 +46,7 @@ struct KrylovBufs {
   T* x = nullptr;      // n (inner solution)
   T* c = nullptr;      // n (inner right-hand side)
   T* K = nullptr;      // n (conductivity in this precision)
+  CycleGraph graphs[kMaxVecs];
 };
 
 struct Workspace {
@@ -48,6 +59,11 @@ struct Workspace {
   double* r64 = nullptr;      // FP64 residual
   double* pro[3] = {nullptr, nullptr, nullptr};  // prolongation scratch (2) + prolonged copy
   double* adj[3] = {nullptr, nullptr, nullptr};  // gradient accumulation / Picard temporaries
+  double* dhess = nullptr;    // device Hessenberg / Givens state of graph cycles
+  double* hhess = nullptr;    // pinned mirror
+  int* dorder = nullptr;      // augmentation slot order (device) and pinned mirror
+  int* horder = nullptr;
+  cudaStream_t gstream = nullptr;  // private stream for graph capture
   double* picK = nullptr;                         // Picard conductivity
   double* picU = nullptr;                         // Picard previous iterate
   Fdm fdm;
@@ -60,6 +76,8 @@ template <> KrylovBufs<float>& bufs<float>(Workspace& w) { return w.k32; }
 template <typename T>
 static void free_bufs(KrylovBufs<T>& b) {
   cudaFree(b.V); cudaFree(b.Z); cudaFree(b.BZ); cudaFree(b.tmp); cudaFree(b.x); cudaFree(b.c); cudaFree(b.K);
+  for (auto& g : b.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   b = KrylovBufs<T>();
 }
 
@@ -72,6 +90,11 @@ void free_workspace(cheb_plan_s* p) {
   for (int i = 0; i < 3; ++i) { cudaFree(w->pro[i]); cudaFree(w->adj[i]); }
   cudaFree(w->picK);
   cudaFree(w->picU);
+  cudaFree(w->dhess);
+  cudaFreeHost(w->hhess);
+  cudaFree(w->dorder);
+  cudaFreeHost(w->horder);
+  if (w->gstream) cudaStreamDestroy(w->gstream);
   fdm_free(w->fdm);
   delete w;
   p->ws = nullptr;
@@ -127,13 +150,14 @@ struct LgOpts {
   int m = 30, k = 3, maxiter = 1000;
   bool reorth = false;
   bool transpose = false;  // solve with A^T and M^{-T} (adjoint)
+  bool use_graph = false;  // run Arnoldi cycles as captured CUDA graphs
   int precond = CHEB_PRECOND_FDM;
   double kref = 1.0;
   double tol_abs = 0.0;  // stop when ||c - B x|| <= tol_abs
 };
 
 struct LgStats {
-  int iterations = 0, cycles = 0, applies = 0;
+  int iterations = 0, cycles = 0, applies = 0, captures = 0;
   double resid = 0.0;  // last true preconditioned residual norm
   bool converged = false;
 };
@@ -159,6 +183,184 @@ static int op_B(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, const
   return st;
 }
 
+// ---------------------------------------------------------------------------
+// device-side Hessenberg update for graph-captured cycles.  Layout of the
+// FP64 block (nb = basis size): H[(nb+1) x nb] unrotated, R[(nb+1) x nb]
+// rotated, cs[nb], sn[nb], g[nb+1], res[nb] (|g_{j+1}| after step j).
+// ---------------------------------------------------------------------------
+struct HessLayout {
+  int nb;
+  __host__ __device__ size_t H() const { return 0; }
+  __host__ __device__ size_t R() const { return (size_t)(nb + 1) * nb; }
+  __host__ __device__ size_t cs() const { return 2 * (size_t)(nb + 1) * nb; }
+  __host__ __device__ size_t sn() const { return cs() + nb; }
+  __host__ __device__ size_t g() const { return sn() + nb; }
+  __host__ __device__ size_t res() const { return g() + nb + 1; }
+  __host__ __device__ size_t total() const { return res() + nb; }
+};
+
+// column j of H from the Gram-Schmidt coefficients of one pass
+__global__ void hcol_kernel(double* hess, HessLayout L, int j, int pass, const double* __restrict__ dv) {
+  double* H = hess + L.H();
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double v = dv[i];
+    H[(size_t)i * L.nb + j] = pass == 0 ? v : H[(size_t)i * L.nb + j] + v;
+  }
+}
+
+// H[j+1][j] = |w|, rotate column j with the earlier rotations, make rotation j,
+// update g and record |g_{j+1}|
+__global__ void givens_kernel(double* hess, HessLayout L, int j, const double* __restrict__ norm2) {
+  if (threadIdx.x != 0) return;
+  double* H = hess + L.H();
+  double* R = hess + L.R();
+  double* cs = hess + L.cs();
+  double* sn = hess + L.sn();
+  double* g = hess + L.g();
+  const int nb = L.nb;
+  const double hn = sqrt(fmax(0.0, *norm2));
+  H[(size_t)(j + 1) * nb + j] = hn;
+  for (int i = 0; i <= j + 1; ++i) R[(size_t)i * nb + j] = H[(size_t)i * nb + j];
+  for (int i = 0; i < j; ++i) {
+    const double a = R[(size_t)i * nb + j], b = R[(size_t)(i + 1) * nb + j];
+    R[(size_t)i * nb + j] = cs[i] * a + sn[i] * b;
+    R[(size_t)(i + 1) * nb + j] = -sn[i] * a + cs[i] * b;
+  }
+  const double a = R[(size_t)j * nb + j], b = R[(size_t)(j + 1) * nb + j];
+  const double den = hypot(a, b);
+  cs[j] = den > 0 ? a / den : 1.0;
+  sn[j] = den > 0 ? b / den : 0.0;
+  R[(size_t)j * nb + j] = den;
+  R[(size_t)(j + 1) * nb + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  hess[L.res() + j] = fabs(g[j + 1]);
+}
+
+// w = BZ[order[q]] (augmentation step q of a cycle)
+template <typename T>
+__global__ void copy_slot_kernel(T* __restrict__ w, const T* __restrict__ BZ, const int* __restrict__ order,
+                                 int q, size_t n) {
+  const T* src = BZ + (size_t)order[q] * n;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+    w[c] = src[c];
+}
+
+// One Arnoldi cycle as a CUDA graph: captured once per cycle shape and
+// operator (K, kref, options), replayed afterwards.  The host reads the
+// Hessenberg state once at the end and keeps the steps up to the first one
+// whose residual estimate meets the tolerance (later steps only extend the
+// basis and are ignored).
+template <typename T>
+static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, int m_eff, int naug,
+                       int next_slot, double beta, int steps_max, int nbasis,
+                       std::vector<double>& H, std::vector<double>& Hr, std::vector<double>& g,
+                       LgStats& stt, int& steps, cudaStream_t s) {
+  const size_t n = w.n;
+  KrylovBufs<T>& B = bufs<T>(w);
+  const int kk = o.k;
+  HessLayout L{nbasis};
+  if (!w.dhess) {
+    HessLayout Lmax{kMaxVecs};
+    CHEB_CUDA(cudaMalloc(&w.dhess, sizeof(double) * Lmax.total()));
+    CHEB_CUDA(cudaMallocHost(&w.hhess, sizeof(double) * Lmax.total()));
+    CHEB_CUDA(cudaMalloc(&w.dorder, sizeof(int) * kMaxVecs));
+    CHEB_CUDA(cudaMallocHost(&w.horder, sizeof(int) * kMaxVecs));
+  }
+  // per-cycle inputs: g = (beta, 0, ...), augmentation order (oldest first)
+  std::fill(w.hhess, w.hhess + L.total(), 0.0);
+  w.hhess[L.g()] = beta;
+  for (int q = 0; q < naug; ++q) w.horder[q] = (next_slot - naug + q + 4 * kk) % std::max(1, kk);
+  CHEB_CUDA(cudaMemcpyAsync(w.dhess, w.hhess, sizeof(double) * L.total(), cudaMemcpyHostToDevice, s));
+  CHEB_CUDA(cudaMemcpyAsync(w.dorder, w.horder, sizeof(int) * std::max(1, naug), cudaMemcpyHostToDevice, s));
+  CycleGraph& cg = B.graphs[m_eff];
+  const bool match = cg.exec && cg.m_eff == m_eff && cg.K == (const void*)K && cg.kref == o.kref &&
+                     cg.precond == o.precond && cg.reorth == (int)o.reorth && cg.transpose == (int)o.transpose &&
+                     cg.m == o.m && cg.k == o.k;
+  if (!match) {
+    if (cg.exec) { cudaGraphExecDestroy(cg.exec); cg.exec = nullptr; }
+    double* dv = w.dscal;
+    auto Vp = [&](int i) { return B.V + (size_t)i * n; };
+    // one uncaptured application first: lazy workspace allocation and kernel
+    // attributes happen outside the capture
+    {
+      int st0 = op_B<T>(p, w, o, K, Vp(0), Vp(1), B.tmp, s);
+      if (st0) return st0;
+      CHEB_CUDA(cudaStreamSynchronize(s));
+    }
+    // capture on a private stream (the legacy stream cannot be captured); the
+    // graph is launched on the plan's stream afterwards
+    if (!w.gstream) CHEB_CUDA(cudaStreamCreateWithFlags(&w.gstream, cudaStreamNonBlocking));
+    cudaStream_t cs = w.gstream;
+    const long long l0 = thread_launches();
+    CHEB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int st = CHEB_OK;
+    for (int j = 0; j < steps_max && st == CHEB_OK; ++j) {
+      T* wv = Vp(j + 1);
+      if (j < m_eff) {
+        st = op_B<T>(p, w, o, K, Vp(j), wv, B.tmp, cs);
+      } else {
+        copy_slot_kernel<T><<<(int)std::min<size_t>((n + 255) / 256, 148 * 8), 256, 0, cs>>>(wv, B.BZ, w.dorder,
+                                                                                              j - m_eff, n);
+        count_launch();
+      }
+      const T* src[kMaxVecs];
+      for (int i = 0; i <= j; ++i) src[i] = Vp(i);
+      for (int pass = 0; pass < (o.reorth ? 2 : 1) && st == CHEB_OK; ++pass) {
+        if ((st = k_mdot<T>(w.rs, src, j + 1, wv, n, false, dv, cs))) break;
+        if ((st = k_maxpy_dev<T>(w.rs, src, dv, -1.0, j + 1, 1.0, wv, n, dv + kMaxVecs + 1, cs))) break;
+        hcol_kernel<<<1, 64, 0, cs>>>(w.dhess, L, j, pass, dv);
+        count_launch();
+      }
+      if (st) break;
+      if ((st = k_scale_inv_norm<T>(wv, dv + kMaxVecs + 1, n, cs))) break;
+      givens_kernel<<<1, 32, 0, cs>>>(w.dhess, L, j, dv + kMaxVecs + 1);
+      count_launch();
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&cg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { cg.exec = nullptr; return cuda_fail(ce, "cudaGraphInstantiate"); }
+    cg.m_eff = m_eff; cg.K = K; cg.kref = o.kref; cg.precond = o.precond; cg.reorth = o.reorth;
+    cg.transpose = o.transpose; cg.m = o.m; cg.k = o.k;
+    cg.nkernels = thread_launches() - l0;
+    stt.captures++;
+  }
+  prof_begin(kProfOther, s);
+  CHEB_CUDA(cudaGraphLaunch(cg.exec, s));
+  prof_end(kProfOther, s);
+  add_launches(cg.nkernels);
+  CHEB_CUDA(cudaMemcpyAsync(w.hhess, w.dhess, sizeof(double) * L.total(), cudaMemcpyDeviceToHost, s));
+  CHEB_CUDA(cudaStreamSynchronize(s));
+  const double* hh = w.hhess;
+  steps = steps_max;
+  for (int j = 0; j < steps_max; ++j) {
+    const double r = hh[L.res() + j];
+    if (!std::isfinite(r) || r <= o.tol_abs || stt.iterations + j + 1 >= o.maxiter) { steps = j + 1; break; }
+  }
+  if (!std::isfinite(hh[L.res() + steps - 1])) { set_error("non-finite Arnoldi residual"); return CHEB_ERR_NONFINITE; }
+  stt.iterations += steps;
+  stt.applies += std::min(steps, m_eff);
+  for (size_t i = 0; i < (size_t)(nbasis + 1) * nbasis; ++i) {
+    H[i] = hh[L.H() + i];
+    Hr[i] = hh[L.R() + i];
+  }
+  for (int i = 0; i <= nbasis; ++i) g[i] = hh[L.g() + i];
+  // g must be the rotated right-hand side after `steps` rotations: recompute it
+  // from the rotations (later rotations only touch entries beyond `steps`)
+  std::fill(g.begin(), g.end(), 0.0);
+  g[0] = beta;
+  for (int j = 0; j < steps; ++j) {
+    const double c = hh[L.cs() + j], sn = hh[L.sn() + j];
+    g[j + 1] = -sn * g[j];
+    g[j] = c * g[j];
+  }
+  return CHEB_OK;
+}
+
 // LGMRES on B x = c (B = M^{-1} A), x in/out.  Returns CHEB_OK when
 // converged, CHEB_ERR_NOT_CONVERGED at maxiter, or an error.
 template <typename T>
@@ -179,6 +381,7 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
   double* dv = w.dscal;
   double* hv = w.hscal;
   bool zero = x_is_zero;
+  bool last_full = false;  // previous cycle ran all its steps (graph replay pays off)
   stt = LgStats();
   while (true) {
     // ---- residual r = c - B x into V[0]
@@ -205,7 +408,13 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int steps = 0;
-    for (int j = 0; j < steps_max; ++j) {
+    const bool graph = o.use_graph && last_full;
+    if (graph) {
+      if ((st = graph_cycle<T>(p, w, o, K, m_eff, naug, next_slot, beta, steps_max, nbasis, H, Hr, g,
+                               stt, steps, s)))
+        return st;
+    }
+    for (int j = 0; j < (graph ? 0 : steps_max); ++j) {
       T* wv = Vp(j + 1);
       if (j < m_eff) {
         if ((st = op_B<T>(p, w, o, K, Vp(j), wv, B.tmp, s))) return st;
@@ -254,6 +463,7 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
       stt.iterations++;
       if (std::fabs(g[j + 1]) <= o.tol_abs || hn == 0.0 || stt.iterations >= o.maxiter) break;
     }
+    last_full = steps == steps_max && std::fabs(g[steps]) > o.tol_abs;
     // ---- least squares: R y = g
     for (int i = steps - 1; i >= 0; --i) {
       double t = g[i];
@@ -317,12 +527,13 @@ static void default_opts(cheb_solve_opts& o) {
   o.restart = 30;
   o.augment = 3;
   o.maxiter = 2000;
-  o.inner_rtol = 1e-5;
+  o.inner_rtol = 1e-4;
   o.inner_maxiter = 400;
   o.max_refinements = 30;
   o.reorth = 0;
   o.precond = CHEB_PRECOND_FDM;
   o.kref = 0.0;
+  o.use_graph = 0;
 }
 
 static double norm2_dev(Workspace& w, const double* x, cudaStream_t s, int* st) {
@@ -368,6 +579,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   lo.reorth = o.reorth != 0;
   lo.precond = o.precond;
   lo.transpose = transpose;
+  lo.use_graph = o.use_graph != 0;
   if (o.precond == CHEB_PRECOND_FDM) {
     if ((st = fdm_setup(p, w.fdm))) return st;
     if (o.kref > 0) lo.kref = o.kref;
@@ -399,6 +611,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     info.iterations = stt.iterations;
     info.cycles = stt.cycles;
     info.applies_fp64 = stt.applies;
+    info.graph_captures = stt.captures;
     info.rel_residual = stt.resid / nb;
     info.seconds = now_s() - t0;
     info.status = rc;
@@ -453,6 +666,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     info.iterations += stt.iterations;
     info.cycles += stt.cycles;
     info.applies_fp32 += stt.applies;
+    info.graph_captures += stt.captures;
     info.refinements++;
     info.rel_residual_inner = stt.resid / cn;
     if ((st = k_axpy64<float>(u, B.x, sr, n, s))) return st;
@@ -560,12 +774,14 @@ static int picard_impl(cheb_plan_s* p, const double* K0, const double* b, double
   cheb_solve_info tot;
   std::memset(&tot, 0, sizeof(tot));
   const double t0 = now_s();
+  cheb_solve_opts oi = o;  // kref frozen after the first step: captured graphs stay valid
   for (m = 1; m <= maxit; ++m) {
     if ((st = picard_conductivity(p, K0, u, beta, w.picK))) return st;
     CHEB_CUDA(cudaMemcpyAsync(w.picU, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, p->stream));
     cheb_solve_info li;
     std::memset(&li, 0, sizeof(li));
-    int r = solve_impl(p, w.picK, b, u, o, li);
+    int r = solve_impl(p, w.picK, b, u, oi, li);
+    if (oi.kref <= 0) oi.kref = li.kref;
     tot.iterations += li.iterations;
     tot.cycles += li.cycles;
     tot.refinements += li.refinements;

@@ -213,3 +213,24 @@ def test_apply_full_size_sampled(nn):
         got = p.apply(_dev(K, dtype), _dev(u, dtype)).double().cpu().numpy()
         vals = np.array([got[k, j, i] for (k, j, i) in pts])
         assert np.abs(vals - ref).max() / scale < 20 * _tol(nn - 1, dtype), dtype
+
+
+def test_autotuner_picks_a_route_and_caches(tmp_path):
+    """The autotuner times both routes where both exist, records the decision,
+    reuses it from the cache file, and the tuned plan still matches the oracle."""
+    import paper_2606_21410_b300 as P
+    cache = str(tmp_path / "routes.txt")
+    n = (65, 33, 12)
+    p = P.Plan(n)
+    r = p.autotune(cache)
+    assert r["fp64"][2] == "dense" and r["fp32"][2] == "dense"   # n = 12: dense only
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 4                                       # 65 and 33, two precisions
+    r2 = P.Plan(n).autotune(cache)
+    assert r2 == r and len(open(cache).read().splitlines()) == 4
+    g = O.Grid(n)
+    u = W.random_field(g.shape, 71)
+    K = W.random_positive_field(g.shape, 72)
+    got = p.apply(_dev(K), _dev(u)).cpu().numpy()
+    ref = O.apply(u, K, g)
+    assert np.linalg.norm(got - ref) / _apply_scale(K, u, g) < _tol(64, torch.float64)

@@ -80,7 +80,7 @@ def test_picard_batch_of_uneven_lognormal_instances():
     K0 = [_dev(it[1]) for it in items]
     b = [it[2] for it in items]
     u, infos, its = P.picard_batched(plans, K0, b, beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1,
-                                     rtol=1e-12)
+                                     rtol=1e-12, use_graph=1)
     for i, p in enumerate(plans):
         assert infos[i]["status"] == 0, (sizes[i], infos[i], its[i])
         us, _, its1, _ = p.picard_solve(K0[i], b[i], beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1,

@@ -160,3 +160,27 @@ def test_singular_and_iteration_cap():
     u, info = p2.solve(K2, b2, mode=0, maxiter=3, check_status=False)
     assert info["status"] == 1 and info["iterations"] == 3
     assert torch.isfinite(u).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_graph_captured_cycles_match_stepwise(mode):
+    """use_graph = 1 (captured Arnoldi cycles, device Givens) reaches the same
+    solution as the step-synchronised path."""
+    bc = [0, 0, 1, 1, 1, 1]
+    n = (33, 17, 21)
+    p = _plan(n, bc=bc)
+    X, Y, Z = p.mesh()
+    K = _dev(W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 100.0))
+    b = _dev(W.random_field(p.shape, 61))
+    u0, i0 = p.solve(K, b, mode=mode, rtol=1e-12)
+    u1, i1 = p.solve(K, b, mode=mode, rtol=1e-12, use_graph=1)
+    assert _rel(u1.cpu().numpy(), u0.cpu().numpy()) < 1e-11
+    assert abs(i1["iterations"] - i0["iterations"]) <= 2 * max(1, i0["refinements"])
+    # graphs are cached per operator: a second solve with another K re-captures
+    K2 = K * 2.0
+    u2, _ = p.solve(K2, b, mode=mode, rtol=1e-12, use_graph=1)
+    u3, _ = p.solve(K2, b, mode=mode, rtol=1e-12)
+    assert _rel(u2.cpu().numpy(), u3.cpu().numpy()) < 1e-11
+    lam0, _, _ = p.adjoint_solve(K, b, mode=mode, rtol=1e-12)
+    lam1, _, _ = p.adjoint_solve(K, b, mode=mode, rtol=1e-12, use_graph=1)
+    assert _rel(lam1.cpu().numpy(), lam0.cpu().numpy()) < 1e-11
