@@ -51,6 +51,8 @@ def parse():
                     help="hierarchy: the 257^3 hierarchical solve (the metric); batch: 16 uneven "
                          "lognormal Picard instances solved concurrently (a secondary line)")
     ap.add_argument("--use-graph", type=int, default=0)
+    ap.add_argument("--fdm-only", type=int, default=0, metavar="BITS",
+                    help="only time the preconditioner at the finest level (profiling)")
     ap.add_argument("--apply-only", type=int, default=0, metavar="BITS",
                     help="only time cheb_apply at the finest level in FP32 (32) or FP64 (64); "
                          "for profiling")
@@ -233,26 +235,38 @@ def apply_only(args, n):
     import torch
     import paper_2606_21410_b300 as P
     import workloads as W
-    dt = torch.float32 if args.apply_only == 32 else torch.float64
+    bits = args.apply_only or args.fdm_only
+    dt = torch.float32 if bits == 32 else torch.float64
     p = P.Plan((n, n, n), bc=BC)
     X, Y, Z = p.mesh()
     K = torch.from_numpy(W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0,
                                                   args.contrast)).to("cuda", dt)
     u = torch.from_numpy(np.sin(X + 2 * Y) * np.cos(Z)).to("cuda", dt)
     out = torch.empty_like(u)
+
+    def op():
+        if args.fdm_only:
+            p.precond_apply(u, 1.5, out)
+        else:
+            p.apply(K, u, out)
     for _ in range(max(3, args.warmup)):
-        p.apply(K, u, out)
+        op()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
-        p.apply(K, u, out)
+        op()
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     wb = 4 if dt == torch.float32 else 8
-    print(json.dumps({"apply_only": args.apply_only, "n": n, "ms": t * 1e3, "gdofs": n ** 3 / t / 1e9,
-                      "gbs_11words": 11 * wb * n ** 3 / t / 1e9}), flush=True)
+    rec = {"op": "fdm" if args.fdm_only else "apply", "bits": bits, "n": n, "ms": t * 1e3,
+           "gdofs": n ** 3 / t / 1e9}
+    if args.fdm_only:
+        rec["tflops_12m4"] = 12.0 * (n - 2) ** 4 / t / 1e12
+    else:
+        rec["gbs_11words"] = 11 * wb * n ** 3 / t / 1e9
+    print(json.dumps(rec), flush=True)
 
 
 def batch_workload(args):
@@ -318,7 +332,7 @@ def main():
     import paper_2606_21410_b300 as P
     lib = P.lib
     levels = [int(v) for v in args.levels.split(",")]
-    if args.apply_only:
+    if args.apply_only or args.fdm_only:
         apply_only(args, levels[-1])
         return
     if args.workload == "batch":
@@ -419,6 +433,25 @@ def main():
     h2d = sum(k.numel() * 8 + b.numel() * 8 for k, b in zip(hostK, hostb))
     d2h = out_host.numel() * 8
 
+    # ---- finest-level timing of the preconditioner (the dominant phase)
+    def time_prec(dtype, reps=10):
+        r = bs[-1].to(dtype)
+        out = torch.empty_like(r)
+        kref = float(infos[-1]["kref"])
+        for _ in range(3):
+            pf.precond_apply(r, kref, out)
+        torch.cuda.synchronize()
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            pf.precond_apply(r, kref, out)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b2) / 1e3 / reps
+
+    tp32 = time_prec(torch.float32)
+    apply["fdm_fp32_ms"] = tp32 * 1e3
+
     # ---- roofline of the dominant kernel group
     peaks = {}
     try:
@@ -426,35 +459,35 @@ def main():
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6400.0)
+    bf16 = peaks.get("bf16_tflops", 1800.0)
     top = max(phase, key=lambda k: phase[k]["ms"])
     m = nf - 2
     if top.startswith("prec"):
         # 6 dense contractions of m x m matrices per application: 12 m^4 flops
+        # (FP32 operands on the TF32 tensor cores with the split-TF32 scheme,
+        # which issues 3 TF32 products per algorithmic product)
         flops = 12.0 * m ** 4
-        per = phase[top]["ms"] / max(1, phase[top]["count"]) / 1e3
-        sm_mhz = peaks.get("sm_max_mhz", 2032.0)
-        fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        fp64_peak = fp32_peak / 64.0
-        peak = fp32_peak if top.endswith("32") else fp64_peak
-        roof = {"bound": "alu", "kernel": "fdm preconditioner (gemm_kernel contractions)",
-                "achieved": flops / per / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "frac": flops / per / 1e12 / peak, "traffic": None,
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x max SM clock "
-                               "(FP64 = FP32/64 nominal, unmeasured)"}
+        tf32_peak = bf16 * (1.1 / 2.25)
+        ach = flops / tp32 / 1e12
+        roof = {"bound": "tensor", "kernel": "fdm preconditioner (gemm_tf32x3_kernel contractions + "
+                                              "lift/scale/scatter/face kernels), 257^3 FP32",
+                "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
+                "traffic": None,
+                "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 ratio)",
+                "note": "split-TF32 issues 3 TF32 MMAs per algorithmic flop: tensor-pipe work = 3x achieved"}
     else:
         words = 11.0 / 3.0 if top.startswith("apply") else None
-        wb = 4 if top.endswith("32") else 8
-        per = phase[top]["ms"] / max(1, phase[top]["count"]) / 1e3
+        per = t32 / 3.0
         if words is not None:
-            per_launch = per / 3.0
-            algo = words * wb * ntot
-            roof = {"bound": "hbm", "kernel": "line_pass_kernel", "achieved": algo / per_launch / 1e9,
-                    "peak": hbm, "unit": "GB/s", "frac": algo / per_launch / 1e9 / hbm, "traffic": None}
+            algo = words * 4 * ntot
+            roof = {"bound": "hbm", "kernel": "tf_pass_kernel (FP32 apply, per launch)",
+                    "achieved": algo / per / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": algo / per / 1e9 / hbm, "traffic": None}
         else:
             roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": hbm, "unit": "GB/s",
                     "frac": None, "traffic": None}
     # apply kernel roofline, stated beside (the hot path's streaming kernel)
-    apply_roof = {"bound": "hbm", "kernel": "line_pass_kernel (FP32 apply, 3 launches)",
+    apply_roof = {"bound": "hbm", "kernel": "tf_pass_kernel (FP32 apply, 3 launches)",
                   "achieved": 11 * 4 * ntot / t32 / 1e9, "peak": hbm, "unit": "GB/s",
                   "frac": 11 * 4 * ntot / t32 / 1e9 / hbm,
                   "algorithmic_bytes": "11 words/DOF over the three axis passes"}

@@ -42,14 +42,27 @@ static std::vector<double> transpose(const std::vector<double>& A, int r, int c)
   return B;
 }
 
+// m x m matrix zero-padded to mp x mp
+static std::vector<double> pad_square(const std::vector<double>& A, int m, int mp) {
+  std::vector<double> B((size_t)mp * mp, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) B[(size_t)i * mp + j] = A[(size_t)i * m + j];
+  return B;
+}
+
+static int pad4(int m) { return (m + 3) / 4 * 4; }
+
 template <typename T>
 static int upload_axis(FdmAxisDev<T>& d, const FdmAxisHost& h) {
   int st;
-  if ((st = upload(&d.S, h.S))) return st;
-  if ((st = upload(&d.Sinv, h.Sinv))) return st;
-  if ((st = upload(&d.ST, transpose(h.S, h.m, h.m)))) return st;
-  if ((st = upload(&d.SinvT, transpose(h.Sinv, h.m, h.m)))) return st;
-  if ((st = upload(&d.lam, h.lam))) return st;
+  const int m = h.m, mp = pad4(h.m);
+  if ((st = upload(&d.S, pad_square(h.S, m, mp)))) return st;
+  if ((st = upload(&d.Sinv, pad_square(h.Sinv, m, mp)))) return st;
+  if ((st = upload(&d.ST, pad_square(transpose(h.S, m, m), m, mp)))) return st;
+  if ((st = upload(&d.SinvT, pad_square(transpose(h.Sinv, m, m), m, mp)))) return st;
+  std::vector<double> lam(mp, 0.0);
+  for (int i = 0; i < m; ++i) lam[i] = h.lam[i];
+  if ((st = upload(&d.lam, lam))) return st;
   if ((st = upload(&d.G, h.G))) return st;
   if ((st = upload(&d.Binv, h.Binv))) return st;
   if ((st = upload(&d.Lh, h.Lh))) return st;
@@ -126,7 +139,10 @@ int fdm_setup(const cheb_plan_s* p, Fdm& f) {
     if ((st = upload_axis<double>(f.d64[a], f.host[a]))) return st;
     if ((st = upload_axis<float>(f.d32[a], f.host[a]))) return st;
   }
-  for (int a = 0; a < 3; ++a) f.m[a] = a < p->dim ? p->n[a] - 2 : 1;
+  for (int a = 0; a < 3; ++a) {
+    f.m[a] = a < p->dim ? p->n[a] - 2 : 1;
+    f.mp[a] = a < p->dim ? pad4(f.m[a]) : 1;
+  }
   f.ready = true;
   return CHEB_OK;
 }
@@ -147,7 +163,7 @@ void fdm_free(Fdm& f) {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct FdmK {
-  int m[3], off[3];
+  int m[3], mp[3], off[3];
   const T* Lh[3];
   const T* lam[3];
   const T* G[3];
@@ -157,6 +173,11 @@ struct FdmK {
 
 __device__ __forceinline__ size_t gidx3(const Geom& g, int i, int j, int k) {
   return ((size_t)k * g.n[1] + j) * g.n[0] + i;
+}
+// position of interior entry (ci, cj, ck) in the padded compact array
+template <typename T>
+__device__ __forceinline__ size_t cpos(const FdmK<T>& t, int ci, int cj, int ck) {
+  return ((size_t)ck * t.mp[1] + cj) * t.mp[0] + ci;
 }
 
 // U (compact interior) = r_I + kref sum_a Lh_a (r at the two ends of the a-line)
@@ -179,7 +200,7 @@ __global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__
       const T r0 = r[gidx3(g, e0[0], e0[1], e0[2])], rN = r[gidx3(g, eN[0], eN[1], eN[2])];
       v += kref * (t.Lh[a][cl[a] * 2 + 0] * r0 + t.Lh[a][cl[a] * 2 + 1] * rN);
     }
-    U[c] = v;
+    U[cpos(t, ci, cj, ck)] = v;
   }
 }
 
@@ -193,7 +214,8 @@ __global__ void fdm_scale_kernel(FdmK<T> t, int dim, T kref, T* __restrict__ U) 
     T l = t.lam[0][ci];
     if (dim > 1) l += t.lam[1][cj];
     if (dim > 2) l += t.lam[2][ck];
-    U[c] = U[c] / (kref * l);
+    const size_t q = cpos(t, ci, cj, ck);
+    U[q] = U[q] / (kref * l);
   }
 }
 
@@ -204,7 +226,7 @@ __global__ void fdm_scatter_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, T
     const int ci = (int)(c % t.m[0]);
     const int cj = (int)((c / t.m[0]) % t.m[1]);
     const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
-    x[gidx3(g, ci + t.off[0], cj + t.off[1], ck + t.off[2])] = U[c];
+    x[gidx3(g, ci + t.off[0], cj + t.off[1], ck + t.off[2])] = U[cpos(t, ci, cj, ck)];
   }
 }
 
@@ -217,8 +239,7 @@ __global__ void fdm_faces_kernel(Geom g, FdmK<T> t, int a, const T* __restrict__
   // the two other compact axes
   const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
   const size_t lines = (size_t)t.m[b] * t.m[c];
-  const size_t sx = 1, sy = t.m[0], sz = (size_t)t.m[0] * t.m[1];
-  const size_t str[3] = {sx, sy, sz};
+  const size_t str[3] = {1, (size_t)t.mp[0], (size_t)t.mp[0] * t.mp[1]};
   const T* G0 = t.G[a];
   const T* GN = t.G[a] + ma;
   const T* Bi = t.Binv[a];
@@ -458,7 +479,7 @@ __global__ void fdm_gather_t_kernel(Geom g, FdmK<T> t, const T* __restrict__ Y, 
       v += t.G[a][cl[a]] * Y[gidx3(g, e0[0], e0[1], e0[2])] +
            t.G[a][ma + cl[a]] * Y[gidx3(g, eN[0], eN[1], eN[2])];
     }
-    U[c] = v;
+    U[cpos(t, ci, cj, ck)] = v;
   }
 }
 
@@ -469,7 +490,7 @@ __global__ void fdm_faces_t_kernel(Geom g, FdmK<T> t, int a, T kref, const T* __
   const int ma = t.m[a];
   const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
   const size_t lines = (size_t)t.m[b] * t.m[c];
-  const size_t str[3] = {1, (size_t)t.m[0], (size_t)t.m[0] * t.m[1]};
+  const size_t str[3] = {1, (size_t)t.mp[0], (size_t)t.mp[0] * t.mp[1]};
   const T* Lh = t.Lh[a];
   const T* Bi = t.Binv[a];
   for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < lines; L += (size_t)gridDim.x * blockDim.x) {
@@ -499,6 +520,7 @@ template <> FdmK<double> make_k<double>(const Fdm& f, int dim) {
   FdmK<double> k;
   for (int a = 0; a < 3; ++a) {
     k.m[a] = f.m[a];
+    k.mp[a] = f.mp[a];
     k.off[a] = a < dim ? 1 : 0;
     k.Lh[a] = f.d64[a].Lh; k.lam[a] = f.d64[a].lam; k.G[a] = f.d64[a].G;
     k.Binv[a] = f.d64[a].Binv; k.Drow[a] = f.d64[a].Drow;
@@ -509,6 +531,7 @@ template <> FdmK<float> make_k<float>(const Fdm& f, int dim) {
   FdmK<float> k;
   for (int a = 0; a < 3; ++a) {
     k.m[a] = f.m[a];
+    k.mp[a] = f.mp[a];
     k.off[a] = a < dim ? 1 : 0;
     k.Lh[a] = f.d32[a].Lh; k.lam[a] = f.d32[a].lam; k.G[a] = f.d32[a].G;
     k.Binv[a] = f.d32[a].Binv; k.Drow[a] = f.d32[a].Drow;
@@ -523,6 +546,39 @@ template <typename T> static const FdmAxisDev<T>& axdev(const Fdm& f, int a);
 template <> const FdmAxisDev<double>& axdev<double>(const Fdm& f, int a) { return f.d64[a]; }
 template <> const FdmAxisDev<float>& axdev<float>(const Fdm& f, int a) { return f.d32[a]; }
 
+template <typename T>
+static int gemm_any(int M, int N, int K, const T* A, int lda, long long sA, const T* B, int ldb, long long sB,
+                    T* C, int ldc, long long sC, int batch, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (tf32x3_ok(K, A, lda, sA, B, ldb, sB))
+      return k_gemm_tf32x3(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, s);
+  }
+  return k_gemm<T>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, s);
+}
+
+// out = Mat applied along axis a of the padded compact array `in`
+// (out[.., i, ..] = sum_l Mat[i][l] in[.., l, ..]); MatT is Mat transposed.
+template <typename T>
+static int along(const Fdm& f, int a, const T* Mat, const T* MatT, const T* in, T* out, cudaStream_t s) {
+  const int px = f.mp[0], py = f.mp[1], pz = f.mp[2];
+  if (a == 0) return gemm_any<T>(py * pz, px, px, in, px, 0, MatT, px, 0, out, px, 0, 1, s);
+  if (a == 1)
+    return gemm_any<T>(py, px, py, Mat, py, 0, in, px, (long long)py * px, out, px, (long long)py * px, pz, s);
+  return gemm_any<T>(pz, py * px, pz, Mat, pz, 0, in, py * px, 0, out, py * px, 0, 1, s);
+}
+
+template <typename T>
+static int ensure_compact(Fdm& f, T** U, cudaStream_t s) {
+  if (U[0]) return CHEB_OK;
+  const size_t ptot = (size_t)f.mp[0] * f.mp[1] * f.mp[2];
+  CHEB_CUDA(cudaMalloc(&U[0], sizeof(T) * ptot));
+  CHEB_CUDA(cudaMalloc(&U[1], sizeof(T) * ptot));
+  // the padding must read as zero for the contractions and stays zero
+  CHEB_CUDA(cudaMemsetAsync(U[0], 0, sizeof(T) * ptot, s));
+  CHEB_CUDA(cudaMemsetAsync(U[1], 0, sizeof(T) * ptot, s));
+  return CHEB_OK;
+}
+
 static int grid_for(size_t n) {
   return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
 }
@@ -533,30 +589,18 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
   const FdmK<T> k = make_k<T>(f, p->dim);
   const size_t tot = (size_t)f.m[0] * f.m[1] * f.m[2];
   T** U = ubuf<T>(f);
-  if (!U[0]) {
-    CHEB_CUDA(cudaMalloc(&U[0], sizeof(T) * tot));
-    CHEB_CUDA(cudaMalloc(&U[1], sizeof(T) * tot));
-  }
-  const int mx = f.m[0], my = f.m[1], mz = f.m[2];
+  int st;
+  if ((st = ensure_compact<T>(f, U, s))) return st;
   fdm_lift_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, (T)kref, r, U[0]);
   CHEB_LAUNCH_CHECK("fdm_lift_kernel");
   int cur = 0;
   auto contract = [&](int a, bool inverse) -> int {
     const FdmAxisDev<T>& d = axdev<T>(f, a);
-    const int o = 1 - cur;
-    int st;
-    if (a == 0) {
-      st = k_gemm<T>(my * mz, mx, mx, U[cur], mx, 0, inverse ? d.SinvT : d.ST, mx, 0, U[o], mx, 0, 1, s);
-    } else if (a == 1) {
-      st = k_gemm<T>(my, mx, my, inverse ? d.Sinv : d.S, my, 0, U[cur], mx, (long long)my * mx, U[o], mx,
-                     (long long)my * mx, mz, s);
-    } else {
-      st = k_gemm<T>(mz, my * mx, mz, inverse ? d.Sinv : d.S, mz, 0, U[cur], my * mx, 0, U[o], my * mx, 0, 1, s);
-    }
-    cur = o;
-    return st;
+    const int rc = inverse ? along<T>(f, a, d.Sinv, d.SinvT, U[cur], U[1 - cur], s)
+                           : along<T>(f, a, d.S, d.ST, U[cur], U[1 - cur], s);
+    cur = 1 - cur;
+    return rc;
   };
-  int st;
   for (int a = 0; a < p->dim; ++a)
     if ((st = contract(a, true))) return st;
   fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
@@ -599,9 +643,9 @@ int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cud
   const size_t tot = (size_t)f.m[0] * f.m[1] * f.m[2];
   const size_t nfull = p->size();
   T** U = ubuf<T>(f);
-  if (!U[0]) {
-    CHEB_CUDA(cudaMalloc(&U[0], sizeof(T) * tot));
-    CHEB_CUDA(cudaMalloc(&U[1], sizeof(T) * tot));
+  {
+    int st0 = ensure_compact<T>(f, U, s);
+    if (st0) return st0;
   }
   if (!ybuf<T>(f)) {
     T* yb = nullptr;
@@ -627,25 +671,14 @@ int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cud
   }
   fdm_gather_t_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, Y, U[0]);
   CHEB_LAUNCH_CHECK("fdm_gather_t_kernel");
-  const int mx = f.m[0], my = f.m[1], mz = f.m[2];
   int cur = 0;
-  // (S_z S_y S_x Lambda^{-1} Sinv_z Sinv_y Sinv_x)^T = Sinv^T ... Lambda^{-1} ... S^T
+  // (S_all Lambda^{-1} Sinv_all)^T = Sinv_all^T Lambda^{-1} S_all^T
   auto contract_t = [&](int a, bool inverse) -> int {
     const FdmAxisDev<T>& d = axdev<T>(f, a);
-    const int o = 1 - cur;
-    int st;
-    // contracting with M^T along axis a: x axis uses (M^T)^T = M as the right factor
-    if (a == 0) {
-      st = k_gemm<T>(my * mz, mx, mx, U[cur], mx, 0, inverse ? d.Sinv : d.S, mx, 0, U[o], mx, 0, 1, s);
-    } else if (a == 1) {
-      st = k_gemm<T>(my, mx, my, inverse ? d.SinvT : d.ST, my, 0, U[cur], mx, (long long)my * mx, U[o], mx,
-                     (long long)my * mx, mz, s);
-    } else {
-      st = k_gemm<T>(mz, my * mx, mz, inverse ? d.SinvT : d.ST, mz, 0, U[cur], my * mx, 0, U[o], my * mx, 0,
-                     1, s);
-    }
-    cur = o;
-    return st;
+    const int rc = inverse ? along<T>(f, a, d.SinvT, d.Sinv, U[cur], U[1 - cur], s)
+                           : along<T>(f, a, d.ST, d.S, U[cur], U[1 - cur], s);
+    cur = 1 - cur;
+    return rc;
   };
   int st;
   for (int a = 0; a < p->dim; ++a)

@@ -22,7 +22,8 @@ struct FdmAxisDev {
 
 struct Fdm {
   bool ready = false;
-  int m[3] = {1, 1, 1};
+  int m[3] = {1, 1, 1};   // interior points per axis
+  int mp[3] = {1, 1, 1};  // padded to a multiple of 4 (compact-array extents; pad is zero)
   FdmAxisHost host[3];
   FdmAxisDev<double> d64[3];
   FdmAxisDev<float> d32[3];
