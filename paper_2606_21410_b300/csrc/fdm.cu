@@ -14,12 +14,14 @@
 //    known, edges before corners.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "device.cuh"
 #include "fdm.h"
 #include "gemm.h"
 #include "hostmath.h"
+#include "umma.h"
 
 namespace cheb {
 
@@ -67,6 +69,21 @@ static int upload_axis(FdmAxisDev<T>& d, const FdmAxisHost& h) {
   if ((st = upload(&d.Binv, h.Binv))) return st;
   if ((st = upload(&d.Lh, h.Lh))) return st;
   if ((st = upload(&d.Drow, h.Drow))) return st;
+  return CHEB_OK;
+}
+
+// split-TF32 pair of the m x m matrix A, zero-padded to umma_n_tile(mp) x mp
+static int upload_split(float** hi, float** lo, const std::vector<double>& A, int m, int mp) {
+  const int rows = umma_n_tile(mp);
+  std::vector<double> P((size_t)rows * mp, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) P[(size_t)i * mp + j] = A[(size_t)i * m + j];
+  std::vector<float> h(P.size()), l(P.size());
+  tf32_split_host(P.data(), P.size(), h.data(), l.data());
+  CHEB_CUDA(cudaMalloc(hi, sizeof(float) * P.size()));
+  CHEB_CUDA(cudaMalloc(lo, sizeof(float) * P.size()));
+  CHEB_CUDA(cudaMemcpy(*hi, h.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice));
+  CHEB_CUDA(cudaMemcpy(*lo, l.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice));
   return CHEB_OK;
 }
 
@@ -143,12 +160,35 @@ int fdm_setup(const cheb_plan_s* p, Fdm& f) {
     f.m[a] = a < p->dim ? p->n[a] - 2 : 1;
     f.mp[a] = a < p->dim ? pad4(f.m[a]) : 1;
   }
+  f.rot = false;
+  if (p->dim >= 2 && !std::getenv("CHEB_FDM_NO_TCGEN05")) {
+    const size_t ptot = (size_t)f.mp[0] * f.mp[1] * f.mp[2];
+    bool ok = ptot < ((size_t)1 << 31);
+    for (int a = 0; a < p->dim && ok; ++a) ok = umma_ok((int)(ptot / f.mp[a]), f.mp[a], f.mp[a]);
+    if (ok) {
+      for (int a = 0; a < p->dim; ++a) {
+        const FdmAxisHost& h = f.host[a];
+        const std::vector<double> mats[4] = {h.S, h.Sinv, transpose(h.S, h.m, h.m), transpose(h.Sinv, h.m, h.m)};
+        for (int q = 0; q < 4; ++q) {
+          int st = upload_split(&f.uw[a][2 * q], &f.uw[a][2 * q + 1], mats[q], h.m, f.mp[a]);
+          if (st) return st;
+        }
+      }
+      f.rot = true;
+    }
+  }
   f.ready = true;
   return CHEB_OK;
 }
 
 void fdm_free(Fdm& f) {
   for (int a = 0; a < 3; ++a) { free_axis(f.d64[a]); free_axis(f.d32[a]); }
+  for (int a = 0; a < 3; ++a)
+    for (int q = 0; q < 8; ++q) {
+      cudaFree(f.uw[a][q]);
+      f.uw[a][q] = nullptr;
+    }
+  f.rot = false;
   cudaFree(f.U64[0]); cudaFree(f.U64[1]); cudaFree(f.U32[0]); cudaFree(f.U32[1]);
   cudaFree(f.Y64); cudaFree(f.Y32);
   f.U64[0] = f.U64[1] = nullptr;
@@ -230,6 +270,42 @@ __global__ void fdm_scatter_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, T
   }
 }
 
+// x-axis variant of the face step: one warp per line (the line is contiguous
+// in the compact array), lanes stride the line and combine with shuffles.
+template <typename T>
+__global__ void fdm_faces_x_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, const T* __restrict__ r,
+                                   T* __restrict__ x) {
+  const int ma = t.m[0];
+  const size_t lines = (size_t)t.m[1] * t.m[2];
+  const int lane = threadIdx.x & 31;
+  const T* G0 = t.G[0];
+  const T* GN = t.G[0] + ma;
+  const T* Bi = t.Binv[0];
+  for (size_t L = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; L < lines;
+       L += ((size_t)gridDim.x * blockDim.x) >> 5) {
+    const int cj = (int)(L % t.m[1]), ck = (int)(L / t.m[1]);
+    const T* line = U + ((size_t)ck * t.mp[1] + cj) * t.mp[0];
+    T s0 = 0, sN = 0;
+    for (int l = lane; l < ma; l += 32) {
+      const T v = line[l];
+      s0 += G0[l] * v;
+      sN += GN[l] * v;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, d);
+      sN += __shfl_down_sync(0xffffffffu, sN, d);
+    }
+    if (lane == 0) {
+      const int j = cj + t.off[1], k = ck + t.off[2];
+      const size_t p0 = gidx3(g, 0, j, k), pN = gidx3(g, g.n[0] - 1, j, k);
+      const T r0 = r[p0], rN = r[pN];
+      x[p0] = s0 + Bi[0] * r0 + Bi[1] * rN;
+      x[pN] = sN + Bi[2] * r0 + Bi[3] * rN;
+    }
+  }
+}
+
 // End values of every interior a-line: [x0; xN] = G u_int(line) + Binv [r0; rN].
 // One thread per line; for a > 0 consecutive threads take x-adjacent lines.
 template <typename T>
@@ -273,6 +349,7 @@ __global__ void fdm_faces_kernel(Geom g, FdmK<T> t, int a, const T* __restrict__
 template <typename T>
 __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __restrict__ r,
                                  T* __restrict__ x) {
+  if (a < 0) a = blockIdx.y;  // one launch for every axis
   const int nb_axes = g.dim - 1;  // other active axes
   int others[2], no = 0;
   for (int q = 0; q < g.dim; ++q)
@@ -579,6 +656,26 @@ static int ensure_compact(Fdm& f, T** U, cudaStream_t s) {
   return CHEB_OK;
 }
 
+template <typename T>
+static bool rotating(const Fdm& f) {
+  return sizeof(T) == 4 && f.rot;
+}
+
+// Matrix q (0 S, 1 S^{-1}, 2 S^T, 3 S^{-T}) along every axis on the tcgen05
+// kernel: each contraction runs along the contiguous axis and writes its
+// output transposed, so after dim contractions the layout is restored.  The
+// axis products commute, so the sweep order is always x, y, z.
+static int rot_sweep(const cheb_plan_s* p, Fdm& f, float** U, int& cur, int q, cudaStream_t s) {
+  const size_t ptot = (size_t)f.mp[0] * f.mp[1] * f.mp[2];
+  for (int a = 0; a < p->dim; ++a) {
+    const int K = f.mp[a];
+    const int st = umma_tf32x3_rot(U[cur], f.uw[a][2 * q], f.uw[a][2 * q + 1], U[1 - cur], (int)(ptot / K), K, K, s);
+    if (st) return st;
+    cur = 1 - cur;
+  }
+  return CHEB_OK;
+}
+
 static int grid_for(size_t n) {
   return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
 }
@@ -601,30 +698,36 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
     cur = 1 - cur;
     return rc;
   };
-  for (int a = 0; a < p->dim; ++a)
-    if ((st = contract(a, true))) return st;
-  fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
-  CHEB_LAUNCH_CHECK("fdm_scale_kernel");
-  for (int a = p->dim - 1; a >= 0; --a)
-    if ((st = contract(a, false))) return st;
+  if (rotating<T>(f)) {
+    if ((st = rot_sweep(p, f, (float**)U, cur, 1, s))) return st;  // S^{-1}
+    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+    CHEB_LAUNCH_CHECK("fdm_scale_kernel");
+    if ((st = rot_sweep(p, f, (float**)U, cur, 0, s))) return st;  // S
+  } else {
+    for (int a = 0; a < p->dim; ++a)
+      if ((st = contract(a, true))) return st;
+    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+    CHEB_LAUNCH_CHECK("fdm_scale_kernel");
+    for (int a = p->dim - 1; a >= 0; --a)
+      if ((st = contract(a, false))) return st;
+  }
   fdm_scatter_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, U[cur], x);
   CHEB_LAUNCH_CHECK("fdm_scatter_kernel");
   for (int a = 0; a < p->dim; ++a) {
     const size_t lines = tot / f.m[a];
-    fdm_faces_kernel<T><<<grid_for(lines), 256, 0, s>>>(g, k, a, U[cur], r, x);
+    if (a == 0) fdm_faces_x_kernel<T><<<grid_for(lines * 32), 256, 0, s>>>(g, k, U[cur], r, x);
+    else fdm_faces_kernel<T><<<grid_for(lines), 256, 0, s>>>(g, k, a, U[cur], r, x);
     CHEB_LAUNCH_CHECK("fdm_faces_kernel");
   }
+  // boundary-line solves: every axis in one launch (the axes are independent:
+  // each end is solved only by its owner axis), edges before corners
   if (p->dim >= 2) {
-    for (int a = 0; a < p->dim; ++a) {
-      fdm_bline_kernel<T><<<8, 128, 0, s>>>(g, k, a, 1, r, x);
-      CHEB_LAUNCH_CHECK("fdm_bline_kernel");
-    }
+    fdm_bline_kernel<T><<<dim3(8, p->dim), 128, 0, s>>>(g, k, -1, 1, r, x);
+    CHEB_LAUNCH_CHECK("fdm_bline_kernel");
   }
   if (p->dim == 3) {
-    for (int a = 0; a < 3; ++a) {
-      fdm_bline_kernel<T><<<1, 32, 0, s>>>(g, k, a, 2, r, x);
-      CHEB_LAUNCH_CHECK("fdm_bline_kernel");
-    }
+    fdm_bline_kernel<T><<<dim3(1, 3), 32, 0, s>>>(g, k, -1, 2, r, x);
+    CHEB_LAUNCH_CHECK("fdm_bline_kernel");
   }
   return CHEB_OK;
 }
@@ -681,12 +784,19 @@ int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cud
     return rc;
   };
   int st;
-  for (int a = 0; a < p->dim; ++a)
-    if ((st = contract_t(a, false))) return st;
-  fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
-  CHEB_LAUNCH_CHECK("fdm_scale_kernel");
-  for (int a = p->dim - 1; a >= 0; --a)
-    if ((st = contract_t(a, true))) return st;
+  if (rotating<T>(f)) {
+    if ((st = rot_sweep(p, f, (float**)U, cur, 2, s))) return st;  // S^T
+    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+    CHEB_LAUNCH_CHECK("fdm_scale_kernel");
+    if ((st = rot_sweep(p, f, (float**)U, cur, 3, s))) return st;  // S^{-T}
+  } else {
+    for (int a = 0; a < p->dim; ++a)
+      if ((st = contract_t(a, false))) return st;
+    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+    CHEB_LAUNCH_CHECK("fdm_scale_kernel");
+    for (int a = p->dim - 1; a >= 0; --a)
+      if ((st = contract_t(a, true))) return st;
+  }
   fdm_scatter_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, U[cur], z);
   CHEB_LAUNCH_CHECK("fdm_scatter_kernel");
   for (int a = 0; a < p->dim; ++a) {

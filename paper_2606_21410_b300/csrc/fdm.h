@@ -31,6 +31,12 @@ struct Fdm {
   float* U32[2] = {nullptr, nullptr};
   double* Y64 = nullptr;                // transposed application: work copy of the input
   float* Y32 = nullptr;
+  // FP32 contractions on the tcgen05 kernel (each contraction along the
+  // contiguous axis, output transposed: the axes rotate and three
+  // contractions restore the layout).  Per axis, split-TF32 pairs
+  // (hi, lo) of S, S^{-1}, S^T, S^{-T}, each umma_n_tile(mp) x mp.
+  bool rot = false;
+  float* uw[3][8] = {};
 };
 
 int fdm_setup(const cheb_plan_s* p, Fdm& f);

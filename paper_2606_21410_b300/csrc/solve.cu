@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "fdm.h"
+#include "umma.h"
 #include "krylov.h"
 #include "prolong.h"
 
@@ -817,6 +818,17 @@ void cheb_solve_opts_default(cheb_solve_opts* o) {
   if (o) default_opts(*o);
 }
 
+// rc, or CHEB_ERR_CUDA when a tensor-core contraction of this plan's
+// preconditioner gave up a bounded wait (its output is then invalid).
+static int tensor_core_status(cheb_plan p, int rc) {
+  if (!p->ws || !p->ws->fdm.rot) return rc;
+  const int e = umma_take_error();
+  if (e == 0) return rc;
+  set_error(e < 0 ? "could not read the tensor-core error word"
+                  : "tensor-core contraction: a bounded pipeline wait gave up");
+  return CHEB_ERR_CUDA;
+}
+
 int cheb_solve(cheb_plan p, const double* K, const double* b, double* u, const cheb_solve_opts* opts,
                cheb_solve_info* info) {
   if (!p || !K || !b || !u) { set_error("null argument"); return CHEB_ERR_ARG; }
@@ -830,6 +842,7 @@ int cheb_solve(cheb_plan p, const double* K, const double* b, double* u, const c
   cheb_solve_info tmp;
   std::memset(&tmp, 0, sizeof(tmp));
   int rc = solve_impl(p, K, b, u, o, tmp);
+  if (rc >= 0 && (rc = tensor_core_status(p, rc)) < 0) tmp.status = rc;
   if (info) *info = tmp;
   return rc;
 }
@@ -908,7 +921,12 @@ int cheb_precond_apply_t(cheb_plan p, int prec, double kref, const void* y, void
   if ((st = ensure_ws(p))) return st;
   if ((st = fdm_setup(p, p->ws->fdm))) return st;
   if (prec == CHEB_FP64) return fdm_apply_t<double>(p, p->ws->fdm, kref, (const double*)y, (double*)z, p->stream);
-  if (prec == CHEB_FP32) return fdm_apply_t<float>(p, p->ws->fdm, kref, (const float*)y, (float*)z, p->stream);
+  if (prec == CHEB_FP32) {
+    st = fdm_apply_t<float>(p, p->ws->fdm, kref, (const float*)y, (float*)z, p->stream);
+    if (st) return st;
+    CHEB_CUDA(cudaStreamSynchronize(p->stream));
+    return tensor_core_status(p, CHEB_OK);
+  }
   set_error("prec must be CHEB_FP64 or CHEB_FP32");
   return CHEB_ERR_ARG;
 }
@@ -1015,7 +1033,12 @@ int cheb_precond_apply(cheb_plan p, int prec, double kref, const void* r, void* 
   if ((st = ensure_ws(p))) return st;
   if ((st = fdm_setup(p, p->ws->fdm))) return st;
   if (prec == CHEB_FP64) return fdm_apply<double>(p, p->ws->fdm, kref, (const double*)r, (double*)z, p->stream);
-  if (prec == CHEB_FP32) return fdm_apply<float>(p, p->ws->fdm, kref, (const float*)r, (float*)z, p->stream);
+  if (prec == CHEB_FP32) {
+    st = fdm_apply<float>(p, p->ws->fdm, kref, (const float*)r, (float*)z, p->stream);
+    if (st) return st;
+    CHEB_CUDA(cudaStreamSynchronize(p->stream));
+    return tensor_core_status(p, CHEB_OK);
+  }
   set_error("prec must be CHEB_FP64 or CHEB_FP32");
   return CHEB_ERR_ARG;
 }

@@ -1,0 +1,30 @@
+// Blackwell tensor-core contraction (tcgen05 + TMA) used by the FP32
+// fast-diagonalization preconditioner (umma.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace cheb {
+
+// Y[n * M + m] = sum_k X[m * K + k] * W[n * K + k]  for m < M, n < N.
+//
+// One contraction of the tensor-product factorisation along the contiguous
+// axis of X, written with the output transposed: X viewed as [M][K] (K the
+// contracted axis, contiguous), W an N x K row-major matrix given as its
+// split-TF32 pair (Wh = tf32(W), Wl = tf32(W - Wh), both n_rows x K with
+// n_rows = umma_n_tile(N) and zero rows past N), Y written as [N][M].
+// Arithmetic: three TF32 tensor-core products Xh Wh + Xh Wl + Xl Wh with
+// FP32 accumulation, X split on the fly; FP32-level accuracy.
+// Requirements (checked by umma_ok): K >= 32, K % 4 == 0, 32 <= N <= 256,
+// M >= 128, 16-byte aligned X and W.  X and Y must not overlap.
+int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M, int N, int K,
+                    cudaStream_t s);
+bool umma_ok(int M, int N, int K);
+int umma_n_tile(int N);
+// Split-TF32 pair of a row-major matrix (host): hi = tf32(x), lo = tf32(x - hi).
+void tf32_split_host(const double* x, size_t n, float* hi, float* lo);
+// Reads and clears the device-side error word the kernel sets when one of
+// its bounded waits gives up (returns 0 when no wait gave up).
+int umma_take_error();
+
+}  // namespace cheb
