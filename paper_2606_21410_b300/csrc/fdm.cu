@@ -220,60 +220,60 @@ __device__ __forceinline__ size_t cpos(const FdmK<T>& t, int ci, int cj, int ck)
   return ((size_t)ck * t.mp[1] + cj) * t.mp[0] + ci;
 }
 
+// Element kernels run on a 3-D grid: x = (ci blocks of 128), y = cj, z = ck.
+#define FDM_CELL_INDEX                                   \
+  const int ci = blockIdx.x * blockDim.x + threadIdx.x; \
+  const int cj = blockIdx.y, ck = blockIdx.z;           \
+  if (ci >= t.m[0]) return;
+
 // U (compact interior) = r_I + kref sum_a Lh_a (r at the two ends of the a-line)
 template <typename T>
 __global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__ r, T* __restrict__ U) {
-  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(c % t.m[0]);
-    const int cj = (int)((c / t.m[0]) % t.m[1]);
-    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
-    const int idx[3] = {ci + t.off[0], cj + t.off[1], ck + t.off[2]};
-    T v = r[gidx3(g, idx[0], idx[1], idx[2])];
-    const int cl[3] = {ci, cj, ck};
+  FDM_CELL_INDEX
+  const int idx[3] = {ci + t.off[0], cj + t.off[1], ck + t.off[2]};
+  T v = r[gidx3(g, idx[0], idx[1], idx[2])];
+  const int cl[3] = {ci, cj, ck};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (a >= g.dim) break;
-      int e0[3] = {idx[0], idx[1], idx[2]}, eN[3] = {idx[0], idx[1], idx[2]};
-      e0[a] = 0;
-      eN[a] = g.n[a] - 1;
-      const T r0 = r[gidx3(g, e0[0], e0[1], e0[2])], rN = r[gidx3(g, eN[0], eN[1], eN[2])];
-      v += kref * (t.Lh[a][cl[a] * 2 + 0] * r0 + t.Lh[a][cl[a] * 2 + 1] * rN);
-    }
-    U[cpos(t, ci, cj, ck)] = v;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= g.dim) break;
+    int e0[3] = {idx[0], idx[1], idx[2]}, eN[3] = {idx[0], idx[1], idx[2]};
+    e0[a] = 0;
+    eN[a] = g.n[a] - 1;
+    const T r0 = r[gidx3(g, e0[0], e0[1], e0[2])], rN = r[gidx3(g, eN[0], eN[1], eN[2])];
+    v += kref * (t.Lh[a][cl[a] * 2 + 0] * r0 + t.Lh[a][cl[a] * 2 + 1] * rN);
   }
+  U[cpos(t, ci, cj, ck)] = v;
 }
 
 template <typename T>
 __global__ void fdm_scale_kernel(FdmK<T> t, int dim, T kref, T* __restrict__ U) {
-  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(c % t.m[0]);
-    const int cj = (int)((c / t.m[0]) % t.m[1]);
-    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
-    T l = t.lam[0][ci];
-    if (dim > 1) l += t.lam[1][cj];
-    if (dim > 2) l += t.lam[2][ck];
-    const size_t q = cpos(t, ci, cj, ck);
-    U[q] = U[q] / (kref * l);
-  }
+  FDM_CELL_INDEX
+  T l = t.lam[0][ci];
+  if (dim > 1) l += t.lam[1][cj];
+  if (dim > 2) l += t.lam[2][ck];
+  const size_t q = cpos(t, ci, cj, ck);
+  U[q] = U[q] / (kref * l);
 }
 
 template <typename T>
 __global__ void fdm_scatter_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, T* __restrict__ x) {
-  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(c % t.m[0]);
-    const int cj = (int)((c / t.m[0]) % t.m[1]);
-    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
-    x[gidx3(g, ci + t.off[0], cj + t.off[1], ck + t.off[2])] = U[cpos(t, ci, cj, ck)];
-  }
+  FDM_CELL_INDEX
+  x[gidx3(g, ci + t.off[0], cj + t.off[1], ck + t.off[2])] = U[cpos(t, ci, cj, ck)];
 }
 
-// x-axis variant of the face step: one warp per line (the line is contiguous
-// in the compact array), lanes stride the line and combine with shuffles.
+// Where the face step reads the interior values: src[off + ci + cj s1 + ck s2]
+// (the compact array, or the interior of the full grid).
 template <typename T>
-__global__ void fdm_faces_x_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, const T* __restrict__ r,
+struct FdmSrc {
+  const T* p;
+  long long off, s1, s2;
+};
+
+// End values of every interior x-line, [x0; xN] = G u_int(line) + Binv [r0; rN]:
+// one warp per line (the line is contiguous), lanes stride the line and
+// combine with shuffles.
+template <typename T>
+__global__ void fdm_faces_x_kernel(Geom g, FdmK<T> t, FdmSrc<T> u, const T* __restrict__ r,
                                    T* __restrict__ x) {
   const int ma = t.m[0];
   const size_t lines = (size_t)t.m[1] * t.m[2];
@@ -284,7 +284,7 @@ __global__ void fdm_faces_x_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, c
   for (size_t L = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; L < lines;
        L += ((size_t)gridDim.x * blockDim.x) >> 5) {
     const int cj = (int)(L % t.m[1]), ck = (int)(L / t.m[1]);
-    const T* line = U + ((size_t)ck * t.mp[1] + cj) * t.mp[0];
+    const T* line = u.p + u.off + cj * u.s1 + ck * u.s2;
     T s0 = 0, sN = 0;
     for (int l = lane; l < ma; l += 32) {
       const T v = line[l];
@@ -306,35 +306,44 @@ __global__ void fdm_faces_x_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, c
   }
 }
 
-// End values of every interior a-line: [x0; xN] = G u_int(line) + Binv [r0; rN].
-// One thread per line; for a > 0 consecutive threads take x-adjacent lines.
+// Same for the y (a = 1) or z (a = 2) lines: a 32 x 8 block takes 32
+// x-adjacent lines (coalesced reads), its 8 rows split the line and reduce
+// through shared memory.  Grid: (ceil(m_x / 32), m_other).
 template <typename T>
-__global__ void fdm_faces_kernel(Geom g, FdmK<T> t, int a, const T* __restrict__ U,
-                                 const T* __restrict__ r, T* __restrict__ x) {
+__global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, int a, FdmSrc<T> u,
+                                                           const T* __restrict__ r, T* __restrict__ x) {
+  __shared__ T red[2][8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int ci = blockIdx.x * 32 + tx, co = blockIdx.y;
   const int ma = t.m[a];
-  // the two other compact axes
-  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-  const size_t lines = (size_t)t.m[b] * t.m[c];
-  const size_t str[3] = {1, (size_t)t.mp[0], (size_t)t.mp[0] * t.mp[1]};
+  const long long sl = a == 1 ? u.s1 : u.s2, so = a == 1 ? u.s2 : u.s1;
   const T* G0 = t.G[a];
   const T* GN = t.G[a] + ma;
-  const T* Bi = t.Binv[a];
-  for (size_t L = blockIdx.x * (size_t)blockDim.x + threadIdx.x; L < lines; L += (size_t)gridDim.x * blockDim.x) {
-    const int cb = (int)(L % t.m[b]), cc = (int)(L / t.m[b]);
-    int cidx[3];
-    cidx[a] = 0; cidx[b] = cb; cidx[c] = cc;
-    const size_t base = cidx[0] * str[0] + cidx[1] * str[1] + cidx[2] * str[2];
-    T s0 = 0, sN = 0;
-    for (int l = 0; l < ma; ++l) {
-      const T v = U[base + (size_t)l * str[a]];
+  T s0 = 0, sN = 0;
+  if (ci < t.m[0]) {
+    const T* line = u.p + u.off + ci + co * so;
+    for (int l = ty; l < ma; l += 8) {
+      const T v = line[l * sl];
       s0 += G0[l] * v;
       sN += GN[l] * v;
     }
-    int idx[3] = {cidx[0] + t.off[0], cidx[1] + t.off[1], cidx[2] + t.off[2]};
-    idx[a] = 0;
-    const size_t p0 = gidx3(g, idx[0], idx[1], idx[2]);
-    idx[a] = g.n[a] - 1;
-    const size_t pN = gidx3(g, idx[0], idx[1], idx[2]);
+  }
+  red[0][ty][tx] = s0;
+  red[1][ty][tx] = sN;
+  __syncthreads();
+  if (ty == 0 && ci < t.m[0]) {
+    for (int q = 1; q < 8; ++q) {
+      s0 += red[0][q][tx];
+      sN += red[1][q][tx];
+    }
+    int e[3] = {ci + t.off[0], 0, 0};
+    if (a == 1) e[2] = co + t.off[2];
+    else e[1] = co + t.off[1];
+    e[a] = 0;
+    const size_t p0 = gidx3(g, e[0], e[1], e[2]);
+    e[a] = g.n[a] - 1;
+    const size_t pN = gidx3(g, e[0], e[1], e[2]);
+    const T* Bi = t.Binv[a];
     const T r0 = r[p0], rN = r[pN];
     x[p0] = s0 + Bi[0] * r0 + Bi[1] * rN;
     x[pN] = sN + Bi[2] * r0 + Bi[3] * rN;
@@ -342,14 +351,16 @@ __global__ void fdm_faces_kernel(Geom g, FdmK<T> t, int a, const T* __restrict__
 }
 
 // Boundary-row solve on a-lines that lie in one face (kind 1: the third
-// index interior) or in two faces (kind 2).  End nodes owned by a Neumann
-// face of axis a are solved from their rows s (D x)_e = r_e with the line
-// interior known; Dirichlet-owned ends copy r; other ends belong to another
-// axis' line and are left alone.
+// index interior) or in two faces (kind 2), one warp per line.  End nodes
+// owned by a Neumann face of axis a are solved from their rows
+// s (D x)_e = r_e with the line interior known; Dirichlet-owned ends copy r;
+// other ends belong to another axis' line and are left alone.  An a-line
+// may read an end owned by a lower axis (never a higher one: at a shared
+// end the lower axis wins among Neumann faces), so the axes run in
+// increasing order, one launch each.
 template <typename T>
 __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __restrict__ r,
                                  T* __restrict__ x) {
-  if (a < 0) a = blockIdx.y;  // one launch for every axis
   const int nb_axes = g.dim - 1;  // other active axes
   int others[2], no = 0;
   for (int q = 0; q < g.dim; ++q)
@@ -371,7 +382,8 @@ __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __
   const int n = g.n[a], N = n - 1;
   const T* D0 = t.Drow[a];
   const T* DN = t.Drow[a] + n;
-  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < total; L += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int L = blockIdx.x * wpb + (threadIdx.x >> 5); L < total; L += gridDim.x * wpb) {
     int idx[3] = {0, 0, 0};
     if (kind == 1) {
       int rest = L, q = 0;
@@ -401,16 +413,24 @@ __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __
     const bool neu0 = (o0 == 2 * a + 1) && !dir0;
     const bool neuN = (oN == 2 * a) && !dirN;
     const T r0 = r[p0], rN = r[pN];
-    if (dir0) x[p0] = r0;
-    if (dirN) x[pN] = rN;
+    if (lane == 0) {
+      if (dir0) x[p0] = r0;
+      if (dirN) x[pN] = rN;
+    }
     if (!neu0 && !neuN) continue;
     T s0 = 0, sN = 0;
-    for (int l = 1; l < N; ++l) {
+    for (int l = 1 + lane; l < N; l += 32) {
       e[a] = l;
       const T v = x[gidx3(g, e[0], e[1], e[2])];
       s0 += D0[l] * v;
       sN += DN[l] * v;
     }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, d);
+      sN += __shfl_down_sync(0xffffffffu, sN, d);
+    }
+    if (lane != 0) continue;
     // rows: +(D00 x0 + D0N xN + s0) = r0 ; -(DN0 x0 + DNN xN + sN) = rN
     const T a00 = D0[0], a01 = D0[N], a10 = DN[0], a11 = DN[N];
     const T b0 = r0 - s0, b1 = -rN - sN;
@@ -538,11 +558,8 @@ __global__ void fdm_edge_dirichlet_t_kernel(Geom g, const T* __restrict__ Y, T* 
 //   Ubar[c] = Y[I(c)] + sum_a (G_a[0][c_a] Y[e0_a(c)] + G_a[1][c_a] Y[eN_a(c)])
 template <typename T>
 __global__ void fdm_gather_t_kernel(Geom g, FdmK<T> t, const T* __restrict__ Y, T* __restrict__ U) {
-  const size_t tot = (size_t)t.m[0] * t.m[1] * t.m[2];
-  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
-    const int ci = (int)(c % t.m[0]);
-    const int cj = (int)((c / t.m[0]) % t.m[1]);
-    const int ck = (int)(c / ((size_t)t.m[0] * t.m[1]));
+  FDM_CELL_INDEX
+  {
     const int idx[3] = {ci + t.off[0], cj + t.off[1], ck + t.off[2]};
     const int cl[3] = {ci, cj, ck};
     T v = Y[gidx3(g, idx[0], idx[1], idx[2])];
@@ -656,6 +673,10 @@ static int ensure_compact(Fdm& f, T** U, cudaStream_t s) {
   return CHEB_OK;
 }
 
+static int grid_for(size_t n) {
+  return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+}
+
 template <typename T>
 static bool rotating(const Fdm& f) {
   return sizeof(T) == 4 && f.rot;
@@ -664,33 +685,116 @@ static bool rotating(const Fdm& f) {
 // Matrix q (0 S, 1 S^{-1}, 2 S^T, 3 S^{-T}) along every axis on the tcgen05
 // kernel: each contraction runs along the contiguous axis and writes its
 // output transposed, so after dim contractions the layout is restored.  The
-// axis products commute, so the sweep order is always x, y, z.
-static int rot_sweep(const cheb_plan_s* p, Fdm& f, float** U, int& cur, int q, cudaStream_t s) {
+// axis products commute, so the sweep order is always x, y, z.  The last
+// contraction uses the epilogue `last` (its row decomposition filled here).
+static int rot_sweep(const cheb_plan_s* p, Fdm& f, float** U, int& cur, int q, UmmaEpi last,
+                     cudaStream_t s) {
   const size_t ptot = (size_t)f.mp[0] * f.mp[1] * f.mp[2];
+  const int L = p->dim - 1;
+  // rows of the last contraction: [y][x] in 3-D, [x] in 2-D
+  last.mpf = f.mp[0];
+  last.mf = f.m[0];
+  last.ms = p->dim == 3 ? f.m[1] : 1;
+  last.mc = f.m[L];
   for (int a = 0; a < p->dim; ++a) {
     const int K = f.mp[a];
-    const int st = umma_tf32x3_rot(U[cur], f.uw[a][2 * q], f.uw[a][2 * q + 1], U[1 - cur], (int)(ptot / K), K, K, s);
+    const UmmaEpi plain;
+    const int st = umma_tf32x3_rot(U[cur], f.uw[a][2 * q], f.uw[a][2 * q + 1], U[1 - cur], (int)(ptot / K), K, K,
+                                   a == L ? last : plain, s);
     if (st) return st;
-    cur = 1 - cur;
+    if (!(a == L && last.mode == 2)) cur = 1 - cur;
   }
   return CHEB_OK;
 }
 
-static int grid_for(size_t n) {
-  return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+// eigenvalue division fused into the last contraction of the S^{-1} sweep
+static UmmaEpi epi_scale(const cheb_plan_s* p, const Fdm& f, double kref) {
+  UmmaEpi e;
+  e.mode = 1;
+  e.lf = f.d32[0].lam;
+  e.ls = p->dim == 3 ? f.d32[1].lam : nullptr;
+  e.lc = f.d32[p->dim - 1].lam;
+  e.kref = (float)kref;
+  return e;
 }
+
+static dim3 grid3(const Fdm& f) { return dim3((f.m[0] + 127) / 128, f.m[1], f.m[2]); }
+
+// interior of the full grid as a face-step source
+template <typename T>
+static FdmSrc<T> full_src(const cheb_plan_s* p, const T* x) {
+  const long long n0 = p->n[0], n01 = (long long)p->n[0] * (p->dim > 1 ? p->n[1] : 1);
+  long long off = 1;
+  if (p->dim > 1) off += n0;
+  if (p->dim > 2) off += n01;
+  return FdmSrc<T>{x, off, n0, n01};
+}
+
+// Face end values of the interior lines of axes [a0, a1), then the
+// boundary-line solves (edges, axis by axis, then corners).
+template <typename T>
+static int faces_and_blines(const cheb_plan_s* p, const Fdm& f, const FdmK<T>& k, FdmSrc<T> u, int a0, int a1,
+                            const T* r, T* x, cudaStream_t s) {
+  const Geom g = p->geom();
+  for (int a = a0; a < a1; ++a) {
+    if (a == 0) {
+      const size_t lines = (size_t)f.m[1] * f.m[2];
+      fdm_faces_x_kernel<T><<<grid_for(lines * 32), 256, 0, s>>>(g, k, u, r, x);
+    } else {
+      const dim3 grid((f.m[0] + 31) / 32, a == 1 ? f.m[2] : f.m[1]);
+      fdm_faces_yz_kernel<T><<<grid, 256, 0, s>>>(g, k, a, u, r, x);
+    }
+    CHEB_LAUNCH_CHECK("fdm_faces_kernel");
+  }
+  if (p->dim >= 2) {
+    for (int a = 0; a < p->dim; ++a) {
+      fdm_bline_kernel<T><<<64, 256, 0, s>>>(g, k, a, 1, r, x);
+      CHEB_LAUNCH_CHECK("fdm_bline_kernel");
+    }
+  }
+  if (p->dim == 3) {
+    for (int a = 0; a < 3; ++a) {
+      fdm_bline_kernel<T><<<1, 128, 0, s>>>(g, k, a, 2, r, x);
+      CHEB_LAUNCH_CHECK("fdm_bline_kernel");
+    }
+  }
+  return CHEB_OK;
+}
+
 
 template <typename T>
 int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaStream_t s) {
   const Geom g = p->geom();
   const FdmK<T> k = make_k<T>(f, p->dim);
-  const size_t tot = (size_t)f.m[0] * f.m[1] * f.m[2];
   T** U = ubuf<T>(f);
   int st;
   if ((st = ensure_compact<T>(f, U, s))) return st;
-  fdm_lift_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, (T)kref, r, U[0]);
+  fdm_lift_kernel<T><<<grid3(f), 128, 0, s>>>(g, k, (T)kref, r, U[0]);
   CHEB_LAUNCH_CHECK("fdm_lift_kernel");
   int cur = 0;
+  if constexpr (sizeof(T) == 4) {
+    if (f.rot) {
+      // S^{-1} sweep with the eigenvalue division fused into its last
+      // contraction; S sweep whose last contraction writes the interior of
+      // x and the end values of the last axis' lines
+      if ((st = rot_sweep(p, f, U, cur, 1, epi_scale(p, f, kref), s))) return st;
+      UmmaEpi e;
+      e.mode = 2;
+      const FdmSrc<T> xs = full_src<T>(p, x);
+      const int L = p->dim - 1;
+      e.x = x;
+      e.r = r;
+      e.xoff = xs.off;
+      e.xs_f = 1;
+      e.xs_s = xs.s1;
+      e.xs_c = L == 2 ? xs.s2 : xs.s1;
+      e.ncol = p->n[L];
+      e.G = f.d32[L].G;
+      e.Binv = f.d32[L].Binv;
+      if ((st = rot_sweep(p, f, U, cur, 0, e, s))) return st;
+      return faces_and_blines<T>(p, f, k, xs, 0, L, r, x, s);
+    }
+  }
   auto contract = [&](int a, bool inverse) -> int {
     const FdmAxisDev<T>& d = axdev<T>(f, a);
     const int rc = inverse ? along<T>(f, a, d.Sinv, d.SinvT, U[cur], U[1 - cur], s)
@@ -698,38 +802,16 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
     cur = 1 - cur;
     return rc;
   };
-  if (rotating<T>(f)) {
-    if ((st = rot_sweep(p, f, (float**)U, cur, 1, s))) return st;  // S^{-1}
-    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
-    CHEB_LAUNCH_CHECK("fdm_scale_kernel");
-    if ((st = rot_sweep(p, f, (float**)U, cur, 0, s))) return st;  // S
-  } else {
-    for (int a = 0; a < p->dim; ++a)
-      if ((st = contract(a, true))) return st;
-    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
-    CHEB_LAUNCH_CHECK("fdm_scale_kernel");
-    for (int a = p->dim - 1; a >= 0; --a)
-      if ((st = contract(a, false))) return st;
-  }
-  fdm_scatter_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, U[cur], x);
+  for (int a = 0; a < p->dim; ++a)
+    if ((st = contract(a, true))) return st;
+  fdm_scale_kernel<T><<<grid3(f), 128, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+  CHEB_LAUNCH_CHECK("fdm_scale_kernel");
+  for (int a = p->dim - 1; a >= 0; --a)
+    if ((st = contract(a, false))) return st;
+  fdm_scatter_kernel<T><<<grid3(f), 128, 0, s>>>(g, k, U[cur], x);
   CHEB_LAUNCH_CHECK("fdm_scatter_kernel");
-  for (int a = 0; a < p->dim; ++a) {
-    const size_t lines = tot / f.m[a];
-    if (a == 0) fdm_faces_x_kernel<T><<<grid_for(lines * 32), 256, 0, s>>>(g, k, U[cur], r, x);
-    else fdm_faces_kernel<T><<<grid_for(lines), 256, 0, s>>>(g, k, a, U[cur], r, x);
-    CHEB_LAUNCH_CHECK("fdm_faces_kernel");
-  }
-  // boundary-line solves: every axis in one launch (the axes are independent:
-  // each end is solved only by its owner axis), edges before corners
-  if (p->dim >= 2) {
-    fdm_bline_kernel<T><<<dim3(8, p->dim), 128, 0, s>>>(g, k, -1, 1, r, x);
-    CHEB_LAUNCH_CHECK("fdm_bline_kernel");
-  }
-  if (p->dim == 3) {
-    fdm_bline_kernel<T><<<dim3(1, 3), 32, 0, s>>>(g, k, -1, 2, r, x);
-    CHEB_LAUNCH_CHECK("fdm_bline_kernel");
-  }
-  return CHEB_OK;
+  const FdmSrc<T> us{U[cur], 0, f.mp[0], (long long)f.mp[0] * f.mp[1]};
+  return faces_and_blines<T>(p, f, k, us, 0, p->dim, r, x, s);
 }
 
 template int fdm_apply<double>(const cheb_plan_s*, Fdm&, double, const double*, double*, cudaStream_t);
@@ -772,7 +854,7 @@ int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cud
     fdm_edge_dirichlet_t_kernel<T><<<grid_for(nfull), 256, 0, s>>>(g, Y, z);
     CHEB_LAUNCH_CHECK("fdm_edge_dirichlet_t_kernel");
   }
-  fdm_gather_t_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, Y, U[0]);
+  fdm_gather_t_kernel<T><<<grid3(f), 128, 0, s>>>(g, k, Y, U[0]);
   CHEB_LAUNCH_CHECK("fdm_gather_t_kernel");
   int cur = 0;
   // (S_all Lambda^{-1} Sinv_all)^T = Sinv_all^T Lambda^{-1} S_all^T
@@ -785,19 +867,18 @@ int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cud
   };
   int st;
   if (rotating<T>(f)) {
-    if ((st = rot_sweep(p, f, (float**)U, cur, 2, s))) return st;  // S^T
-    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
-    CHEB_LAUNCH_CHECK("fdm_scale_kernel");
-    if ((st = rot_sweep(p, f, (float**)U, cur, 3, s))) return st;  // S^{-T}
+    // S^T sweep with the eigenvalue division fused, then the S^{-T} sweep
+    if ((st = rot_sweep(p, f, (float**)U, cur, 2, epi_scale(p, f, kref), s))) return st;
+    if ((st = rot_sweep(p, f, (float**)U, cur, 3, UmmaEpi(), s))) return st;
   } else {
     for (int a = 0; a < p->dim; ++a)
       if ((st = contract_t(a, false))) return st;
-    fdm_scale_kernel<T><<<grid_for(tot), 256, 0, s>>>(k, p->dim, (T)kref, U[cur]);
+    fdm_scale_kernel<T><<<grid3(f), 128, 0, s>>>(k, p->dim, (T)kref, U[cur]);
     CHEB_LAUNCH_CHECK("fdm_scale_kernel");
     for (int a = p->dim - 1; a >= 0; --a)
       if ((st = contract_t(a, true))) return st;
   }
-  fdm_scatter_kernel<T><<<grid_for(tot), 256, 0, s>>>(g, k, U[cur], z);
+  fdm_scatter_kernel<T><<<grid3(f), 128, 0, s>>>(g, k, U[cur], z);
   CHEB_LAUNCH_CHECK("fdm_scatter_kernel");
   for (int a = 0; a < p->dim; ++a) {
     const size_t lines = tot / f.m[a];

@@ -159,7 +159,7 @@ __device__ __forceinline__ float tf32_rna(float x) {
 __global__ void __launch_bounds__(kUThreads, 1)
     umma_tf32x3_rot_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmWh,
                            const __grid_constant__ CUtensorMap tmWl, float* __restrict__ Y, int M, int N, int K,
-                           int n_tile, int tmem_cols) {
+                           int n_tile, int tmem_cols, const UmmaEpi ep) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -280,14 +280,54 @@ __global__ void __launch_bounds__(kUThreads, 1)
       const int q = warp & 3;
       const int row = m0 + 32 * q + lane;
       const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16);
+      int rf = row, rs = 0;
+      bool rv = row < M;
+      if (ep.mode != 0) {
+        rs = row / ep.mpf;
+        rf = row - rs * ep.mpf;
+        rv = rv && rf < ep.mf && rs < ep.ms;
+      }
+      float lrow = 0.f;
+      if (ep.mode == 1 && rv) lrow = ep.lf[rf] + (ep.ls ? ep.ls[rs] : 0.f);
+      const long long xb = ep.xoff + rf * ep.xs_f + rs * ep.xs_s;
+      float s0 = 0.f, sN = 0.f;
       for (int col = 0; col < n_tile; col += 16) {
         float v[16];
         tmem_ld16(tl + (uint32_t)col, v);
-        if (row < M) {
+        if (ep.mode == 0) {
+          if (row < M) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (col + j < N) Y[(size_t)(col + j) * M + row] = v[j];
+            for (int j = 0; j < 16; ++j)
+              if (col + j < N) Y[(size_t)(col + j) * M + row] = v[j];
+          }
+        } else if (ep.mode == 1) {
+          if (row < M) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int n = col + j;
+              if (n < N) {
+                const float fac = (rv && n < ep.mc) ? 1.f / (ep.kref * (lrow + ep.lc[n])) : 0.f;
+                Y[(size_t)n * M + row] = v[j] * fac;
+              }
+            }
+          }
+        } else if (rv) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = col + j;
+            if (n < ep.mc) {
+              ep.x[xb + n * ep.xs_c] = v[j];
+              s0 += ep.G[n] * v[j];
+              sN += ep.G[ep.mc + n] * v[j];
+            }
+          }
         }
+      }
+      if (ep.mode == 2 && rv) {
+        const long long p0 = xb - ep.xs_c, pN = p0 + (long long)(ep.ncol - 1) * ep.xs_c;
+        const float r0 = ep.r[p0], rN = ep.r[pN];
+        ep.x[p0] = s0 + ep.Binv[0] * r0 + ep.Binv[1] * rN;
+        ep.x[pN] = sN + ep.Binv[2] * r0 + ep.Binv[3] * rN;
       }
     }
   }
@@ -369,7 +409,7 @@ void tf32_split_host(const double* x, size_t n, float* hi, float* lo) {
 }
 
 int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M, int N, int K,
-                    cudaStream_t s) {
+                    const UmmaEpi& ep, cudaStream_t s) {
   if (!umma_ok(M, N, K) || (((uintptr_t)X | (uintptr_t)Wh | (uintptr_t)Wl) & 15)) {
     set_error("umma_tf32x3_rot: unsupported shape or alignment");
     return CHEB_ERR_UNSUPPORTED;
@@ -391,7 +431,7 @@ int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, 
   });
   CHEB_CUDA(attr_err);
   const int grid = (M + kBM - 1) / kBM;
-  umma_tf32x3_rot_kernel<<<grid, kUThreads, sm, s>>>(mx, mh, ml, Y, M, N, K, n_tile, tmem_cols);
+  umma_tf32x3_rot_kernel<<<grid, kUThreads, sm, s>>>(mx, mh, ml, Y, M, N, K, n_tile, tmem_cols, ep);
   CHEB_LAUNCH_CHECK("umma_tf32x3_rot_kernel");
   return CHEB_OK;
 }

@@ -17,8 +17,33 @@ namespace cheb {
 // FP32 accumulation, X split on the fly; FP32-level accuracy.
 // Requirements (checked by umma_ok): K >= 32, K % 4 == 0, 32 <= N <= 256,
 // M >= 128, 16-byte aligned X and W.  X and Y must not overlap.
+//
+// Epilogue modes (row m = rs * mpf + rf: rf the fast row axis, rs the slow
+// one; column n = the contracted axis after the contraction):
+//   0: Y[n * M + m] = acc
+//   1: Y[n * M + m] = acc / (kref (lf[rf] + ls[rs] + lc[n])) on the valid
+//      entries (rf < mf, rs < ms, n < mc), 0 on the padding  (the eigenvalue
+//      division of the fast-diagonalization inverse)
+//   2: no Y; acc goes to the interior of the full grid x at
+//      xoff + rf xs_f + rs xs_s + n xs_c for valid entries, and the two end
+//      values of every column-axis line are set from the elimination
+//      x_end = G (line) + Binv r_end  (G: 2 x mc, Binv 2 x 2 row-major)
+struct UmmaEpi {
+  int mode = 0;
+  int mpf = 1, mf = 1, ms = 1, mc = 1;
+  const float* lf = nullptr;
+  const float* ls = nullptr;
+  const float* lc = nullptr;
+  float kref = 1.f;
+  float* x = nullptr;
+  const float* r = nullptr;
+  long long xoff = 0, xs_f = 0, xs_s = 0, xs_c = 0;
+  int ncol = 0;  // points of the column axis, ends included
+  const float* G = nullptr;
+  const float* Binv = nullptr;
+};
 int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M, int N, int K,
-                    cudaStream_t s);
+                    const UmmaEpi& ep, cudaStream_t s);
 bool umma_ok(int M, int N, int K);
 int umma_n_tile(int N);
 // Split-TF32 pair of a row-major matrix (host): hi = tf32(x), lo = tf32(x - hi).
