@@ -211,13 +211,15 @@ struct FdmK {
   const T* Drow[3];
 };
 
-__device__ __forceinline__ size_t gidx3(const Geom& g, int i, int j, int k) {
-  return ((size_t)k * g.n[1] + j) * g.n[0] + i;
+// Grids have at most 257^3 points (axis sizes <= 257) and compact arrays
+// at most 256^3 entries, so 32-bit index arithmetic is exact.
+__device__ __forceinline__ uint32_t gidx3(const Geom& g, int i, int j, int k) {
+  return ((uint32_t)k * (uint32_t)g.n[1] + (uint32_t)j) * (uint32_t)g.n[0] + (uint32_t)i;
 }
 // position of interior entry (ci, cj, ck) in the padded compact array
 template <typename T>
-__device__ __forceinline__ size_t cpos(const FdmK<T>& t, int ci, int cj, int ck) {
-  return ((size_t)ck * t.mp[1] + cj) * t.mp[0] + ci;
+__device__ __forceinline__ uint32_t cpos(const FdmK<T>& t, int ci, int cj, int ck) {
+  return ((uint32_t)ck * (uint32_t)t.mp[1] + (uint32_t)cj) * (uint32_t)t.mp[0] + (uint32_t)ci;
 }
 
 // Element kernels run on a 3-D grid: x = (ci blocks of 128), y = cj, z = ck.
@@ -226,23 +228,34 @@ __device__ __forceinline__ size_t cpos(const FdmK<T>& t, int ci, int cj, int ck)
   const int cj = blockIdx.y, ck = blockIdx.z;           \
   if (ci >= t.m[0]) return;
 
-// U (compact interior) = r_I + kref sum_a Lh_a (r at the two ends of the a-line)
+// U (compact interior) = r_I + kref sum_a Lh_a (r at the two ends of the a-line).
+// Grid (ceil(m_x / 128), m_y, ceil(m_z / kLiftK)): each thread takes kLiftK
+// consecutive z entries of one (x, y) column (independent loads in flight;
+// the z-end values of the column are read once).
+constexpr int kLiftK = 8;
 template <typename T>
 __global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__ r, T* __restrict__ U) {
-  FDM_CELL_INDEX
-  const int idx[3] = {ci + t.off[0], cj + t.off[1], ck + t.off[2]};
-  T v = r[gidx3(g, idx[0], idx[1], idx[2])];
-  const int cl[3] = {ci, cj, ck};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (a >= g.dim) break;
-    int e0[3] = {idx[0], idx[1], idx[2]}, eN[3] = {idx[0], idx[1], idx[2]};
-    e0[a] = 0;
-    eN[a] = g.n[a] - 1;
-    const T r0 = r[gidx3(g, e0[0], e0[1], e0[2])], rN = r[gidx3(g, eN[0], eN[1], eN[2])];
-    v += kref * (t.Lh[a][cl[a] * 2 + 0] * r0 + t.Lh[a][cl[a] * 2 + 1] * rN);
+  const int ci = blockIdx.x * blockDim.x + threadIdx.x, cj = blockIdx.y;
+  if (ci >= t.m[0]) return;
+  const int i = ci + t.off[0], j = cj + t.off[1];
+  const int s1 = g.n[0], s2 = g.n[0] * g.n[1];
+  const T lx0 = kref * t.Lh[0][2 * ci], lxN = kref * t.Lh[0][2 * ci + 1];
+  const T ly0 = g.dim > 1 ? kref * t.Lh[1][2 * cj] : T(0), lyN = g.dim > 1 ? kref * t.Lh[1][2 * cj + 1] : T(0);
+  T rz0 = 0, rzN = 0;
+  if (g.dim > 2) {
+    rz0 = r[j * s1 + i];
+    rzN = r[(g.n[2] - 1) * s2 + j * s1 + i];
   }
-  U[cpos(t, ci, cj, ck)] = v;
+  const int ck0 = blockIdx.z * kLiftK, ck1 = min(ck0 + kLiftK, t.m[2]);
+#pragma unroll 4
+  for (int ck = ck0; ck < ck1; ++ck) {
+    const int k = ck + t.off[2];
+    const int p = k * s2 + j * s1 + i;
+    T v = r[p] + lx0 * r[p - i] + lxN * r[p - i + g.n[0] - 1];
+    if (g.dim > 1) v += ly0 * r[p - j * s1] + lyN * r[p + (g.n[1] - 1 - j) * s1];
+    if (g.dim > 2) v += kref * (t.Lh[2][2 * ck] * rz0 + t.Lh[2][2 * ck + 1] * rzN);
+    U[cpos(t, ci, cj, ck)] = v;
+  }
 }
 
 template <typename T>
@@ -270,26 +283,38 @@ struct FdmSrc {
 };
 
 // End values of every interior x-line, [x0; xN] = G u_int(line) + Binv [r0; rN]:
-// one warp per line (the line is contiguous), lanes stride the line and
-// combine with shuffles.
+// one warp per line (the line is contiguous); each lane keeps its eight
+// entries of G (m <= 255 < 8 * 32) in registers for all its lines, loads its
+// eight line values at once and the warp combines with shuffles.
 template <typename T>
-__global__ void fdm_faces_x_kernel(Geom g, FdmK<T> t, FdmSrc<T> u, const T* __restrict__ r,
-                                   T* __restrict__ x) {
+__global__ void __launch_bounds__(256) fdm_faces_x_kernel(Geom g, FdmK<T> t, FdmSrc<T> u,
+                                                          const T* __restrict__ r, T* __restrict__ x) {
   const int ma = t.m[0];
-  const size_t lines = (size_t)t.m[1] * t.m[2];
+  const int lines = t.m[1] * t.m[2];
   const int lane = threadIdx.x & 31;
-  const T* G0 = t.G[0];
-  const T* GN = t.G[0] + ma;
+  T g0[8], gN[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int l = lane + 32 * q;
+    g0[q] = l < ma ? t.G[0][l] : T(0);
+    gN[q] = l < ma ? t.G[0][ma + l] : T(0);
+  }
   const T* Bi = t.Binv[0];
-  for (size_t L = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5; L < lines;
-       L += ((size_t)gridDim.x * blockDim.x) >> 5) {
-    const int cj = (int)(L % t.m[1]), ck = (int)(L / t.m[1]);
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; L < lines; L += nw) {
+    const int cj = L % t.m[1], ck = L / t.m[1];
     const T* line = u.p + u.off + cj * u.s1 + ck * u.s2;
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int l = lane + 32 * q;
+      v[q] = l < ma ? line[l] : T(0);
+    }
     T s0 = 0, sN = 0;
-    for (int l = lane; l < ma; l += 32) {
-      const T v = line[l];
-      s0 += G0[l] * v;
-      sN += GN[l] * v;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      s0 += g0[q] * v[q];
+      sN += gN[q] * v[q];
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -298,7 +323,7 @@ __global__ void fdm_faces_x_kernel(Geom g, FdmK<T> t, FdmSrc<T> u, const T* __re
     }
     if (lane == 0) {
       const int j = cj + t.off[1], k = ck + t.off[2];
-      const size_t p0 = gidx3(g, 0, j, k), pN = gidx3(g, g.n[0] - 1, j, k);
+      const uint32_t p0 = gidx3(g, 0, j, k), pN = p0 + g.n[0] - 1;
       const T r0 = r[p0], rN = r[pN];
       x[p0] = s0 + Bi[0] * r0 + Bi[1] * rN;
       x[pN] = sN + Bi[2] * r0 + Bi[3] * rN;
@@ -322,6 +347,7 @@ __global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, in
   T s0 = 0, sN = 0;
   if (ci < t.m[0]) {
     const T* line = u.p + u.off + ci + co * so;
+#pragma unroll 4
     for (int l = ty; l < ma; l += 8) {
       const T v = line[l * sl];
       s0 += G0[l] * v;
@@ -769,7 +795,8 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
   T** U = ubuf<T>(f);
   int st;
   if ((st = ensure_compact<T>(f, U, s))) return st;
-  fdm_lift_kernel<T><<<grid3(f), 128, 0, s>>>(g, k, (T)kref, r, U[0]);
+  fdm_lift_kernel<T><<<dim3((f.m[0] + 127) / 128, f.m[1], (f.m[2] + kLiftK - 1) / kLiftK), 128, 0, s>>>(
+      g, k, (T)kref, r, U[0]);
   CHEB_LAUNCH_CHECK("fdm_lift_kernel");
   int cur = 0;
   if constexpr (sizeof(T) == 4) {

@@ -876,15 +876,13 @@ int cheb_rel_diff(cheb_plan p, const double* a, const double* b, double* out) {
   int st;
   if ((st = ensure_ws(p))) return st;
   Workspace& w = *p->ws;
-  const double* src[1] = {b};
-  // |a|^2, <a, b>, |b|^2 -> |a - b|^2 = |a|^2 - 2<a,b> + |b|^2 loses digits; use a difference vector
+  // |a - b|^2 from |a|^2, <a, b>, |b|^2 loses digits: form the difference vector
   if (!w.r64) CHEB_CUDA(cudaMalloc(&w.r64, sizeof(double) * w.n));
   const double* one[1] = {a};
   double cf[2] = {1.0, -1.0};
   const double* two[2] = {a, b};
   if ((st = k_maxpy<double>(w.rs, two, cf, 2, 0.0, w.r64, w.n, w.dscal + 1, p->stream))) return st;
   if ((st = k_mdot<double>(w.rs, one, 0, a, w.n, true, w.dscal, p->stream))) return st;
-  (void)src;
   if ((st = sync_read(w, 2, p->stream))) return st;
   *out = w.hscal[0] > 0 ? std::sqrt(w.hscal[1] / w.hscal[0]) : 0.0;
   return CHEB_OK;
