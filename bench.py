@@ -51,6 +51,9 @@ def parse():
                     help="hierarchy: the 257^3 hierarchical solve (the metric); batch: 16 uneven "
                          "lognormal Picard instances solved concurrently (a secondary line)")
     ap.add_argument("--use-graph", type=int, default=0)
+    ap.add_argument("--route32", default="transform", choices=["transform", "tensor"],
+                    help="FP32 operator-apply route: FFT line transforms, or the dense "
+                         "derivative on the tensor cores (tcgen05)")
     ap.add_argument("--fdm-only", type=int, default=0, metavar="BITS",
                     help="only time the preconditioner at the finest level (profiling)")
     ap.add_argument("--apply-only", type=int, default=0, metavar="BITS",
@@ -81,7 +84,19 @@ def host_level(n, spheres, contrast, nodes):
     return K, faces
 
 
-def setup_gpu(levels, contrast):
+def set_routes(p, route32):
+    """FP32 apply route of every axis that allows it."""
+    import paper_2606_21410_b300 as P
+    if route32 != "tensor":
+        return
+    for a in range(p.dim):
+        try:
+            p.set_route32(a, P.ROUTE_TENSOR)
+        except P.ChebError:
+            pass
+
+
+def setup_gpu(levels, contrast, route32="transform"):
     import torch
     import paper_2606_21410_b300 as P
     import workloads as W
@@ -89,6 +104,7 @@ def setup_gpu(levels, contrast):
     plans, Ks, bs, hostK, hostb = [], [], [], [], []
     for n in levels:
         p = P.Plan((n, n, n), bc=BC)
+        set_routes(p, route32)
         K, faces = host_level(n, sp, contrast, [p.nodes(0), p.nodes(1), p.nodes(2)])
         Kd = torch.from_numpy(K).cuda()
         bd = p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"),
@@ -238,6 +254,7 @@ def apply_only(args, n):
     bits = args.apply_only or args.fdm_only
     dt = torch.float32 if bits == 32 else torch.float64
     p = P.Plan((n, n, n), bc=BC)
+    set_routes(p, args.route32)
     X, Y, Z = p.mesh()
     K = torch.from_numpy(W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0,
                                                   args.contrast)).to("cuda", dt)
@@ -338,7 +355,7 @@ def main():
     if args.workload == "batch":
         batch_workload(args)
         return
-    plans, Ks, bs, hostK, hostb = setup_gpu(levels, args.contrast)
+    plans, Ks, bs, hostK, hostb = setup_gpu(levels, args.contrast, args.route32)
     opts = dict(mode=1, rtol=1e-12, reorth=args.reorth, inner_rtol=args.inner_rtol,
                 restart=args.restart, use_graph=args.use_graph)
     stream = torch.cuda.current_stream()

@@ -54,8 +54,13 @@ enum cheb_prec { CHEB_FP64 = 0, CHEB_FP32 = 1 };
 enum cheb_solve_mode { CHEB_SOLVE_FP64 = 0, CHEB_SOLVE_MIXED = 1 };
 
 /* per-axis line-derivative route: FFT-based DCT-I + recurrence, or the
- * dense differentiation matrix.  CHEB_ROUTE_AUTO lets the plan choose. */
-enum cheb_route { CHEB_ROUTE_AUTO = -1, CHEB_ROUTE_TRANSFORM = 0, CHEB_ROUTE_DENSE = 1 };
+ * dense differentiation matrix.  CHEB_ROUTE_AUTO lets the plan choose.
+ * CHEB_ROUTE_TENSOR (FP32 operator apply only): the dense matrix on the
+ * tensor cores (split-TF32 tcgen05 contractions, FP32-level accuracy);
+ * needs a 2-D or 3-D grid, 33 <= n <= 257 on the axis and at least 128
+ * lines; the other FP32 line operations of that axis (derivative, adjoint)
+ * then use the transform route where it exists, else the dense one. */
+enum cheb_route { CHEB_ROUTE_AUTO = -1, CHEB_ROUTE_TRANSFORM = 0, CHEB_ROUTE_DENSE = 1, CHEB_ROUTE_TENSOR = 2 };
 
 enum cheb_status {
   CHEB_OK = 0,
@@ -90,6 +95,10 @@ int cheb_plan_set_stream(cheb_plan plan, void* stream);
  * allow it.  get_route reports the FP64 route. */
 int cheb_plan_set_route(cheb_plan plan, int axis, int route);
 int cheb_plan_get_route(cheb_plan plan, int axis, int* route);
+/* The FP32 route of one axis alone (CHEB_ROUTE_TRANSFORM, _DENSE, _TENSOR
+ * or _AUTO); same errors as cheb_plan_set_route.  get_route32 reports it. */
+int cheb_plan_set_route32(cheb_plan plan, int axis, int route);
+int cheb_plan_get_route32(cheb_plan plan, int axis, int* route);
 
 /* Autotuner: for every active axis whose size allows both routes, time
  * the operator line pass with the transform route and with the dense route

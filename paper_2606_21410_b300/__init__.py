@@ -20,7 +20,7 @@ from ._lib import ChebError, SolveInfo, SolveOpts, check, lib  # noqa: F401
 DIRICHLET, NEUMANN = 0, 1
 FP64, FP32 = 0, 1
 SOLVE_FP64, SOLVE_MIXED = 0, 1
-ROUTE_AUTO, ROUTE_TRANSFORM, ROUTE_DENSE = -1, 0, 1
+ROUTE_AUTO, ROUTE_TRANSFORM, ROUTE_DENSE, ROUTE_TENSOR = -1, 0, 1, 2
 PRECOND_NONE, PRECOND_FDM = 0, 2
 
 
@@ -98,13 +98,23 @@ class Plan:
     def set_route(self, axis: int, route: int):
         check(lib.cheb_plan_set_route(self._h, axis, route), "cheb_plan_set_route")
 
+    def set_route32(self, axis: int, route: int):
+        """FP32 route of one axis alone (ROUTE_TENSOR: the operator apply on
+        the tensor cores)."""
+        check(lib.cheb_plan_set_route32(self._h, axis, route), "cheb_plan_set_route32")
+
+    def route32(self, axis: int) -> int:
+        r = C.c_int()
+        check(lib.cheb_plan_get_route32(self._h, axis, C.byref(r)), "cheb_plan_get_route32")
+        return r.value
+
     def autotune(self, cache: str | None = None) -> dict:
         """Pick the faster line-derivative route per axis and precision
         (``cheb_autotune``); cache: optional decision file."""
         out = (C.c_int * 6)()
         self._sync_stream()
         check(lib.cheb_autotune(self._h, cache.encode() if cache else None, out), "cheb_autotune")
-        names = {0: "transform", 1: "dense"}
+        names = {0: "transform", 1: "dense", 2: "tensor"}
         return {"fp64": [names[out[a]] for a in range(self.dim)],
                 "fp32": [names[out[3 + a]] for a in range(self.dim)]}
 

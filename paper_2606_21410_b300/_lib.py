@@ -70,6 +70,8 @@ _SIGS = {
     "cheb_plan_set_stream": (i32, [vp, vp]),
     "cheb_plan_set_route": (i32, [vp, i32, i32]),
     "cheb_plan_get_route": (i32, [vp, i32, i32p]),
+    "cheb_plan_set_route32": (i32, [vp, i32, i32]),
+    "cheb_plan_get_route32": (i32, [vp, i32, i32p]),
     "cheb_nodes": (i32, [vp, i32, f64p]),
     "cheb_autotune": (i32, [vp, C.c_char_p, i32p]),
     "cheb_plan_size": (C.c_size_t, [vp]),

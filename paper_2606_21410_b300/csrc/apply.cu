@@ -21,6 +21,7 @@
 #include <atomic>
 
 #include "device.cuh"
+#include "umma.h"
 
 namespace cheb {
 
@@ -614,7 +615,14 @@ int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u
     nblocks = nbx * (axis == 1 ? g.n[2] : g.n[1]);
   }
   if (nblocks == 0) return CHEB_OK;
-  const int route = sizeof(T) == 4 ? t.route32 : t.route;
+  int route = sizeof(T) == 4 ? t.route32 : t.route;
+  if (route == CHEB_ROUTE_TENSOR) {
+    if constexpr (sizeof(T) == 4) {
+      if (kind == kApplyFirst || kind == kApplyAcc)
+        return tensor_apply_pass(p, axis, kind == kApplyFirst, K, u, out, s);
+    }
+    route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  }
   if (route == CHEB_ROUTE_DENSE)
     return launch_kernel<T, CHEB_ROUTE_DENSE, 0, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
   switch (t.P) {

@@ -40,7 +40,8 @@ struct Geom {
   int bc[6];
 };
 
-struct Workspace;  // Krylov / solver workspace (solve.cu)
+struct Workspace;    // Krylov / solver workspace (solve.cu)
+struct TensorApply;  // tensor-core route resources (umma.cu)
 
 }  // namespace cheb
 
@@ -54,6 +55,7 @@ struct cheb_plan_s {
   int device = 0;
   cheb::AxisTables ax[3];
   cheb::Workspace* ws = nullptr;
+  cheb::TensorApply* tap = nullptr;
   size_t size() const { return (size_t)n[0] * n[1] * n[2]; }
   cheb::Geom geom() const {
     cheb::Geom g;

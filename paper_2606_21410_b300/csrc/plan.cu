@@ -9,6 +9,7 @@
 
 #include "hostmath.h"
 #include "internal.h"
+#include "umma.h"
 
 namespace cheb {
 
@@ -233,6 +234,8 @@ int cheb_plan_create(cheb_plan* out, int dim, const int n[3], const double lo[3]
 int cheb_plan_destroy(cheb_plan p) {
   if (!p) return CHEB_OK;
   free_workspace(p);
+  tensor_apply_free(p->tap);
+  p->tap = nullptr;
   for (int a = 0; a < 3; ++a) free_axis(p->ax[a]);
   delete p;
   return CHEB_OK;
@@ -259,6 +262,33 @@ int cheb_plan_set_route(cheb_plan p, int axis, int route) {
   }
   t.route = route;
   t.route32 = route;
+  return CHEB_OK;
+}
+
+int cheb_plan_set_route32(cheb_plan p, int axis, int route) {
+  if (!p || axis < 0 || axis >= p->dim) { set_error("bad plan or axis"); return CHEB_ERR_ARG; }
+  AxisTables& t = p->ax[axis];
+  if (route == CHEB_ROUTE_AUTO) route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  if (route == CHEB_ROUTE_TRANSFORM && !t.transform_ok) {
+    set_error("transform route needs n - 1 a power of two in [4, 256]"); return CHEB_ERR_UNSUPPORTED;
+  }
+  if (route == CHEB_ROUTE_DENSE && !t.dense_ok) {
+    set_error("dense route needs n <= 129"); return CHEB_ERR_UNSUPPORTED;
+  }
+  if (route == CHEB_ROUTE_TENSOR && !tensor_route_ok(p, axis)) {
+    set_error("tensor route needs a 2-D or 3-D grid, 33 <= n <= 257 and at least 128 lines");
+    return CHEB_ERR_UNSUPPORTED;
+  }
+  if (route != CHEB_ROUTE_TRANSFORM && route != CHEB_ROUTE_DENSE && route != CHEB_ROUTE_TENSOR) {
+    set_error("unknown route"); return CHEB_ERR_ARG;
+  }
+  t.route32 = route;
+  return CHEB_OK;
+}
+
+int cheb_plan_get_route32(cheb_plan p, int axis, int* route) {
+  if (!p || !route || axis < 0 || axis >= p->dim) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  *route = p->ax[axis].route32;
   return CHEB_OK;
 }
 

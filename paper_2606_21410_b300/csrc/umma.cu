@@ -27,9 +27,12 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <vector>
 #include <cstring>
 #include <mutex>
 
+#include "device.cuh"
+#include "hostmath.h"
 #include "umma.h"
 
 namespace cheb {
@@ -537,6 +540,449 @@ int launch_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M
   return CHEB_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Tensor-core route of the operator apply.  The line derivative is the dense
+// collocation matrix, f' = D f on every line (Sec. 2.2), so the interior rows
+// of A u = -sum_a D_a (K (D_a u)) are two contractions per axis:
+//   phase 1: Q = K * (D_a u) on every node, and (D_a u) at the two ends of
+//            every a-line (the normal derivatives of the Neumann rows);
+//   phase 2: out (+)= -(D_a Q) on interior nodes, and the boundary rows
+//            (Dirichlet: u; Neumann of this axis: the signed end derivative)
+//            with the owner rule of the line passes.
+// Tile: 128 a-lines (UMMA M = 128) x nA output points (UMMA N, in groups of
+// at most 256 columns), K = the points of the line in chunks of 16 (64-byte
+// swizzle).  The converter warps read the line tile from global memory (the
+// odd grid extents rule out TMA for it: rows of 257 floats are not 16-byte
+// strided) and write its TF32 hi/lo split in the swizzled K-major layout;
+// D comes pre-split by TMA.  Same warp roles, bounded waits and teardown as
+// the contraction kernel above.
+// ---------------------------------------------------------------------------
+constexpr int kDK = 16;      // K chunk (one 64-byte swizzle row)
+constexpr int kDStages = 4;
+
+// Line L of axis a starts at base(L) with point stride stride(); 32-bit
+// offsets (grids have < 2^31 points).
+struct LineGeo {
+  int axis, nx, ny, n, nl;
+  __device__ __forceinline__ int base(int L) const {
+    return axis == 0 ? L * nx : (axis == 1 ? (L / nx) * (nx * ny) + (L % nx) : L);
+  }
+  __device__ __forceinline__ int stride() const { return axis == 0 ? 1 : (axis == 1 ? nx : nx * ny); }
+  __device__ __forceinline__ void node(int L, int pt, int& i, int& j, int& k) const {
+    if (axis == 0) { i = pt; j = L % ny; k = L / ny; }
+    else if (axis == 1) { i = L % nx; j = pt; k = L / nx; }
+    else { i = L % nx; j = L / nx; k = pt; }
+  }
+};
+
+struct DenseArgs {
+  Geom g;
+  int phase, first;
+  const float* src;  // u (phase 1) or Q (phase 2)
+  const float* K;    // phase 1
+  float* Q;          // phase 1 output
+  float2* ends;      // (D u) at points 0 and n-1 of every line
+  const float* u;    // phase 2: Dirichlet rows
+  float* out;        // phase 2
+};
+
+// shared-memory bytes of the dense pass for nA output columns
+size_t dense_smem_bytes(int nA) {
+  return 1024 + (size_t)kDStages * (2u * kBM + 2u * (size_t)nA) * (kDK * 4) + 256 + 128 * 17 * 4 +
+         4 * 32 * 32 * 4 + 4 * 32 * 8;
+}
+
+// Boundary rows in phase 2.  A line either runs through the interior of the
+// other axes (its points 1 .. n-2 are interior nodes: out (+)= -C), or lies in
+// a face of another axis (its points 1 .. n-2 all have the same owner face:
+// Dirichlet -> u on the first pass, Neumann of the other axis -> 0 on the
+// first pass, else untouched).  The two line ends are boundary nodes of this
+// axis and take the owner rule per node.  The grid and boundary set are held
+// in registers (a Dirichlet-face bit mask).
+struct BcInfo {
+  int nx, ny, nz, dim, dmask, first, axis;
+  __device__ __forceinline__ int owner(int i, int j, int k) const {
+    // Dirichlet faces beat Neumann faces, then the lowest axis (node index 0
+    // of an axis is its hi face 2a + 1, index n - 1 the lo face 2a)
+    int fd = -1, fn = -1;
+    const int f0 = i == 0 ? 1 : (i == nx - 1 ? 0 : -1);
+    const int f1 = dim > 1 ? (j == 0 ? 3 : (j == ny - 1 ? 2 : -1)) : -1;
+    const int f2 = dim > 2 ? (k == 0 ? 5 : (k == nz - 1 ? 4 : -1)) : -1;
+    if (f2 >= 0) { if ((dmask >> f2) & 1) fd = f2; else fn = f2; }
+    if (f1 >= 0) { if ((dmask >> f1) & 1) fd = f1; else fn = f1; }
+    if (f0 >= 0) { if ((dmask >> f0) & 1) fd = f0; else fn = f0; }
+    return fd >= 0 ? fd : fn;
+  }
+};
+// class of the points 1 .. n-2 of a line (phase 2)
+enum LineClass { kLineInterior = 0, kLineCopyU = 1, kLineZero = 2, kLineSkip = 3 };
+
+template <bool XAX>
+__global__ void __launch_bounds__(kUThreads, 1)
+    dense_pass_kernel(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
+                      const LineGeo lg, const DenseArgs A, int nA, int tmem_cols, int nbuf) {
+  constexpr int S = kDStages;
+  constexpr uint32_t RB = kDK * 4;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const uint32_t xbytes = kBM * RB, dbytes = (uint32_t)nA * RB;
+  const uint32_t stage_bytes = 2u * xbytes + 2u * dbytes;  // [Xh | Xl | Dh | Dl]
+  const uint32_t bars = base + S * stage_bytes;
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto conv = [&](int s) { return bars + 8u * (S + s); };
+  auto empty = [&](int s) { return bars + 8u * (2 * S + s); };
+  auto tfull = [&](int b) { return bars + 8u * (3 * S + b); };
+  auto tempty = [&](int b) { return bars + 8u * (3 * S + 2 + b); };
+  const uint32_t fin = bars + 8u * (3 * S + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * stage_bytes + 8 * (3 * S + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* rawt = reinterpret_cast<float*>(gbase + S * stage_bytes + 256);  // 128 x 17 (x-lines)
+  float* stg = rawt + 128 * 17;                                            // 4 x 32 x 32 (x-lines)
+  float2* endw = reinterpret_cast<float2*>(stg + 4 * 32 * 32);             // 4 x 32
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = lg.n;
+  const int nchunks = (n + kDK - 1) / kDK;
+  const int ntiles = (lg.nl + kBM - 1) / kBM;
+  const int ng = nA > 256 ? 2 : 1;  // MMA column groups
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(conv(s), 128);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 128);
+    }
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(nbuf * tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmDh)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmDl)) : "memory");
+      int last[S];
+      for (int s = 0; s < S; ++s) last[s] = -1;
+      int g = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int s = g % S;
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+          const uint32_t st = base + s * stage_bytes + 2u * xbytes;
+          mbar_expect_tx(full(s), 2u * dbytes);
+          // D rows in two boxes of nA / 2 rows each (a box has at most 256 rows)
+          tma_load_2d(st, &tmDh, full(s), c * kDK, 0);
+          tma_load_2d(st + dbytes / 2, &tmDh, full(s), c * kDK, nA / 2);
+          tma_load_2d(st + dbytes, &tmDl, full(s), c * kDK, 0);
+          tma_load_2d(st + dbytes + dbytes / 2, &tmDl, full(s), c * kDK, nA / 2);
+          last[s] = g;
+        }
+      }
+      if (*abort_flag)
+        for (int s = 0; s < S; ++s)
+          if (last[s] >= 0) mbar_drain(full(s), (uint32_t)(last[s] / S) & 1u);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int g = 0, it = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++it) {
+        const int b = it % nbuf, use = it / nbuf;
+        const uint32_t d = tmem + (uint32_t)(b * tmem_cols);
+        if (!mbar_wait(tempty(b), ((uint32_t)use & 1u) ^ 1u, abort_flag)) break;
+        tc_fence_after();
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int s = g % S;
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(conv(s), ph, abort_flag) || !mbar_wait(full(s), ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + s * stage_bytes;
+#pragma unroll
+          for (int kk = 0; kk < kDK / 8; ++kk) {
+            const uint64_t ah = sdesc_k<kDK>(st + 32u * kk);
+            const uint64_t al = sdesc_k<kDK>(st + xbytes + 32u * kk);
+            for (int gi = 0; gi < ng; ++gi) {
+              const int nb = gi == 0 ? (nA < 256 ? nA : 256) : nA - 256;
+              const uint32_t idesc = idesc_tf32(kBM, nb);
+              const uint32_t boff = (uint32_t)gi * 256u * RB;
+              const uint64_t bh = sdesc_k<kDK>(st + 2u * xbytes + boff + 32u * kk);
+              const uint64_t bl = sdesc_k<kDK>(st + 2u * xbytes + dbytes + boff + 32u * kk);
+              const uint32_t dc = d + (uint32_t)(gi * 256);
+              umma_tf32(dc, ah, bh, idesc, (c | kk) != 0);
+              umma_tf32(dc, ah, bl, idesc, 1u);
+              umma_tf32(dc, al, bh, idesc, 1u);
+            }
+          }
+          umma_commit(empty(s));
+        }
+        if (!ok) break;
+        umma_commit(tfull(b));
+      }
+      umma_commit(fin);
+      mbar_drain(fin, 0);
+    }
+    __syncwarp();
+  } else if (warp >= 4 && warp < 8) {
+    // converters: one line per thread; the global loads of chunk c + 1 are
+    // in flight while chunk c waits for its stage and is split
+    const int t = threadIdx.x - 128;
+    const int stride = lg.stride();
+    int g = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const int L0 = tile * kBM, L = L0 + t;
+      const bool lv = L < lg.nl;
+      const int lb = lv ? lg.base(L) : 0;
+      // x-lines: element e = t + 128 r of the 128 x 16 chunk (16 threads per
+      // line, coalesced); other axes: point kk of this thread's line
+      auto load = [&](int c, float (&w)[kDK]) {
+#pragma unroll
+        for (int r = 0; r < kDK; ++r) {
+          if (XAX) {
+            const int e = t + 128 * r, m = e >> 4, pt = c * kDK + (e & 15), Lm = L0 + m;
+            w[r] = (Lm < lg.nl && pt < n) ? __ldcg(A.src + Lm * lg.nx + pt) : 0.f;
+          } else {
+            const int pt = c * kDK + r;
+            w[r] = (lv && pt < n) ? __ldcg(A.src + lb + pt * stride) : 0.f;
+          }
+        }
+      };
+      float cur[kDK];
+      load(0, cur);
+      for (int c = 0; c < nchunks; ++c, ++g) {
+        const int s = g % S;
+        const uint32_t ph = (uint32_t)(g / S) & 1u;
+        float nxt[kDK];
+        if (c + 1 < nchunks) load(c + 1, nxt);
+        float v[kDK];
+        if (XAX) {
+#pragma unroll
+          for (int r = 0; r < kDK; ++r) {
+            const int e = t + 128 * r;
+            rawt[(e >> 4) * 17 + (e & 15)] = cur[r];
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+          for (int kk = 0; kk < kDK; ++kk) v[kk] = rawt[t * 17 + kk];
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < kDK; ++kk) v[kk] = cur[kk];
+        }
+        // the stage is free once the MMAs of its previous use completed
+        if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        uint8_t* xh = gbase + s * stage_bytes + t * RB;
+        uint8_t* xl = xh + xbytes;
+#pragma unroll
+        for (int q = 0; q < kDK / 4; ++q) {
+          // 64-byte swizzle: 16-byte granule q of row t sits at q ^ ((t >> 1) & 3)
+          const int gp = q ^ ((t >> 1) & 3);
+          float4 h, l;
+          h.x = tf32_rna(v[4 * q + 0]); l.x = tf32_rna(v[4 * q + 0] - h.x);
+          h.y = tf32_rna(v[4 * q + 1]); l.y = tf32_rna(v[4 * q + 1] - h.y);
+          h.z = tf32_rna(v[4 * q + 2]); l.z = tf32_rna(v[4 * q + 2] - h.z);
+          h.w = tf32_rna(v[4 * q + 3]); l.w = tf32_rna(v[4 * q + 3] - h.w);
+          *reinterpret_cast<float4*>(xh + gp * 16) = h;
+          *reinterpret_cast<float4*>(xl + gp * 16) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(conv(s));
+#pragma unroll
+        for (int r = 0; r < kDK; ++r) cur[r] = nxt[r];
+      }
+    }
+  } else if (warp >= 8) {
+    const int q = warp & 3;
+    const int stride = lg.stride();
+    float* sw = stg + q * 32 * 32;  // this warp's 32 x 32 staging block (x-lines)
+    BcInfo bi;
+    bi.nx = A.g.n[0];
+    bi.ny = A.g.n[1];
+    bi.nz = A.g.n[2];
+    bi.dim = A.g.dim;
+    bi.dmask = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) bi.dmask |= (A.g.bc[f] == CHEB_DIRICHLET ? 1 : 0) << f;
+    bi.first = A.first;
+    bi.axis = lg.axis;
+    const int phase = A.phase, first = A.first;
+    const float* Kp = A.K;
+    float* Qp = A.Q;
+    float* outp = A.out;
+    const float* up = A.u;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+      const int b = it % nbuf, use = it / nbuf;
+      if (!mbar_wait(tfull(b), (uint32_t)use & 1u, abort_flag)) break;
+      tc_fence_after();
+      const int Lw = tile * kBM + 32 * q;  // first line of this warp
+      const int L = Lw + lane;
+      const bool lv = L < lg.nl;
+      const int lb = lv ? lg.base(L) : 0;
+      const uint32_t tl = tmem + (uint32_t)(b * tmem_cols) + ((uint32_t)(32 * q) << 16);
+      // line class (phase 2) from its point 1
+      int cls = kLineSkip;
+      int ci, cj, ck;
+      lg.node(lv ? L : 0, 1, ci, cj, ck);
+      if (phase == 2 && lv) {
+        const int o = bi.owner(ci, cj, ck);
+        if (o < 0) cls = kLineInterior;
+        else if (!first) cls = kLineSkip;
+        else cls = ((bi.dmask >> o) & 1) ? kLineCopyU : kLineZero;
+      }
+      float e0 = 0.f, eN = 0.f;
+      if (phase == 2 && lv) {
+        const float2 e = A.ends[L];
+        e0 = e.x;
+        eN = e.y;
+      }
+      if (XAX) {
+        endw[q * 32 + lane] = make_float2(__int_as_float(cls), 0.f);
+        __syncwarp();
+      }
+      const int ncol = phase == 1 ? nA : n;
+      // 16 columns at a time (x-lines: 32-column staging blocks, two halves);
+      // every global load of a block is issued before its stores
+      for (int col = 0; col < ncol; col += 16) {
+        float v[16];
+        if (col < nA) {
+          tmem_ld16(tl + (uint32_t)col, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = 0.f;
+        }
+        if (phase == 1) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (col + j == 0) e0 = v[j];
+            if (col + j == n - 1) eN = v[j];
+          }
+        }
+        if (XAX) {
+          const int half = (col >> 4) & 1;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) sw[lane * 32 + ((16 * half + j) ^ lane)] = v[j];
+          if (!half && col + 16 < ncol) continue;
+          __syncwarp();
+          const int pt = (col & ~31) + lane;
+          const bool pin = pt > 0 && pt < n - 1;
+          float ld[32];
+#pragma unroll
+          for (int r = 0; r < 32; ++r) {
+            const int Lr = Lw + r;
+            const int idx = Lr * lg.nx + pt;
+            ld[r] = 0.f;
+            if (Lr < lg.nl && pt < n) {
+              if (phase == 1) {
+                ld[r] = __ldcg(Kp + idx);
+              } else if (pin) {
+                const int c = __float_as_int(endw[q * 32 + r].x);
+                if (c == kLineInterior && !first) ld[r] = __ldcg(outp + idx);
+                else if (c == kLineCopyU) ld[r] = __ldcg(up + idx);
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 32; ++r) {
+            const int Lr = Lw + r;
+            if (Lr >= lg.nl || pt >= n) continue;
+            const int idx = Lr * lg.nx + pt;
+            const float C = sw[r * 32 + (lane ^ r)];
+            if (phase == 1) {
+              __stcg(Qp + idx, ld[r] * C);
+            } else if (pin) {
+              const int c = __float_as_int(endw[q * 32 + r].x);
+              if (c == kLineInterior) __stcg(outp + idx, ld[r] - C);
+              else if (c == kLineCopyU) __stcg(outp + idx, ld[r]);
+              else if (c == kLineZero) __stcg(outp + idx, 0.f);
+            }
+          }
+          __syncwarp();
+        } else if (lv) {
+          float ld[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int pt = col + j;
+            const int idx = lb + pt * stride;
+            ld[j] = 0.f;
+            if (phase == 1) {
+              if (pt < n) ld[j] = __ldcg(Kp + idx);
+            } else if (pt > 0 && pt < n - 1) {
+              if (cls == kLineInterior && !first) ld[j] = __ldcg(outp + idx);
+              else if (cls == kLineCopyU) ld[j] = __ldcg(up + idx);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int pt = col + j;
+            const int idx = lb + pt * stride;
+            if (phase == 1) {
+              if (pt < n) __stcg(Qp + idx, ld[j] * v[j]);
+            } else if (pt > 0 && pt < n - 1) {
+              if (cls == kLineInterior) __stcg(outp + idx, ld[j] - v[j]);
+              else if (cls == kLineCopyU) __stcg(outp + idx, ld[j]);
+              else if (cls == kLineZero) __stcg(outp + idx, 0.f);
+            }
+          }
+        }
+      }
+      // accumulator drained: hand it back to the MMA issuer
+      tc_fence_before();
+      mbar_arrive(tempty(b));
+      if (phase == 1 && lv) A.ends[L] = make_float2(e0, eN);
+      if (phase == 2 && lv) {
+        // the two line ends: boundary nodes of this axis, owner rule per node
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const int pt = side ? n - 1 : 0;
+          int i, jj, k;
+          lg.node(L, pt, i, jj, k);
+          const int idx = lb + pt * stride;
+          const int o = bi.owner(i, jj, k);
+          if ((bi.dmask >> o) & 1) {
+            if (first) outp[idx] = up[idx];
+          } else if ((o >> 1) == lg.axis) {
+            // hi face (side 1) is line point 0, lo face (side 0) is point n - 1
+            outp[idx] = (o & 1) ? e0 : -eN;
+          } else if (first) {
+            outp[idx] = 0.f;  // Neumann row of another axis: written by that axis' pass
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(nbuf * tmem_cols)
+                 : "memory");
+  }
+}
 }  // namespace
 
 int umma_n_tile(int N) { return (N + 15) / 16 * 16; }
@@ -573,6 +1019,132 @@ int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, 
   while (tmem_cols < n_tile) tmem_cols *= 2;
   return chunk_k() == 32 ? launch_rot<32>(X, Wh, Wl, Y, M, N, K, n_tile, tmem_cols, ep, s)
                          : launch_rot<16>(X, Wh, Wl, Y, M, N, K, n_tile, tmem_cols, ep, s);
+}
+
+
+// ---------------------------------------------------------------------------
+// tensor-core route of the FP32 operator apply: per-plan resources
+// ---------------------------------------------------------------------------
+struct TensorApply {
+  int nA1[3] = {0, 0, 0};   // phase-1 output columns (all n points), multiple of 16
+  int nA2[3] = {0, 0, 0};   // phase-2 output columns (points 0 .. n-2)
+  int Kp[3] = {0, 0, 0};    // padded K (points), multiple of 16
+  float* Dh[3] = {nullptr, nullptr, nullptr};  // split-TF32 D, nA1 x Kp, zero padded
+  float* Dl[3] = {nullptr, nullptr, nullptr};
+  float* Q = nullptr;       // K * (D_a u), one field
+  float2* ends = nullptr;   // per line: (D_a u) at both ends
+  size_t ends_len = 0;
+};
+
+bool tensor_route_ok(const cheb_plan_s* p, int axis) {
+  if (p->dim < 2 || axis < 0 || axis >= p->dim) return false;
+  const int n = p->n[axis];
+  return n >= 33 && n <= 257 && p->size() / (size_t)n >= (size_t)kBM;
+}
+
+static int tensor_setup(cheb_plan_s* p) {
+  if (p->tap) return CHEB_OK;
+  TensorApply* t = new TensorApply();
+  auto fail = [&](int st) {
+    tensor_apply_free(t);
+    return st;
+  };
+  size_t maxl = 0;
+  for (int a = 0; a < p->dim; ++a) {
+    const int n = p->n[a];
+    t->nA1[a] = umma_n_tile(n);
+    t->nA2[a] = umma_n_tile(n - 1);
+    t->Kp[a] = umma_n_tile(n);
+    maxl = std::max(maxl, p->size() / (size_t)n);
+    if (!tensor_route_ok(p, a)) continue;
+    const std::vector<double> D = dense_deriv_matrix(n - 1, 2.0 / (p->hi[a] - p->lo[a]));
+    const size_t rows = t->nA1[a], cols = t->Kp[a];
+    std::vector<double> P(rows * cols, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) P[i * cols + j] = D[(size_t)i * n + j];
+    std::vector<float> h(P.size()), l(P.size());
+    tf32_split_host(P.data(), P.size(), h.data(), l.data());
+    if (cudaMalloc(&t->Dh[a], sizeof(float) * P.size()) != cudaSuccess ||
+        cudaMalloc(&t->Dl[a], sizeof(float) * P.size()) != cudaSuccess)
+      return fail(CHEB_ERR_NOMEM);
+    if (cudaMemcpy(t->Dh[a], h.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->Dl[a], l.data(), sizeof(float) * P.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(CHEB_ERR_CUDA);
+  }
+  if (cudaMalloc(&t->Q, sizeof(float) * p->size()) != cudaSuccess ||
+      cudaMalloc(&t->ends, sizeof(float2) * maxl) != cudaSuccess)
+    return fail(CHEB_ERR_NOMEM);
+  t->ends_len = maxl;
+  p->tap = t;
+  return CHEB_OK;
+}
+
+void tensor_apply_free(TensorApply* t) {
+  if (!t) return;
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(t->Dh[a]);
+    cudaFree(t->Dl[a]);
+  }
+  cudaFree(t->Q);
+  cudaFree(t->ends);
+  delete t;
+}
+
+template <bool XAX>
+static int launch_dense(const CUtensorMap& mh, const CUtensorMap& ml, const LineGeo& lg, const DenseArgs& A,
+                        int nA, cudaStream_t s) {
+  int tmem_cols = 32;
+  while (tmem_cols < nA) tmem_cols *= 2;
+  const int nbuf = 2 * tmem_cols <= 512 ? 2 : 1;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(dense_pass_kernel<XAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dense_smem_bytes(272));
+  });
+  CHEB_CUDA(attr_err);
+  const int ntiles = (lg.nl + kBM - 1) / kBM;
+  const int grid = std::min(ntiles, sm_count());
+  dense_pass_kernel<XAX><<<grid, kUThreads, dense_smem_bytes(nA), s>>>(mh, ml, lg, A, nA, tmem_cols, nbuf);
+  CHEB_LAUNCH_CHECK("dense_pass_kernel");
+  return CHEB_OK;
+}
+
+int tensor_apply_pass(const cheb_plan_s* pc, int axis, bool first, const float* K, const float* u, float* out,
+                      cudaStream_t s) {
+  cheb_plan_s* p = const_cast<cheb_plan_s*>(pc);  // lazily built route resources
+  if (!tensor_route_ok(p, axis)) {
+    set_error("tensor route needs 33 <= n <= 257 on a 2-D or 3-D grid");
+    return CHEB_ERR_UNSUPPORTED;
+  }
+  int st;
+  if ((st = tensor_setup(p))) return st;
+  TensorApply& t = *p->tap;
+  LineGeo lg;
+  lg.axis = axis;
+  lg.nx = p->n[0];
+  lg.ny = p->n[1];
+  lg.n = p->n[axis];
+  lg.nl = (int)(p->size() / (size_t)lg.n);
+  DenseArgs A;
+  A.g = p->geom();
+  A.first = first ? 1 : 0;
+  A.K = K;
+  A.Q = t.Q;
+  A.ends = t.ends;
+  A.u = u;
+  A.out = out;
+  for (int phase = 1; phase <= 2; ++phase) {
+    const int nA = phase == 1 ? t.nA1[axis] : t.nA2[axis];
+    CUtensorMap mh, ml;
+    if ((st = make_map(&mh, t.Dh[axis], t.Kp[axis], t.nA1[axis], nA / 2, kDK))) return st;
+    if ((st = make_map(&ml, t.Dl[axis], t.Kp[axis], t.nA1[axis], nA / 2, kDK))) return st;
+    A.phase = phase;
+    A.src = phase == 1 ? u : t.Q;
+    st = axis == 0 ? launch_dense<true>(mh, ml, lg, A, nA, s) : launch_dense<false>(mh, ml, lg, A, nA, s);
+    if (st) return st;
+  }
+  return CHEB_OK;
 }
 
 int umma_take_error() {

@@ -48,6 +48,16 @@ bool umma_ok(int M, int N, int K);
 int umma_n_tile(int N);
 // Split-TF32 pair of a row-major matrix (host): hi = tf32(x), lo = tf32(x - hi).
 void tf32_split_host(const double* x, size_t n, float* hi, float* lo);
+// Tensor-core route of the FP32 operator apply (dense D on every line):
+// one axis pass of A u, writing (first) or accumulating into out with the
+// boundary rows of this axis; resources are built on first use and freed
+// with the plan.
+struct TensorApply;
+bool tensor_route_ok(const cheb_plan_s* p, int axis);
+int tensor_apply_pass(const cheb_plan_s* p, int axis, bool first, const float* K, const float* u, float* out,
+                      cudaStream_t s);
+void tensor_apply_free(TensorApply* t);
+
 // Reads and clears the device-side error word the kernel sets when one of
 // its bounded waits gives up (returns 0 when no wait gave up).
 int umma_take_error();

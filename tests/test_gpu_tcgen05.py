@@ -102,3 +102,108 @@ def test_tcgen05_precond_full_size(nn):
     if nn == 129:
         ref = FDMPreconditioner(g, 2.0)(r)
         assert _rel(got64, ref) < 1e-10
+
+
+# ------------------------------------------------ tensor-core route of the apply
+
+def _apply_scale(K, u, g):
+    s = np.abs(K).max() * np.linalg.norm(u)
+    return s * max(np.abs(g.D(a)).max() ** 2 for a in g.axes)
+
+
+TENSOR_CASES = [
+    ((33, 40, 65), [0, 1, 1, 0, 0, 1]),   # ragged 128-line tiles, n = 40 off the transform sizes
+    ((65, 33, 41), [1, 1, 0, 1, 1, 0]),   # Neumann-owned edges and corners
+    ((41, 65, 33), [0] * 6),
+    ((129, 129), [1, 0, 0, 1, 0, 0]),     # 2-D
+    ((129, 257), [0, 1, 1, 0, 0, 0]),     # 257 points: 272 output columns in two MMA groups
+]
+
+
+@pytest.mark.parametrize("n,bc", TENSOR_CASES)
+def test_tensor_route_apply_matches_oracle(n, bc):
+    import paper_2606_21410_b300 as P
+    g = O.Grid(n, bc=bc)
+    p = _plan(n, bc)
+    for a in range(len(n)):
+        p.set_route32(a, P.ROUTE_TENSOR)
+        assert p.route32(a) == P.ROUTE_TENSOR
+    u = W.random_field(g.shape, 31)
+    K = W.random_positive_field(g.shape, 32)
+    ref = O.apply(u, K, g)
+    got = p.apply(_dev(K, torch.float32), _dev(u, torch.float32)).double().cpu().numpy()
+    N = max(n) - 1
+    err = np.linalg.norm(got - ref) / _apply_scale(K, u, g)
+    assert err < 8 * N * N * 1.2e-7, err
+    # boundary rows: Dirichlet rows copy u exactly (in FP32)
+    own = O.owners(g)
+    dmask = np.isin(own, [f for f in range(2 * g.dim) if bc[f] == 0])
+    assert np.array_equal(got[dmask], u.astype(np.float32).astype(np.float64)[dmask])
+
+
+def test_tensor_route_unsupported_sizes_are_refused():
+    import paper_2606_21410_b300 as P
+    p = _plan((17, 33, 33), [0] * 6)
+    with pytest.raises(P.ChebError):
+        p.set_route32(0, P.ROUTE_TENSOR)      # n = 17 < 33
+    q = _plan((65,), [0] * 6)
+    with pytest.raises(P.ChebError):
+        q.set_route32(0, P.ROUTE_TENSOR)      # 1-D: a single line
+
+
+@pytest.mark.parametrize("nn", [129, 257])
+def test_tensor_route_full_size_against_transform_and_samples(nn):
+    """At the solve sizes: the tensor route against the FP32 transform route
+    over the whole field and against the oracle's per-line evaluation at
+    sampled interior nodes."""
+    import paper_2606_21410_b300 as P
+    bc = [0, 0, 1, 1, 1, 1]
+    g = O.Grid((nn,) * 3, bc=bc)
+    X, Y, Z = g.mesh()
+    u = np.sin(2 * X + Y) * np.cos(3 * Z) + 0.01 * W.random_field(g.shape, 33)
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 100.0)
+    pt = _plan((nn,) * 3, bc)
+    pc = _plan((nn,) * 3, bc)
+    for a in range(3):
+        pc.set_route32(a, P.ROUTE_TENSOR)
+    Kd, ud = _dev(K, torch.float32), _dev(u, torch.float32)
+    a_tr = pt.apply(Kd, ud).double().cpu().numpy()
+    a_tc = pc.apply(Kd, ud).double().cpu().numpy()
+    scale = _apply_scale(K, u, g)
+    N = nn - 1
+    assert np.linalg.norm(a_tc - a_tr) / scale < 8 * N * N * 1.2e-7
+    rng = W.rng(34)
+    pts = [tuple(int(v) for v in rng.integers(1, nn - 1, size=3)) for _ in range(100)]
+    ref = []
+    for (k, j, i) in pts:
+        v = 0.0
+        idx = {0: i, 1: j, 2: k}
+        for a in g.axes:
+            D = g.D(a)
+            sl = [k, j, i]
+            sl[2 - a] = slice(None)
+            v -= D[idx[a]] @ (K[tuple(sl)] * (D @ u[tuple(sl)]))
+        ref.append(v)
+    ref = np.array(ref)
+    vals = np.array([a_tc[k, j, i] for (k, j, i) in pts])
+    assert np.abs(vals - ref).max() / np.abs(ref).max() < 20 * 8 * N * N * 1.2e-7
+
+
+def test_tensor_route_mixed_solve_matches_fp64():
+    """A mixed-precision solve whose FP32 applies run on the tensor route
+    reaches the FP64 solution (the refinement is in FP64)."""
+    import paper_2606_21410_b300 as P
+    n = (65, 65, 65)
+    bc = [0, 0, 1, 1, 0, 0]
+    g = O.Grid(n, bc=bc)
+    X, Y, Z = g.mesh()
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 10.0)
+    b = W.random_field(g.shape, 35)
+    p64 = _plan(n, bc)
+    u64, i64 = p64.solve(_dev(K), _dev(b), mode=0, rtol=1e-12)
+    pm = _plan(n, bc)
+    for a in range(3):
+        pm.set_route32(a, P.ROUTE_TENSOR)
+    um, im = pm.solve(_dev(K), _dev(b), mode=1, rtol=1e-12)
+    assert im["status"] == 0 and im["applies_fp32"] > 0
+    assert _rel(um.cpu().numpy(), u64.cpu().numpy()) < 1e-9
