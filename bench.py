@@ -51,7 +51,7 @@ def parse():
                     help="hierarchy: the 257^3 hierarchical solve (the metric); batch: 16 uneven "
                          "lognormal Picard instances solved concurrently (a secondary line)")
     ap.add_argument("--use-graph", type=int, default=0)
-    ap.add_argument("--route32", default="transform", choices=["transform", "tensor"],
+    ap.add_argument("--route32", default="tensor", choices=["transform", "tensor"],
                     help="FP32 operator-apply route: FFT line transforms, or the dense "
                          "derivative on the tensor cores (tcgen05)")
     ap.add_argument("--fdm-only", type=int, default=0, metavar="BITS",
@@ -469,7 +469,17 @@ def main():
     tp32 = time_prec(torch.float32)
     apply["fdm_fp32_ms"] = tp32 * 1e3
 
-    # ---- roofline of the dominant kernel group
+    # ---- roofline of the dominant kernel: the FP32 apply passes (the largest
+    # single-kernel share of the solve; the Arnoldi dot/axpy work is split
+    # over two kernels).  Per launch = the finest-level apply time (CUDA events
+    # on the plan stream around 20 applies, right after the timed region) /
+    # launches; the level-mixed per-apply time of the timed solve itself (phase
+    # profiler) is reported beside it.  Algorithmic bytes per apply (FP32
+    # words per DOF):
+    #   tensor route: x 3 + 2 (phase 1 reads u, K, writes Q; phase 2 of the
+    #   first axis reads Q, writes out), y and z 3 + 3 (phase 2 also reads the
+    #   accumulated out) = 17 words over 6 launches;
+    #   transform route: x 3, y 4, z 4 = 11 words over 3 launches.
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -477,37 +487,34 @@ def main():
         pass
     hbm = peaks.get("hbm_gbs", 6400.0)
     bf16 = peaks.get("bf16_tflops", 1800.0)
-    top = max(phase, key=lambda k: phase[k]["ms"])
+    tensor_route = args.route32 == "tensor"
+    launches_per_apply = 6 if tensor_route else 3
+    words = 17.0 if tensor_route else 11.0
+    ph = phase.get("apply32", {"ms": 0.0, "count": 0})
+    per = t32 / launches_per_apply
+    algo = words * 4 * ntot / launches_per_apply
+    roof = {"bound": "hbm",
+            "kernel": ("dense_pass_kernel (tcgen05 split-TF32 FP32 apply, 6 launches per apply)"
+                       if tensor_route else "tf_pass_kernel (FP32 apply, 3 launches per apply)"),
+            "achieved": algo / per / 1e9, "peak": hbm, "unit": "GB/s", "frac": algo / per / 1e9 / hbm,
+            "traffic": None, "algorithmic_bytes_per_launch": algo,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
+            "apply_ms_finest": t32 * 1e3,
+            "apply_ms_timed_solve_all_levels": (ph["ms"] / ph["count"]) if ph["count"] else None}
+    if tensor_route:
+        flops = 2.0 * ntot * levels[-1] * 6  # useful dense-D flops of one apply
+        roof["tensor_tflops_useful"] = flops / t32 / 1e12
+        roof["tensor_frac_split_tf32"] = 3.0 * flops / t32 / 1e12 / (bf16 * 1.1 / 2.25)
+    # preconditioner contractions beside it (tcgen05, tensor bound)
     m = nf - 2
-    if top.startswith("prec"):
-        # 6 dense contractions of m x m matrices per application: 12 m^4 flops
-        # (FP32 operands on the TF32 tensor cores with the split-TF32 scheme,
-        # which issues 3 TF32 products per algorithmic product)
-        flops = 12.0 * m ** 4
-        tf32_peak = bf16 * (1.1 / 2.25)
-        ach = flops / tp32 / 1e12
-        roof = {"bound": "tensor", "kernel": "fdm preconditioner (gemm_tf32x3_kernel contractions + "
-                                              "lift/scale/scatter/face kernels), 257^3 FP32",
-                "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
-                "traffic": None,
-                "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 ratio)",
-                "note": "split-TF32 issues 3 TF32 MMAs per algorithmic flop: tensor-pipe work = 3x achieved"}
-    else:
-        words = 11.0 / 3.0 if top.startswith("apply") else None
-        per = t32 / 3.0
-        if words is not None:
-            algo = words * 4 * ntot
-            roof = {"bound": "hbm", "kernel": "tf_pass_kernel (FP32 apply, per launch)",
-                    "achieved": algo / per / 1e9, "peak": hbm, "unit": "GB/s",
-                    "frac": algo / per / 1e9 / hbm, "traffic": None}
-        else:
-            roof = {"bound": "hbm", "kernel": top, "achieved": None, "peak": hbm, "unit": "GB/s",
-                    "frac": None, "traffic": None}
-    # apply kernel roofline, stated beside (the hot path's streaming kernel)
-    apply_roof = {"bound": "hbm", "kernel": "tf_pass_kernel (FP32 apply, 3 launches)",
-                  "achieved": 11 * 4 * ntot / t32 / 1e9, "peak": hbm, "unit": "GB/s",
-                  "frac": 11 * 4 * ntot / t32 / 1e9 / hbm,
-                  "algorithmic_bytes": "11 words/DOF over the three axis passes"}
+    fl = 12.0 * m ** 4
+    tf32_peak = bf16 * (1.1 / 2.25)
+    prec_roof = {"bound": "tensor", "kernel": "umma_tf32x3_rot_kernel (FDM contractions, 6 per application)",
+                 "achieved": fl / tp32 / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
+                 "frac": fl / tp32 / 1e12 / tf32_peak,
+                 "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 ratio)",
+                 "note": "whole preconditioner time; split-TF32 issues 3 TF32 MMAs per useful flop"}
+    apply_roof = prec_roof
 
     # ---- CPU baseline (oracle on the host cores, bounded sample)
     cpu = None
@@ -531,7 +538,7 @@ def main():
             "refinements_per_level": [i["refinements"] for i in infos],
             "rel_residual": infos[-1]["rel_residual"], "e_ref": eref,
             "apply": apply, "fp64": fp64, "phase_ms_per_step": phase,
-            "roofline": roof, "apply_roofline": apply_roof,
+            "roofline": roof, "prec_roofline": apply_roof, "fp32_route": args.route32,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

@@ -100,10 +100,10 @@ int cheb_plan_get_route(cheb_plan plan, int axis, int* route);
 int cheb_plan_set_route32(cheb_plan plan, int axis, int route);
 int cheb_plan_get_route32(cheb_plan plan, int axis, int* route);
 
-/* Autotuner: for every active axis whose size allows both routes, time
- * the operator line pass with the transform route and with the dense route
- * (FP64 and FP32 separately, on the plan's grid and stream) and keep the
- * faster.  cache_path (nullable) names a text file of earlier decisions,
+/* Autotuner: for every active axis whose size allows more than one route,
+ * time the operator line pass with each of them - transform, dense and,
+ * for FP32, tensor (CHEB_ROUTE_TENSOR) - FP64 and FP32 separately, on the
+ * plan's grid and stream, and keep the fastest.  cache_path (nullable) names a text file of earlier decisions,
  * one line per (GPU name, axis size, precision); hits skip the timing and
  * new decisions are appended.  routes_out[6] (nullable) receives the FP64
  * routes of axes x, y, z then the FP32 routes.  Allocates three temporary

@@ -1,7 +1,7 @@
 // Route autotuner: for every active axis and both precisions, time the
-// operator line pass on the plan's own grid with the FFT transform route and
-// with the dense differentiation-matrix route (where the axis size allows
-// both), and keep the faster one.  Decisions are cached in a plain text
+// operator line pass on the plan's own grid with every route the axis size
+// allows - the FFT transform route, the dense differentiation-matrix route
+// and, for FP32, the tensor-core route - and keep the fastest.  Decisions are cached in a plain text
 // file, one line per (GPU name, axis size, precision), so later plans of the
 // same size skip the timing.
 #include <cstdio>
@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "umma.h"
 
 namespace cheb {
 
@@ -20,7 +21,7 @@ std::mutex g_tune_mu;
 struct TuneRec {
   std::string gpu;
   int n = 0, bits = 0, route = 0;
-  double ms_tf = 0, ms_dense = 0;
+  double ms_tf = 0, ms_dense = 0, ms_tensor = 0;  // 0: not timed
 };
 
 std::vector<TuneRec> load_cache(const char* path) {
@@ -32,8 +33,9 @@ std::vector<TuneRec> load_cache(const char* path) {
   while (std::fgets(line, sizeof(line), f)) {
     char gpu[256];
     TuneRec r;
-    // format: "<gpu name with underscores> <n> <bits> <route> <ms_tf> <ms_dense>"
-    if (std::sscanf(line, "%255s %d %d %d %lf %lf", gpu, &r.n, &r.bits, &r.route, &r.ms_tf, &r.ms_dense) == 6) {
+    // format: "<gpu name with underscores> <n> <bits> <route> <ms_tf> <ms_dense> [<ms_tensor>]"
+    if (std::sscanf(line, "%255s %d %d %d %lf %lf %lf", gpu, &r.n, &r.bits, &r.route, &r.ms_tf, &r.ms_dense,
+                    &r.ms_tensor) >= 6) {
       r.gpu = gpu;
       v.push_back(r);
     }
@@ -46,7 +48,8 @@ void append_cache(const char* path, const TuneRec& r) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %.6f %.6f\n", r.gpu.c_str(), r.n, r.bits, r.route, r.ms_tf, r.ms_dense);
+  std::fprintf(f, "%s %d %d %d %.6f %.6f %.6f\n", r.gpu.c_str(), r.n, r.bits, r.route, r.ms_tf, r.ms_dense,
+               r.ms_tensor);
   std::fclose(f);
 }
 
@@ -81,6 +84,17 @@ int time_pass(cheb_plan_s* p, int axis, T* K, T* u, T* out, float* ms) {
   return st;
 }
 
+// routes the axis allows in this precision
+template <typename T>
+std::vector<int> candidates(const cheb_plan_s* p, int a) {
+  std::vector<int> c;
+  const AxisTables& t = p->ax[a];
+  if (t.transform_ok) c.push_back(CHEB_ROUTE_TRANSFORM);
+  if (t.dense_ok) c.push_back(CHEB_ROUTE_DENSE);
+  if (sizeof(T) == 4 && tensor_route_ok(p, a)) c.push_back(CHEB_ROUTE_TENSOR);
+  return c;
+}
+
 template <typename T>
 int tune_precision(cheb_plan_s* p, const char* cache, const std::string& gpu, int* routes_out) {
   const size_t n = p->size();
@@ -90,7 +104,7 @@ int tune_precision(cheb_plan_s* p, const char* cache, const std::string& gpu, in
   bool need = false;
   for (int a = 0; a < p->dim; ++a) {
     const AxisTables& t = p->ax[a];
-    if (!(t.transform_ok && t.dense_ok)) continue;
+    if (candidates<T>(p, a).size() < 2) continue;
     bool hit = false;
     for (auto& r : cached)
       if (r.gpu == gpu && r.n == t.n && r.bits == bits) hit = true;
@@ -108,7 +122,8 @@ int tune_precision(cheb_plan_s* p, const char* cache, const std::string& gpu, in
   for (int a = 0; a < p->dim && !st; ++a) {
     AxisTables& t = p->ax[a];
     int& route = (sizeof(T) == 4) ? t.route32 : t.route;
-    if (!(t.transform_ok && t.dense_ok)) {
+    const std::vector<int> cand = candidates<T>(p, a);
+    if (cand.size() < 2) {
       routes_out[a] = route;
       continue;
     }
@@ -118,14 +133,21 @@ int tune_precision(cheb_plan_s* p, const char* cache, const std::string& gpu, in
     if (hit) {
       route = hit->route;
     } else {
-      float ms_tf = 0, ms_dense = 0;
-      route = CHEB_ROUTE_TRANSFORM;
-      if ((st = time_pass<T>(p, a, K, u, out, &ms_tf))) break;
-      route = CHEB_ROUTE_DENSE;
-      if ((st = time_pass<T>(p, a, K, u, out, &ms_dense))) break;
-      route = ms_dense < ms_tf ? CHEB_ROUTE_DENSE : CHEB_ROUTE_TRANSFORM;
       TuneRec r;
-      r.gpu = gpu; r.n = t.n; r.bits = bits; r.route = route; r.ms_tf = ms_tf; r.ms_dense = ms_dense;
+      float best = 0;
+      int best_route = cand[0];
+      for (int c : cand) {
+        float ms = 0;
+        route = c;
+        if ((st = time_pass<T>(p, a, K, u, out, &ms))) break;
+        if (c == CHEB_ROUTE_TRANSFORM) r.ms_tf = ms;
+        else if (c == CHEB_ROUTE_DENSE) r.ms_dense = ms;
+        else r.ms_tensor = ms;
+        if (c == cand[0] || ms < best) { best = ms; best_route = c; }
+      }
+      if (st) break;
+      route = best_route;
+      r.gpu = gpu; r.n = t.n; r.bits = bits; r.route = route;
       append_cache(cache, r);
       cached.push_back(r);
     }

@@ -559,7 +559,9 @@ int launch_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M
 // the contraction kernel above.
 // ---------------------------------------------------------------------------
 constexpr int kDK = 16;      // K chunk (one 64-byte swizzle row)
-constexpr int kDStages = 4;
+constexpr int kDStages = 3;  // D / split-tile stages
+constexpr int kRaw = 3;      // raw line-tile slots filled by cp.async (two chunks ahead)
+constexpr int kRawFloats = 128 * 17;  // one slot: 128 lines x 16 points (x-lines: rows padded to 17)
 
 // Line L of axis a starts at base(L) with point stride stride(); 32-bit
 // offsets (grids have < 2^31 points).
@@ -585,13 +587,28 @@ struct DenseArgs {
   float2* ends;      // (D u) at points 0 and n-1 of every line
   const float* u;    // phase 2: Dirichlet rows
   float* out;        // phase 2
+  const float* Dend; // phase 1, 257-point lines: row n-1 of D (FP32); that output point
+                     // is a dot product in the converters, so the MMA needs N = 256 only
 };
 
 // shared-memory bytes of the dense pass for nA output columns
+constexpr int kPf = 2 * 32 * 32;  // epilogue prefetch floats per warp (x-lines: 2 x 32 x 32, else 4 x 16 x 32)
+
 size_t dense_smem_bytes(int nA) {
-  return 1024 + (size_t)kDStages * (2u * kBM + 2u * (size_t)nA) * (kDK * 4) + 256 + 128 * 17 * 4 +
-         4 * 32 * 32 * 4 + 4 * 32 * 8;
+  return 1024 + (size_t)kDStages * (2u * kBM + 2u * (size_t)nA) * (kDK * 4) + 256 + kRaw * kRawFloats * 4 +
+         4 * 32 * 32 * 4 + 4 * 32 * 8 + 4 * kPf * 4 + 272 * 4 + 2 * 128 * 4;
 }
+
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc, bool valid) {
+  // 4-byte asynchronous copy; an invalid element (gsrc still a valid address)
+  // copies zero source bytes and fills zero
+  const uint32_t sa = smem_u32(sdst);
+  const uint32_t n = valid ? 4u : 0u;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NW>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NW) : "memory"); }
 
 // Boundary rows in phase 2.  A line either runs through the interior of the
 // other axes (its points 1 .. n-2 are interior nodes: out (+)= -C), or lies in
@@ -637,11 +654,17 @@ __global__ void __launch_bounds__(kUThreads, 1)
   auto tfull = [&](int b) { return bars + 8u * (3 * S + b); };
   auto tempty = [&](int b) { return bars + 8u * (3 * S + 2 + b); };
   const uint32_t fin = bars + 8u * (3 * S + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * stage_bytes + 8 * (3 * S + 5));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * stage_bytes + 8 * (3 * S + 7));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* rawt = reinterpret_cast<float*>(gbase + S * stage_bytes + 256);  // 128 x 17 (x-lines)
-  float* stg = rawt + 128 * 17;                                            // 4 x 32 x 32 (x-lines)
+  float* rawt = reinterpret_cast<float*>(gbase + S * stage_bytes + 256);  // kRaw slots of the line tile
+  float* stg = rawt + kRaw * kRawFloats;                                   // 4 x 32 x 32 (x-lines)
   float2* endw = reinterpret_cast<float2*>(stg + 4 * 32 * 32);             // 4 x 32
+  float* pfb = reinterpret_cast<float*>(endw + 4 * 32);                    // 4 x kPf
+  float* dend = pfb + 4 * kPf;                                             // 272: row n-1 of D
+  float* gend = dend + 272;                                                // 2 x 128 end values
+  const bool xend = A.phase == 1 && A.Dend != nullptr;
+  // end-value barriers (converters -> epilogue), one per accumulator buffer
+  auto endb = [&](int b) { return bars + 8u * (3 * S + 5) + 8u * b; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = lg.n;
@@ -658,11 +681,14 @@ __global__ void __launch_bounds__(kUThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
       mbar_init(tempty(b), 128);
+      mbar_init(endb(b), 128);
     }
     mbar_init(fin, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (xend)
+    for (int i = threadIdx.x; i < 272; i += blockDim.x) dend[i] = i < n ? A.Dend[i] : 0.f;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(nbuf * tmem_cols)
@@ -744,51 +770,57 @@ __global__ void __launch_bounds__(kUThreads, 1)
     }
     __syncwarp();
   } else if (warp >= 4 && warp < 8) {
-    // converters: one line per thread; the global loads of chunk c + 1 are
-    // in flight while chunk c waits for its stage and is split
+    // converters: one line per thread.  The line tile of chunk c + 2 is copied
+    // by cp.async into a raw slot while chunk c is split, so the global loads
+    // stay in flight across the per-chunk proxy fence.
     const int t = threadIdx.x - 128;
     const int stride = lg.stride();
-    int g = 0;
+    int g = 0, tile_it = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tile_it) {
       const int L0 = tile * kBM, L = L0 + t;
       const bool lv = L < lg.nl;
       const int lb = lv ? lg.base(L) : 0;
-      // x-lines: element e = t + 128 r of the 128 x 16 chunk (16 threads per
-      // line, coalesced); other axes: point kk of this thread's line
-      auto load = [&](int c, float (&w)[kDK]) {
+      // raw slot layout: x-lines [line][17] (16 threads per line, coalesced);
+      // other axes [point][128] (a thread per line, coalesced across lines)
+      auto issue = [&](int c) {
+        float* slot = rawt + (c % kRaw) * kRawFloats;
 #pragma unroll
         for (int r = 0; r < kDK; ++r) {
           if (XAX) {
-            const int e = t + 128 * r, m = e >> 4, pt = c * kDK + (e & 15), Lm = L0 + m;
-            w[r] = (Lm < lg.nl && pt < n) ? __ldcg(A.src + Lm * lg.nx + pt) : 0.f;
+            const int e = t + 128 * r, m = e >> 4, kk = e & 15, pt = c * kDK + kk, Lm = L0 + m;
+            const bool v = Lm < lg.nl && pt < n;
+            cp_async4(slot + m * 17 + kk, A.src + (v ? Lm * lg.nx + pt : 0), v);
           } else {
             const int pt = c * kDK + r;
-            w[r] = (lv && pt < n) ? __ldcg(A.src + lb + pt * stride) : 0.f;
+            const bool v = lv && pt < n;
+            cp_async4(slot + r * 128 + t, A.src + (v ? lb + pt * stride : 0), v);
           }
         }
+        cp_async_commit();
       };
-      float cur[kDK];
-      load(0, cur);
+      issue(0);
+      if (nchunks > 1) issue(1);
+      float gacc = 0.f;  // row n-1 of D against this thread's line (xend)
       for (int c = 0; c < nchunks; ++c, ++g) {
         const int s = g % S;
         const uint32_t ph = (uint32_t)(g / S) & 1u;
-        float nxt[kDK];
-        if (c + 1 < nchunks) load(c + 1, nxt);
-        float v[kDK];
-        if (XAX) {
-#pragma unroll
-          for (int r = 0; r < kDK; ++r) {
-            const int e = t + 128 * r;
-            rawt[(e >> 4) * 17 + (e & 15)] = cur[r];
-          }
-          asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll
-          for (int kk = 0; kk < kDK; ++kk) v[kk] = rawt[t * 17 + kk];
-          asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (c + 2 < nchunks) {
+          issue(c + 2);
+          cp_async_wait<2>();
+        } else if (c + 1 < nchunks) {
+          cp_async_wait<1>();
         } else {
+          cp_async_wait<0>();
+        }
+        if (XAX) asm volatile("bar.sync 1, 128;" ::: "memory");  // rows filled by 16 threads each
+        const float* slot = rawt + (c % kRaw) * kRawFloats;
+        float v[kDK];
 #pragma unroll
-          for (int kk = 0; kk < kDK; ++kk) v[kk] = cur[kk];
+        for (int kk = 0; kk < kDK; ++kk) v[kk] = XAX ? slot[t * 17 + kk] : slot[kk * 128 + t];
+        if (xend) {
+#pragma unroll
+          for (int kk = 0; kk < kDK; ++kk) gacc = fmaf(dend[c * kDK + kk], v[kk], gacc);
         }
         // the stage is free once the MMAs of its previous use completed
         if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) {
@@ -810,10 +842,16 @@ __global__ void __launch_bounds__(kUThreads, 1)
           *reinterpret_cast<float4*>(xl + gp * 16) = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (xend && c == nchunks - 1) {
+          gend[(tile_it & 1) * 128 + t] = gacc;
+          mbar_arrive(endb(tile_it & 1));
+        }
         mbar_arrive(conv(s));
-#pragma unroll
-        for (int r = 0; r < kDK; ++r) cur[r] = nxt[r];
+        // the raw slot of chunk c is refilled by issue(c + 3): all its readers
+        // are past this point before any thread issues it (x-lines share rows)
+        if (XAX) asm volatile("bar.sync 1, 128;" ::: "memory");
       }
+      if (!ok) cp_async_wait<0>();  // no copy may land after the CTA gave up
     }
   } else if (warp >= 8) {
     const int q = warp & 3;
@@ -864,88 +902,143 @@ __global__ void __launch_bounds__(kUThreads, 1)
         endw[q * 32 + lane] = make_float2(__int_as_float(cls), 0.f);
         __syncwarp();
       }
-      const int ncol = phase == 1 ? nA : n;
-      // 16 columns at a time (x-lines: 32-column staging blocks, two halves);
-      // every global load of a block is issued before its stores
-      for (int col = 0; col < ncol; col += 16) {
-        float v[16];
-        if (col < nA) {
-          tmem_ld16(tl + (uint32_t)col, v);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] = 0.f;
-        }
-        if (phase == 1) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (col + j == 0) e0 = v[j];
-            if (col + j == n - 1) eN = v[j];
-          }
-        }
+      float gl = 0.f;  // D u at point n-1 (xend)
+      if (xend) {
+        if (!mbar_wait(endb(b), (uint32_t)use & 1u, abort_flag)) break;
+        gl = gend[b * 128 + 32 * q + lane];
+      }
+      const int ncol = phase == 1 ? (xend ? n : nA) : n;
+      // The global operands of the epilogue (K in phase 1; the accumulated
+      // output or u in phase 2) are copied by cp.async one block ahead into
+      // this warp's prefetch buffers; each thread reads back only its own
+      // copies.  x-lines: 32-column blocks (lane = point, 32 rows = lines);
+      // other axes: 16-column blocks (lane = line, 16 points).
+      float* pf = pfb + q * kPf;
+      const int bw = XAX ? 32 : 16;
+      const int nblk = (ncol + bw - 1) / bw;
+      constexpr int PD = XAX ? 1 : 3;        // blocks in flight ahead of the current one
+      constexpr int PS = XAX ? 1024 : 512;   // floats per prefetch slot
+      auto prefetch = [&](int blk) {
+        float* dst = pf + (blk % (PD + 1)) * PS;
+        const int c0 = blk * bw;
         if (XAX) {
-          const int half = (col >> 4) & 1;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) sw[lane * 32 + ((16 * half + j) ^ lane)] = v[j];
-          if (!half && col + 16 < ncol) continue;
-          __syncwarp();
-          const int pt = (col & ~31) + lane;
+          const int pt = c0 + lane;
           const bool pin = pt > 0 && pt < n - 1;
-          float ld[32];
-#pragma unroll
+#pragma unroll 4
           for (int r = 0; r < 32; ++r) {
             const int Lr = Lw + r;
-            const int idx = Lr * lg.nx + pt;
-            ld[r] = 0.f;
-            if (Lr < lg.nl && pt < n) {
-              if (phase == 1) {
-                ld[r] = __ldcg(Kp + idx);
-              } else if (pin) {
-                const int c = __float_as_int(endw[q * 32 + r].x);
-                if (c == kLineInterior && !first) ld[r] = __ldcg(outp + idx);
-                else if (c == kLineCopyU) ld[r] = __ldcg(up + idx);
+            const int idx = (Lr < lg.nl && pt < n) ? Lr * lg.nx + pt : 0;
+            const float* src = Kp;
+            bool v = Lr < lg.nl && pt < n;
+            if (phase == 2) {
+              const int c = __float_as_int(endw[q * 32 + r].x);
+              v = v && pin && ((c == kLineInterior && !first) || c == kLineCopyU);
+              src = c == kLineCopyU ? up : outp;
+            }
+            cp_async4(dst + r * 32 + lane, (v ? src : Kp) + (v ? idx : 0), v);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int pt = c0 + j;
+            const float* src = Kp;
+            bool v = lv && pt < n;
+            if (phase == 2) {
+              v = v && pt > 0 && pt < n - 1 && ((cls == kLineInterior && !first) || cls == kLineCopyU);
+              src = cls == kLineCopyU ? up : outp;
+            }
+            cp_async4(dst + j * 32 + lane, (v ? src : Kp) + (v ? lb + pt * stride : 0), v);
+          }
+        }
+        cp_async_commit();
+      };
+      for (int pb = 0; pb < PD && pb < nblk; ++pb) prefetch(pb);
+      for (int blk = 0; blk < nblk; ++blk) {
+        const int c0 = blk * bw;
+        // keep PD blocks in flight: the copies of block blk are complete
+        // when at most (blocks issued after it) groups are pending
+        if (blk + PD < nblk) {
+          prefetch(blk + PD);
+          cp_async_wait<PD>();
+        } else if (XAX) {
+          cp_async_wait<0>();
+        } else {
+          const int ahead = nblk - 1 - blk;
+          if (ahead >= 2) cp_async_wait<2>();
+          else if (ahead == 1) cp_async_wait<1>();
+          else cp_async_wait<0>();
+        }
+        const float* cur = pf + (blk % (PD + 1)) * PS;
+        if (XAX) {
+          // two 16-column TMEM loads staged as one 32 x 32 block (row = line)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int col = c0 + 16 * h;
+            float v[16];
+            if (col < nA) {
+              tmem_ld16(tl + (uint32_t)col, v);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) v[j] = (xend && col + j == n - 1) ? gl : 0.f;
+            }
+            if (phase == 1) {
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                if (col + j == 0) e0 = v[j];
+                if (col + j == n - 1) eN = v[j];
               }
             }
-          }
 #pragma unroll
+            for (int j = 0; j < 16; ++j) sw[lane * 32 + ((16 * h + j) ^ lane)] = v[j];
+          }
+          __syncwarp();
+          const int pt = c0 + lane;
+          const bool pin = pt > 0 && pt < n - 1;
+#pragma unroll 4
           for (int r = 0; r < 32; ++r) {
             const int Lr = Lw + r;
             if (Lr >= lg.nl || pt >= n) continue;
             const int idx = Lr * lg.nx + pt;
             const float C = sw[r * 32 + (lane ^ r)];
+            const float ld = cur[r * 32 + lane];
             if (phase == 1) {
-              __stcg(Qp + idx, ld[r] * C);
+              __stcg(Qp + idx, ld * C);
             } else if (pin) {
               const int c = __float_as_int(endw[q * 32 + r].x);
-              if (c == kLineInterior) __stcg(outp + idx, ld[r] - C);
-              else if (c == kLineCopyU) __stcg(outp + idx, ld[r]);
+              if (c == kLineInterior) __stcg(outp + idx, ld - C);
+              else if (c == kLineCopyU) __stcg(outp + idx, ld);
               else if (c == kLineZero) __stcg(outp + idx, 0.f);
             }
           }
           __syncwarp();
-        } else if (lv) {
-          float ld[16];
+        } else {
+          float v[16];
+          if (c0 < nA) {
+            tmem_ld16(tl + (uint32_t)c0, v);
+          } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int pt = col + j;
-            const int idx = lb + pt * stride;
-            ld[j] = 0.f;
-            if (phase == 1) {
-              if (pt < n) ld[j] = __ldcg(Kp + idx);
-            } else if (pt > 0 && pt < n - 1) {
-              if (cls == kLineInterior && !first) ld[j] = __ldcg(outp + idx);
-              else if (cls == kLineCopyU) ld[j] = __ldcg(up + idx);
+            for (int j = 0; j < 16; ++j) v[j] = (xend && c0 + j == n - 1) ? gl : 0.f;
+          }
+          if (phase == 1) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (c0 + j == 0) e0 = v[j];
+              if (c0 + j == n - 1) eN = v[j];
             }
           }
+          if (lv) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int pt = col + j;
-            const int idx = lb + pt * stride;
-            if (phase == 1) {
-              if (pt < n) __stcg(Qp + idx, ld[j] * v[j]);
-            } else if (pt > 0 && pt < n - 1) {
-              if (cls == kLineInterior) __stcg(outp + idx, ld[j] - v[j]);
-              else if (cls == kLineCopyU) __stcg(outp + idx, ld[j]);
-              else if (cls == kLineZero) __stcg(outp + idx, 0.f);
+            for (int j = 0; j < 16; ++j) {
+              const int pt = c0 + j;
+              const int idx = lb + pt * stride;
+              const float ld = cur[j * 32 + lane];
+              if (phase == 1) {
+                if (pt < n) __stcg(Qp + idx, ld * v[j]);
+              } else if (pt > 0 && pt < n - 1) {
+                if (cls == kLineInterior) __stcg(outp + idx, ld - v[j]);
+                else if (cls == kLineCopyU) __stcg(outp + idx, ld);
+                else if (cls == kLineZero) __stcg(outp + idx, 0.f);
+              }
             }
           }
         }
@@ -1031,6 +1124,7 @@ struct TensorApply {
   int Kp[3] = {0, 0, 0};    // padded K (points), multiple of 16
   float* Dh[3] = {nullptr, nullptr, nullptr};  // split-TF32 D, nA1 x Kp, zero padded
   float* Dl[3] = {nullptr, nullptr, nullptr};
+  float* Dend[3] = {nullptr, nullptr, nullptr};  // row n-1 of D (FP32) when n = 257
   float* Q = nullptr;       // K * (D_a u), one field
   float2* ends = nullptr;   // per line: (D_a u) at both ends
   size_t ends_len = 0;
@@ -1052,7 +1146,9 @@ static int tensor_setup(cheb_plan_s* p) {
   size_t maxl = 0;
   for (int a = 0; a < p->dim; ++a) {
     const int n = p->n[a];
-    t->nA1[a] = umma_n_tile(n);
+    // n = 257: the MMA covers points 0..255; point 256 is a dot product in
+    // the converters (so both phases keep two 256-column accumulators)
+    t->nA1[a] = std::min(umma_n_tile(n), 256);
     t->nA2[a] = umma_n_tile(n - 1);
     t->Kp[a] = umma_n_tile(n);
     maxl = std::max(maxl, p->size() / (size_t)n);
@@ -1060,8 +1156,15 @@ static int tensor_setup(cheb_plan_s* p) {
     const std::vector<double> D = dense_deriv_matrix(n - 1, 2.0 / (p->hi[a] - p->lo[a]));
     const size_t rows = t->nA1[a], cols = t->Kp[a];
     std::vector<double> P(rows * cols, 0.0);
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < std::min<int>(n, (int)rows); ++i)
       for (int j = 0; j < n; ++j) P[i * cols + j] = D[(size_t)i * n + j];
+    if ((int)rows < n) {
+      std::vector<float> de(cols, 0.f);
+      for (int j = 0; j < n; ++j) de[j] = (float)D[(size_t)(n - 1) * n + j];
+      if (cudaMalloc(&t->Dend[a], sizeof(float) * cols) != cudaSuccess) return fail(CHEB_ERR_NOMEM);
+      if (cudaMemcpy(t->Dend[a], de.data(), sizeof(float) * cols, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(CHEB_ERR_CUDA);
+    }
     std::vector<float> h(P.size()), l(P.size());
     tf32_split_host(P.data(), P.size(), h.data(), l.data());
     if (cudaMalloc(&t->Dh[a], sizeof(float) * P.size()) != cudaSuccess ||
@@ -1084,6 +1187,7 @@ void tensor_apply_free(TensorApply* t) {
   for (int a = 0; a < 3; ++a) {
     cudaFree(t->Dh[a]);
     cudaFree(t->Dl[a]);
+    cudaFree(t->Dend[a]);
   }
   cudaFree(t->Q);
   cudaFree(t->ends);
@@ -1100,7 +1204,7 @@ static int launch_dense(const CUtensorMap& mh, const CUtensorMap& ml, const Line
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [] {
     attr_err = cudaFuncSetAttribute(dense_pass_kernel<XAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dense_smem_bytes(272));
+                                    (int)dense_smem_bytes(256));
   });
   CHEB_CUDA(attr_err);
   const int ntiles = (lg.nl + kBM - 1) / kBM;
@@ -1141,6 +1245,7 @@ int tensor_apply_pass(const cheb_plan_s* pc, int axis, bool first, const float* 
     if ((st = make_map(&ml, t.Dl[axis], t.Kp[axis], t.nA1[axis], nA / 2, kDK))) return st;
     A.phase = phase;
     A.src = phase == 1 ? u : t.Q;
+    A.Dend = phase == 1 ? t.Dend[axis] : nullptr;
     st = axis == 0 ? launch_dense<true>(mh, ml, lg, A, nA, s) : launch_dense<false>(mh, ml, lg, A, nA, s);
     if (st) return st;
   }

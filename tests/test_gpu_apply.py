@@ -216,14 +216,17 @@ def test_apply_full_size_sampled(nn):
 
 
 def test_autotuner_picks_a_route_and_caches(tmp_path):
-    """The autotuner times both routes where both exist, records the decision,
-    reuses it from the cache file, and the tuned plan still matches the oracle."""
+    """The autotuner times every route an axis allows (FP32 includes the
+    tensor-core route), records the decision, reuses it from the cache file,
+    and the tuned plan still matches the oracle."""
     import paper_2606_21410_b300 as P
     cache = str(tmp_path / "routes.txt")
     n = (65, 33, 12)
     p = P.Plan(n)
     r = p.autotune(cache)
     assert r["fp64"][2] == "dense" and r["fp32"][2] == "dense"   # n = 12: dense only
+    assert all(x in ("transform", "dense") for x in r["fp64"])
+    assert all(x in ("transform", "dense", "tensor") for x in r["fp32"])
     lines = open(cache).read().splitlines()
     assert len(lines) == 4                                       # 65 and 33, two precisions
     r2 = P.Plan(n).autotune(cache)
