@@ -4,6 +4,7 @@
 // residual update.  Reductions are deterministic: per-CTA partials in a
 // fixed order, the last CTA to finish sums the partials in index order.
 #include <algorithm>
+#include <cstdint>
 
 #include "krylov.h"
 
@@ -13,7 +14,7 @@ constexpr int kRedThreads = 256;
 
 static int red_blocks(size_t n) {
   // enough CTAs to fill the GPU (148 SMs), never more than the work needs
-  size_t b = (n + kRedThreads * 4 - 1) / (kRedThreads * 4);
+  size_t b = (n + kRedThreads * 16 - 1) / (kRedThreads * 16);
   return (int)std::max<size_t>(1, std::min<size_t>(b, kRedBlocks));
 }
 
@@ -76,22 +77,62 @@ __device__ void block_reduce_store(T (&acc)[MAXV], int cnt, bool extra, double* 
   if (threadIdx.x == 0) *counter = 0u;  // ready for the next launch
 }
 
+// 16-byte vectors of the streaming loops.  Krylov vectors are carved from
+// one allocation at offsets of i * n elements, so they are 16-byte aligned
+// only for some n: the host passes vec = 1 only when every pointer of the
+// launch is, and otherwise the whole range runs element-wise.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  typedef float4 t;
+  static constexpr int W = 4;
+  __device__ static float at(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+  __device__ static void set(float4& v, int k, float x) {
+    if (k == 0) v.x = x; else if (k == 1) v.y = x; else if (k == 2) v.z = x; else v.w = x;
+  }
+};
+template <> struct Vec16<double> {
+  typedef double2 t;
+  static constexpr int W = 2;
+  __device__ static double at(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+  __device__ static void set(double2& v, int k, double x) {
+    if (k == 0) v.x = x; else v.y = x;
+  }
+};
+
 // out[i] = <src_i, w>, i < cnt (cnt <= kMaxVecs); optionally also <w, w>
-// stored at out[cnt].
+// stored at out[cnt].  16-byte vector loads; element-wise tail.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
-mdot_kernel(VecList<T> src, int cnt, const T* __restrict__ w, size_t n, int with_self,
+mdot_kernel(VecList<T> src, int cnt, const T* __restrict__ w, size_t n, int with_self, int vec,
             double* part, unsigned* counter, double* out) {
+  typedef typename Vec16<T>::t V;
+  constexpr int W = Vec16<T>::W;
   T acc[kMaxVecs + 1];
 #pragma unroll
   for (int i = 0; i <= kMaxVecs; ++i) acc[i] = (T)0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-    const T wv = w[e];
+  const size_t nv = vec ? n / W : 0;
+  const V* wv4 = reinterpret_cast<const V*>(w);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nv; e += stride) {
+    const V wv = wv4[e];
 #pragma unroll
     for (int i = 0; i < kMaxVecs; ++i)
-      if (i < cnt) acc[i] += src.p[i][e] * wv;
-    if (with_self) acc[kMaxVecs] += wv * wv;
+      if (i < cnt) {
+        const V sv = reinterpret_cast<const V*>(src.p[i])[e];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[i] += Vec16<T>::at(sv, k) * Vec16<T>::at(wv, k);
+      }
+    if (with_self) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) acc[kMaxVecs] += Vec16<T>::at(wv, k) * Vec16<T>::at(wv, k);
+    }
+  }
+  for (size_t e = nv * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+    const T x = w[e];
+#pragma unroll
+    for (int i = 0; i < kMaxVecs; ++i)
+      if (i < cnt) acc[i] += src.p[i][e] * x;
+    if (with_self) acc[kMaxVecs] += x * x;
   }
   block_reduce_store<T, kMaxVecs + 1>(acc, cnt, with_self != 0, part, counter, out);
 }
@@ -100,8 +141,10 @@ mdot_kernel(VecList<T> src, int cnt, const T* __restrict__ w, size_t n, int with
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads)
 maxpy_kernel(VecList<T> src, CoefList coef, const double* __restrict__ cdev, double csign, int cnt,
-             double beta, T* __restrict__ y, size_t n, int want_norm, double* part,
+             double beta, T* __restrict__ y, size_t n, int want_norm, int vec, double* part,
              unsigned* counter, double* out) {
+  typedef typename Vec16<T>::t V;
+  constexpr int W = Vec16<T>::W;
   T c[kMaxVecs];
 #pragma unroll
   for (int i = 0; i < kMaxVecs; ++i)
@@ -109,7 +152,30 @@ maxpy_kernel(VecList<T> src, CoefList coef, const double* __restrict__ cdev, dou
   T acc[1] = {(T)0};
   const T b = (T)beta;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+  const size_t nv = vec ? n / W : 0;
+  V* y4 = reinterpret_cast<V*>(y);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nv; e += stride) {
+    V v;
+    if (beta == 0.0) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, (T)0);
+    } else {
+      const V yo = y4[e];
+#pragma unroll
+      for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, b * Vec16<T>::at(yo, k));
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxVecs; ++i)
+      if (i < cnt) {
+        const V sv = reinterpret_cast<const V*>(src.p[i])[e];
+#pragma unroll
+        for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, Vec16<T>::at(v, k) + c[i] * Vec16<T>::at(sv, k));
+      }
+    y4[e] = v;
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[0] += Vec16<T>::at(v, k) * Vec16<T>::at(v, k);
+  }
+  for (size_t e = nv * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
     T v = (beta == 0.0) ? (T)0 : b * y[e];
 #pragma unroll
     for (int i = 0; i < kMaxVecs; ++i)
@@ -158,14 +224,20 @@ static int elem_blocks(size_t n) {
   return (int)std::max<size_t>(1, std::min<size_t>(b, 148 * 8));
 }
 
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
 template <typename T>
 int k_mdot(const ReduceScratch& rs, const T* const* src, int cnt, const T* w, size_t n,
            bool with_self, double* out_dev, cudaStream_t s) {
   if (cnt > kMaxVecs) { set_error("too many vectors in multi-dot"); return CHEB_ERR_ARG; }
   VecList<T> L;
-  for (int i = 0; i < kMaxVecs; ++i) L.p[i] = i < cnt ? src[i] : nullptr;
+  bool vec = aligned16(w);
+  for (int i = 0; i < kMaxVecs; ++i) {
+    L.p[i] = i < cnt ? src[i] : nullptr;
+    if (i < cnt) vec = vec && aligned16(src[i]);
+  }
   const int nb = red_blocks(n);
-  mdot_kernel<T><<<nb, kRedThreads, 0, s>>>(L, cnt, w, n, with_self ? 1 : 0, rs.part, rs.counter,
+  mdot_kernel<T><<<nb, kRedThreads, 0, s>>>(L, cnt, w, n, with_self ? 1 : 0, vec ? 1 : 0, rs.part, rs.counter,
                                             out_dev);
   CHEB_LAUNCH_CHECK("mdot_kernel");
   return CHEB_OK;
@@ -177,13 +249,15 @@ int k_maxpy(const ReduceScratch& rs, const T* const* src, const double* coef, in
   if (cnt > kMaxVecs) { set_error("too many vectors in multi-axpy"); return CHEB_ERR_ARG; }
   VecList<T> L;
   CoefList C;
+  bool vec = aligned16(y);
   for (int i = 0; i < kMaxVecs; ++i) {
     L.p[i] = i < cnt ? src[i] : nullptr;
     C.c[i] = i < cnt ? coef[i] : 0.0;
+    if (i < cnt) vec = vec && aligned16(src[i]);
   }
   const int nb = red_blocks(n);
   maxpy_kernel<T><<<nb, kRedThreads, 0, s>>>(L, C, nullptr, 0.0, cnt, beta, y, n, norm2_dev ? 1 : 0,
-                                             rs.part, rs.counter, norm2_dev);
+                                             vec ? 1 : 0, rs.part, rs.counter, norm2_dev);
   CHEB_LAUNCH_CHECK("maxpy_kernel");
   return CHEB_OK;
 }
@@ -194,13 +268,15 @@ int k_maxpy_dev(const ReduceScratch& rs, const T* const* src, const double* coef
   if (cnt > kMaxVecs) { set_error("too many vectors in multi-axpy"); return CHEB_ERR_ARG; }
   VecList<T> L;
   CoefList C;
+  bool vec = aligned16(y);
   for (int i = 0; i < kMaxVecs; ++i) {
     L.p[i] = i < cnt ? src[i] : nullptr;
     C.c[i] = 0.0;
+    if (i < cnt) vec = vec && aligned16(src[i]);
   }
   const int nb = red_blocks(n);
   maxpy_kernel<T><<<nb, kRedThreads, 0, s>>>(L, C, coef_dev, sign, cnt, beta, y, n, norm2_dev ? 1 : 0,
-                                             rs.part, rs.counter, norm2_dev);
+                                             vec ? 1 : 0, rs.part, rs.counter, norm2_dev);
   CHEB_LAUNCH_CHECK("maxpy_kernel");
   return CHEB_OK;
 }

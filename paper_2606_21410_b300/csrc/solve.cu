@@ -40,9 +40,10 @@ template <typename T>
 struct KrylovBufs {
   int nvec = 0;        // allocated basis vectors
   int kaug = 0;        // allocated augmentation pairs
-  T* V = nullptr;      // nvec x n
-  T* Z = nullptr;      // kaug x n  (error approximations)
-  T* BZ = nullptr;     // kaug x n  (M^{-1} A z)
+  size_t ld = 0;       // vector stride: n rounded up to 64 elements (256-byte aligned vectors)
+  T* V = nullptr;      // nvec x ld
+  T* Z = nullptr;      // kaug x ld (error approximations)
+  T* BZ = nullptr;     // kaug x ld (M^{-1} A z)
   T* tmp = nullptr;    // n
   T* x = nullptr;      // n (inner solution)
   T* c = nullptr;      // n (inner right-hand side)
@@ -118,17 +119,18 @@ template <typename T>
 static int ensure_bufs(Workspace& w, int nvec, int kaug) {
   KrylovBufs<T>& b = bufs<T>(w);
   const size_t n = w.n;
+  b.ld = (n + 63) / 64 * 64;
   if (b.nvec < nvec) {
     cudaFree(b.V);
     b.V = nullptr;
-    CHEB_CUDA(cudaMalloc(&b.V, sizeof(T) * n * nvec));
+    CHEB_CUDA(cudaMalloc(&b.V, sizeof(T) * b.ld * nvec));
     b.nvec = nvec;
   }
   if (b.kaug < kaug) {
     cudaFree(b.Z); cudaFree(b.BZ);
     b.Z = b.BZ = nullptr;
-    CHEB_CUDA(cudaMalloc(&b.Z, sizeof(T) * n * kaug));
-    CHEB_CUDA(cudaMalloc(&b.BZ, sizeof(T) * n * kaug));
+    CHEB_CUDA(cudaMalloc(&b.Z, sizeof(T) * b.ld * kaug));
+    CHEB_CUDA(cudaMalloc(&b.BZ, sizeof(T) * b.ld * kaug));
     b.kaug = kaug;
   }
   if (!b.tmp) {
@@ -238,11 +240,11 @@ __global__ void givens_kernel(double* hess, HessLayout L, int j, const double* _
   hess[L.res() + j] = fabs(g[j + 1]);
 }
 
-// w = BZ[order[q]] (augmentation step q of a cycle)
+// w = BZ[order[q]] (augmentation step q of a cycle; vectors ld apart)
 template <typename T>
 __global__ void copy_slot_kernel(T* __restrict__ w, const T* __restrict__ BZ, const int* __restrict__ order,
-                                 int q, size_t n) {
-  const T* src = BZ + (size_t)order[q] * n;
+                                 int q, size_t n, size_t ld) {
+  const T* src = BZ + (size_t)order[q] * ld;
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
     w[c] = src[c];
 }
@@ -281,7 +283,7 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
   if (!match) {
     if (cg.exec) { cudaGraphExecDestroy(cg.exec); cg.exec = nullptr; }
     double* dv = w.dscal;
-    auto Vp = [&](int i) { return B.V + (size_t)i * n; };
+    auto Vp = [&](int i) { return B.V + (size_t)i * B.ld; };
     // one uncaptured application first: lazy workspace allocation and kernel
     // attributes happen outside the capture
     {
@@ -302,7 +304,7 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
         st = op_B<T>(p, w, o, K, Vp(j), wv, B.tmp, cs);
       } else {
         copy_slot_kernel<T><<<(int)std::min<size_t>((n + 255) / 256, 148 * 8), 256, 0, cs>>>(wv, B.BZ, w.dorder,
-                                                                                              j - m_eff, n);
+                                                                                              j - m_eff, n, B.ld);
         count_launch();
       }
       const T* src[kMaxVecs];
@@ -373,9 +375,9 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
   int st;
   if ((st = ensure_bufs<T>(w, nbasis, std::max(1, kk)))) return st;
   KrylovBufs<T>& B = bufs<T>(w);
-  auto Vp = [&](int i) { return B.V + (size_t)i * n; };
-  auto Zp = [&](int i) { return B.Z + (size_t)i * n; };
-  auto BZp = [&](int i) { return B.BZ + (size_t)i * n; };
+  auto Vp = [&](int i) { return B.V + (size_t)i * B.ld; };
+  auto Zp = [&](int i) { return B.Z + (size_t)i * B.ld; };
+  auto BZp = [&](int i) { return B.BZ + (size_t)i * B.ld; };
   int naug = 0, next_slot = 0;
   std::vector<double> H((size_t)(nbasis + 1) * nbasis), Hr((size_t)(nbasis + 1) * nbasis);
   std::vector<double> cs(nbasis), sn(nbasis), g(nbasis + 1), y(nbasis);
