@@ -635,8 +635,15 @@ struct BcInfo {
 // class of the points 1 .. n-2 of a line (phase 2)
 enum LineClass { kLineInterior = 0, kLineCopyU = 1, kLineZero = 2, kLineSkip = 3 };
 
+// threads of the dense pass: 8 warps of producer / MMA / converters plus the
+// epilogue warps (x-lines: 4; strided lines: 8, two per TMEM lane quarter)
 template <bool XAX>
-__global__ void __launch_bounds__(kUThreads, 1)
+__host__ __device__ constexpr int dense_epi_warps() { return XAX ? 4 : 8; }
+template <bool XAX>
+__host__ __device__ constexpr int dense_threads() { return 256 + 32 * dense_epi_warps<XAX>(); }
+
+template <bool XAX>
+__global__ void __launch_bounds__(dense_threads<XAX>(), 1)
     dense_pass_kernel(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
                       const LineGeo lg, const DenseArgs A, int nA, int tmem_cols, int nbuf) {
   constexpr int S = kDStages;
@@ -680,7 +687,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 128);
+      mbar_init(tempty(b), 32 * dense_epi_warps<XAX>());
       mbar_init(endb(b), 128);
     }
     mbar_init(fin, 1);
@@ -855,6 +862,10 @@ __global__ void __launch_bounds__(kUThreads, 1)
     }
   } else if (warp >= 8) {
     const int q = warp & 3;
+    // strided lines: two epilogue groups share each TMEM lane quarter and take
+    // alternate 16-column blocks; group 0 also writes the line-end rows
+    const int grp = (warp - 8) >> 2;
+    const int ngrp = dense_epi_warps<XAX>() / 4;
     const int stride = lg.stride();
     float* sw = stg + q * 32 * 32;  // this warp's 32 x 32 staging block (x-lines)
     BcInfo bi;
@@ -913,13 +924,19 @@ __global__ void __launch_bounds__(kUThreads, 1)
       // this warp's prefetch buffers; each thread reads back only its own
       // copies.  x-lines: 32-column blocks (lane = point, 32 rows = lines);
       // other axes: 16-column blocks (lane = line, 16 points).
-      float* pf = pfb + q * kPf;
+      // x-lines: this warp's 2 x 1024 floats after the staging blocks; strided
+      // lines (staging unused): 3 slots of 512 floats per epilogue warp over
+      // the staging, line-class and prefetch areas
+      float* pf = XAX ? pfb + q * kPf : stg + (warp - 8) * 1536;
       const int bw = XAX ? 32 : 16;
       const int nblk = (ncol + bw - 1) / bw;
-      constexpr int PD = XAX ? 1 : 3;        // blocks in flight ahead of the current one
+      constexpr int PD = XAX ? 1 : 2;        // own blocks in flight ahead of the current one
       constexpr int PS = XAX ? 1024 : 512;   // floats per prefetch slot
-      auto prefetch = [&](int blk) {
-        float* dst = pf + (blk % (PD + 1)) * PS;
+      // this warp's blocks: grp, grp + ngrp, ...; mb counts them
+      const int nmy = (nblk - grp + ngrp - 1) / ngrp;
+      auto prefetch = [&](int mb) {
+        const int blk = grp + mb * ngrp;
+        float* dst = pf + (mb % (PD + 1)) * PS;
         const int c0 = blk * bw;
         if (XAX) {
           const int pt = c0 + lane;
@@ -952,23 +969,22 @@ __global__ void __launch_bounds__(kUThreads, 1)
         }
         cp_async_commit();
       };
-      for (int pb = 0; pb < PD && pb < nblk; ++pb) prefetch(pb);
-      for (int blk = 0; blk < nblk; ++blk) {
+      for (int pb = 0; pb < PD && pb < nmy; ++pb) prefetch(pb);
+      for (int mb = 0; mb < nmy; ++mb) {
+        const int blk = grp + mb * ngrp;
         const int c0 = blk * bw;
-        // keep PD blocks in flight: the copies of block blk are complete
-        // when at most (blocks issued after it) groups are pending
-        if (blk + PD < nblk) {
-          prefetch(blk + PD);
+        // keep PD of this warp's blocks in flight: the copies of block mb are
+        // complete when at most (blocks issued after it) groups are pending
+        if (mb + PD < nmy) {
+          prefetch(mb + PD);
           cp_async_wait<PD>();
         } else if (XAX) {
           cp_async_wait<0>();
         } else {
-          const int ahead = nblk - 1 - blk;
-          if (ahead >= 2) cp_async_wait<2>();
-          else if (ahead == 1) cp_async_wait<1>();
+          if (nmy - 1 - mb >= 1) cp_async_wait<1>();
           else cp_async_wait<0>();
         }
-        const float* cur = pf + (blk % (PD + 1)) * PS;
+        const float* cur = pf + (mb % (PD + 1)) * PS;
         if (XAX) {
           // two 16-column TMEM loads staged as one 32 x 32 block (row = line)
 #pragma unroll
@@ -1046,8 +1062,12 @@ __global__ void __launch_bounds__(kUThreads, 1)
       // accumulator drained: hand it back to the MMA issuer
       tc_fence_before();
       mbar_arrive(tempty(b));
-      if (phase == 1 && lv) A.ends[L] = make_float2(e0, eN);
-      if (phase == 2 && lv) {
+      if (phase == 1 && lv) {
+        float* ef = reinterpret_cast<float*>(A.ends + L);
+        if (grp == 0) ef[0] = e0;                                  // point 0 is in block 0
+        if (((n - 1) / bw) % ngrp == grp) ef[1] = eN;              // the block holding point n-1
+      }
+      if (phase == 2 && lv && grp == 0) {
         // the two line ends: boundary nodes of this axis, owner rule per node
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
@@ -1209,7 +1229,8 @@ static int launch_dense(const CUtensorMap& mh, const CUtensorMap& ml, const Line
   CHEB_CUDA(attr_err);
   const int ntiles = (lg.nl + kBM - 1) / kBM;
   const int grid = std::min(ntiles, sm_count());
-  dense_pass_kernel<XAX><<<grid, kUThreads, dense_smem_bytes(nA), s>>>(mh, ml, lg, A, nA, tmem_cols, nbuf);
+  dense_pass_kernel<XAX><<<grid, dense_threads<XAX>(), dense_smem_bytes(nA), s>>>(mh, ml, lg, A, nA,
+                                                                                 tmem_cols, nbuf);
   CHEB_LAUNCH_CHECK("dense_pass_kernel");
   return CHEB_OK;
 }
