@@ -591,12 +591,13 @@ struct DenseArgs {
                      // is a dot product in the converters, so the MMA needs N = 256 only
 };
 
-// shared-memory bytes of the dense pass for nA output columns
-constexpr int kPf = 2 * 32 * 32;  // epilogue prefetch floats per warp (x-lines: 2 x 32 x 32, else 4 x 16 x 32)
-
+// shared-memory bytes of the dense pass for nA D rows per stage: alignment
+// slack, stages, barriers, raw line-tile slots, epilogue prefetch (8 warps x
+// 3 slots x 512 floats), row n-1 of D, the converters' end values, x-line
+// class tables (8 warps x 128)
 size_t dense_smem_bytes(int nA) {
   return 1024 + (size_t)kDStages * (2u * kBM + 2u * (size_t)nA) * (kDK * 4) + 256 + kRaw * kRawFloats * 4 +
-         4 * 32 * 32 * 4 + 4 * 32 * 8 + 4 * kPf * 4 + 272 * 4 + 2 * 128 * 4;
+         8 * 1536 * 4 + 272 * 4 + 2 * 128 * 4 + 8 * 128 * 4;
 }
 
 __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc, bool valid) {
@@ -635,12 +636,15 @@ struct BcInfo {
 // class of the points 1 .. n-2 of a line (phase 2)
 enum LineClass { kLineInterior = 0, kLineCopyU = 1, kLineZero = 2, kLineSkip = 3 };
 
-// threads of the dense pass: 8 warps of producer / MMA / converters plus the
-// epilogue warps (x-lines: 4; strided lines: 8, two per TMEM lane quarter)
+// threads of the dense pass: 8 warps of producer / MMA / converters plus 8
+// epilogue warps (two per TMEM lane quarter)
 template <bool XAX>
-__host__ __device__ constexpr int dense_epi_warps() { return XAX ? 4 : 8; }
+__host__ __device__ constexpr int dense_epi_warps() { return 8; }
 template <bool XAX>
 __host__ __device__ constexpr int dense_threads() { return 256 + 32 * dense_epi_warps<XAX>(); }
+// D rows held per stage: x-lines use whole 128-row M tiles
+template <bool XAX>
+__host__ __device__ constexpr int dense_rows(int nA) { return XAX ? (nA + 127) / 128 * 128 : nA; }
 
 template <bool XAX>
 __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
@@ -652,7 +656,10 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
-  const uint32_t xbytes = kBM * RB, dbytes = (uint32_t)nA * RB;
+  // x-lines swap the MMA roles (A = D: points on the TMEM lanes, B = the line
+  // tile), so D occupies whole 128-row M tiles
+  const int nAx = dense_rows<XAX>(nA);
+  const uint32_t xbytes = kBM * RB, dbytes = (uint32_t)nAx * RB;
   const uint32_t stage_bytes = 2u * xbytes + 2u * dbytes;  // [Xh | Xl | Dh | Dl]
   const uint32_t bars = base + S * stage_bytes;
   auto full = [&](int s) { return bars + 8u * s; };
@@ -664,11 +671,10 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S * stage_bytes + 8 * (3 * S + 7));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* rawt = reinterpret_cast<float*>(gbase + S * stage_bytes + 256);  // kRaw slots of the line tile
-  float* stg = rawt + kRaw * kRawFloats;                                   // 4 x 32 x 32 (x-lines)
-  float2* endw = reinterpret_cast<float2*>(stg + 4 * 32 * 32);             // 4 x 32
-  float* pfb = reinterpret_cast<float*>(endw + 4 * 32);                    // 4 x kPf
-  float* dend = pfb + 4 * kPf;                                             // 272: row n-1 of D
+  float* stg = rawt + kRaw * kRawFloats;                                   // epilogue prefetch: 8 x 1536
+  float* dend = stg + 8 * 1536;                                            // 272: row n-1 of D
   float* gend = dend + 272;                                                // 2 x 128 end values
+  int* clsw = reinterpret_cast<int*>(gend + 256);                          // x-lines: 8 x 128 line classes
   const bool xend = A.phase == 1 && A.Dend != nullptr;
   // end-value barriers (converters -> epilogue), one per accumulator buffer
   auto endb = [&](int b) { return bars + 8u * (3 * S + 5) + 8u * b; };
@@ -721,11 +727,11 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
           if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
           const uint32_t st = base + s * stage_bytes + 2u * xbytes;
           mbar_expect_tx(full(s), 2u * dbytes);
-          // D rows in two boxes of nA / 2 rows each (a box has at most 256 rows)
+          // D rows in two boxes of nAx / 2 rows each (a box has at most 256 rows)
           tma_load_2d(st, &tmDh, full(s), c * kDK, 0);
-          tma_load_2d(st + dbytes / 2, &tmDh, full(s), c * kDK, nA / 2);
+          tma_load_2d(st + dbytes / 2, &tmDh, full(s), c * kDK, nAx / 2);
           tma_load_2d(st + dbytes, &tmDl, full(s), c * kDK, 0);
-          tma_load_2d(st + dbytes + dbytes / 2, &tmDl, full(s), c * kDK, nA / 2);
+          tma_load_2d(st + dbytes + dbytes / 2, &tmDl, full(s), c * kDK, nAx / 2);
           last[s] = g;
         }
       }
@@ -753,6 +759,22 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
           const uint32_t st = base + s * stage_bytes;
 #pragma unroll
           for (int kk = 0; kk < kDK / 8; ++kk) {
+            if (XAX) {
+              // A = D rows of M tile mt (points), B = the line tile (N = 128)
+              const uint64_t bh = sdesc_k<kDK>(st + 32u * kk);
+              const uint64_t bl = sdesc_k<kDK>(st + xbytes + 32u * kk);
+              const uint32_t idesc = idesc_tf32(kBM, kBM);
+              for (int mt = 0; mt < nAx / 128; ++mt) {
+                const uint32_t aoff = (uint32_t)mt * 128u * RB;
+                const uint64_t ah = sdesc_k<kDK>(st + 2u * xbytes + aoff + 32u * kk);
+                const uint64_t al = sdesc_k<kDK>(st + 2u * xbytes + dbytes + aoff + 32u * kk);
+                const uint32_t dc = d + (uint32_t)(mt * 128);
+                umma_tf32(dc, ah, bh, idesc, (c | kk) != 0);
+                umma_tf32(dc, ah, bl, idesc, 1u);
+                umma_tf32(dc, al, bh, idesc, 1u);
+              }
+              continue;
+            }
             const uint64_t ah = sdesc_k<kDK>(st + 32u * kk);
             const uint64_t al = sdesc_k<kDK>(st + xbytes + 32u * kk);
             for (int gi = 0; gi < ng; ++gi) {
@@ -861,13 +883,6 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
       if (!ok) cp_async_wait<0>();  // no copy may land after the CTA gave up
     }
   } else if (warp >= 8) {
-    const int q = warp & 3;
-    // strided lines: two epilogue groups share each TMEM lane quarter and take
-    // alternate 16-column blocks; group 0 also writes the line-end rows
-    const int grp = (warp - 8) >> 2;
-    const int ngrp = dense_epi_warps<XAX>() / 4;
-    const int stride = lg.stride();
-    float* sw = stg + q * 32 * 32;  // this warp's 32 x 32 staging block (x-lines)
     BcInfo bi;
     bi.nx = A.g.n[0];
     bi.ny = A.g.n[1];
@@ -883,78 +898,180 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
     float* Qp = A.Q;
     float* outp = A.out;
     const float* up = A.u;
-    int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-      const int b = it % nbuf, use = it / nbuf;
-      if (!mbar_wait(tfull(b), (uint32_t)use & 1u, abort_flag)) break;
-      tc_fence_after();
-      const int Lw = tile * kBM + 32 * q;  // first line of this warp
-      const int L = Lw + lane;
-      const bool lv = L < lg.nl;
-      const int lb = lv ? lg.base(L) : 0;
-      const uint32_t tl = tmem + (uint32_t)(b * tmem_cols) + ((uint32_t)(32 * q) << 16);
-      // line class (phase 2) from its point 1
-      int cls = kLineSkip;
+    // class of the points 1 .. n-2 of line L (phase 2), from its point 1
+    auto line_class = [&](int L) {
+      if (L >= lg.nl) return (int)kLineSkip;
       int ci, cj, ck;
-      lg.node(lv ? L : 0, 1, ci, cj, ck);
-      if (phase == 2 && lv) {
-        const int o = bi.owner(ci, cj, ck);
-        if (o < 0) cls = kLineInterior;
-        else if (!first) cls = kLineSkip;
-        else cls = ((bi.dmask >> o) & 1) ? kLineCopyU : kLineZero;
+      lg.node(L, 1, ci, cj, ck);
+      const int o = bi.owner(ci, cj, ck);
+      if (o < 0) return (int)kLineInterior;
+      if (!first) return (int)kLineSkip;
+      return ((bi.dmask >> o) & 1) ? (int)kLineCopyU : (int)kLineZero;
+    };
+    // the two ends of line L: boundary nodes of this axis, owner rule per node
+    auto line_ends = [&](int L, int lb, int stride, float e0, float eN) {
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int pt = side ? n - 1 : 0;
+        int i, jj, k;
+        lg.node(L, pt, i, jj, k);
+        const int idx = lb + pt * stride;
+        const int o = bi.owner(i, jj, k);
+        if ((bi.dmask >> o) & 1) {
+          if (first) outp[idx] = up[idx];
+        } else if ((o >> 1) == lg.axis) {
+          // hi face (side 1) is line point 0, lo face (side 0) is point n - 1
+          outp[idx] = (o & 1) ? e0 : -eN;
+        } else if (first) {
+          outp[idx] = 0.f;  // Neumann row of another axis: written by that axis' pass
+        }
       }
-      float e0 = 0.f, eN = 0.f;
-      if (phase == 2 && lv) {
-        const float2 e = A.ends[L];
-        e0 = e.x;
-        eN = e.y;
-      }
-      if (XAX) {
-        endw[q * 32 + lane] = make_float2(__int_as_float(cls), 0.f);
+    };
+    if constexpr (XAX) {
+      // x-lines: the accumulator holds points on the TMEM lanes and the
+      // tile's 128 lines on the columns.  Warp 8 + 4 mt + q reads the points
+      // mt * 128 + 32 q + lane of M tile mt, so for each line the 32 lanes
+      // store 32 consecutive points (coalesced, no staging).  Global operands
+      // of a 16-line chunk are prefetched by cp.async two chunks ahead; the
+      // line classes of the tile sit in a per-warp table.
+      const int mt = (warp - 8) >> 2, q = warp & 3;
+      const int et = threadIdx.x - 256;  // epilogue thread, one per line in the tails
+      const bool act = mt < nAx / 128;
+      const int pt = mt * 128 + 32 * q + lane;
+      const bool pin = pt > 0 && pt < n - 1;
+      float* pf = stg + (warp - 8) * 1536;
+      int* cw = clsw + (warp - 8) * 128;
+      constexpr int PD = 2, NC = kBM / 16;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int b = it % nbuf, use = it / nbuf;
+        if (!mbar_wait(tfull(b), (uint32_t)use & 1u, abort_flag)) break;
+        tc_fence_after();
+        const int L0 = tile * kBM;
+        if (phase == 2) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) cw[lane + 32 * r] = line_class(L0 + lane + 32 * r);
+          __syncwarp();
+        }
+        const uint32_t tl = tmem + (uint32_t)(b * tmem_cols + mt * 128) + ((uint32_t)(32 * q) << 16);
+        auto prefetch = [&](int c) {
+          float* dst = pf + (c % (PD + 1)) * 512;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int Lr = L0 + 16 * c + j;
+            bool v = act && Lr < lg.nl && pt < n;
+            const float* src = Kp;
+            if (phase == 2) {
+              const int cl = cw[16 * c + j];
+              v = v && pin && ((cl == kLineInterior && !first) || cl == kLineCopyU);
+              src = cl == kLineCopyU ? up : outp;
+            }
+            cp_async4(dst + j * 32 + lane, (v ? src : Kp) + (v ? Lr * lg.nx + pt : 0), v);
+          }
+          cp_async_commit();
+        };
+        for (int c = 0; c < PD; ++c) prefetch(c);
+        for (int c = 0; c < NC; ++c) {
+          if (c + PD < NC) {
+            prefetch(c + PD);
+            cp_async_wait<PD>();
+          } else if (NC - 1 - c >= 1) {
+            cp_async_wait<1>();
+          } else {
+            cp_async_wait<0>();
+          }
+          const float* cur = pf + (c % (PD + 1)) * 512;
+          float v[16];
+          if (act) {
+            tmem_ld16(tl + (uint32_t)(16 * c), v);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int Lr = L0 + 16 * c + j;
+            if (!act || Lr >= lg.nl || pt >= n) continue;
+            const int idx = Lr * lg.nx + pt;
+            const float ld = cur[j * 32 + lane];
+            if (phase == 1) {
+              __stcg(Qp + idx, ld * v[j]);
+              float* ef = reinterpret_cast<float*>(A.ends + Lr);
+              if (pt == 0) ef[0] = v[j];
+              if (!xend && pt == n - 1) ef[1] = v[j];
+            } else if (pin) {
+              const int cl = cw[16 * c + j];
+              if (cl == kLineInterior) __stcg(outp + idx, ld - v[j]);
+              else if (cl == kLineCopyU) __stcg(outp + idx, ld);
+              else if (cl == kLineZero) __stcg(outp + idx, 0.f);
+            }
+          }
+        }
+        // accumulator drained: hand it back to the MMA issuer
+        tc_fence_before();
+        mbar_arrive(tempty(b));
+        // per-line tails, one epilogue thread per line of the tile
+        if (et < 128) {
+          const int L = L0 + et;
+          if (xend) {
+            // point n-1 of 257-point lines: the converters' dot product
+            if (!mbar_wait(endb(b), (uint32_t)use & 1u, abort_flag)) break;
+            if (L < lg.nl) {
+              const float g = gend[b * 128 + et];
+              const int idx = L * lg.nx + n - 1;
+              Qp[idx] = Kp[idx] * g;
+              reinterpret_cast<float*>(A.ends + L)[1] = g;
+            }
+          }
+          if (phase == 2 && L < lg.nl) {
+            const float2 e = A.ends[L];
+            line_ends(L, L * lg.nx, 1, e.x, e.y);
+          }
+        }
+        // the class table is rewritten next tile: this warp's readers are done
         __syncwarp();
       }
-      float gl = 0.f;  // D u at point n-1 (xend)
-      if (xend) {
-        if (!mbar_wait(endb(b), (uint32_t)use & 1u, abort_flag)) break;
-        gl = gend[b * 128 + 32 * q + lane];
-      }
-      const int ncol = phase == 1 ? (xend ? n : nA) : n;
-      // The global operands of the epilogue (K in phase 1; the accumulated
-      // output or u in phase 2) are copied by cp.async one block ahead into
-      // this warp's prefetch buffers; each thread reads back only its own
-      // copies.  x-lines: 32-column blocks (lane = point, 32 rows = lines);
-      // other axes: 16-column blocks (lane = line, 16 points).
-      // x-lines: this warp's 2 x 1024 floats after the staging blocks; strided
-      // lines (staging unused): 3 slots of 512 floats per epilogue warp over
-      // the staging, line-class and prefetch areas
-      float* pf = XAX ? pfb + q * kPf : stg + (warp - 8) * 1536;
-      const int bw = XAX ? 32 : 16;
-      const int nblk = (ncol + bw - 1) / bw;
-      constexpr int PD = XAX ? 1 : 2;        // own blocks in flight ahead of the current one
-      constexpr int PS = XAX ? 1024 : 512;   // floats per prefetch slot
-      // this warp's blocks: grp, grp + ngrp, ...; mb counts them
-      const int nmy = (nblk - grp + ngrp - 1) / ngrp;
-      auto prefetch = [&](int mb) {
-        const int blk = grp + mb * ngrp;
-        float* dst = pf + (mb % (PD + 1)) * PS;
-        const int c0 = blk * bw;
-        if (XAX) {
-          const int pt = c0 + lane;
-          const bool pin = pt > 0 && pt < n - 1;
-#pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const int Lr = Lw + r;
-            const int idx = (Lr < lg.nl && pt < n) ? Lr * lg.nx + pt : 0;
-            const float* src = Kp;
-            bool v = Lr < lg.nl && pt < n;
-            if (phase == 2) {
-              const int c = __float_as_int(endw[q * 32 + r].x);
-              v = v && pin && ((c == kLineInterior && !first) || c == kLineCopyU);
-              src = c == kLineCopyU ? up : outp;
-            }
-            cp_async4(dst + r * 32 + lane, (v ? src : Kp) + (v ? idx : 0), v);
-          }
-        } else {
+    } else {
+      // strided lines: a thread per line (lanes along consecutive lines);
+      // two epilogue groups share each TMEM lane quarter and take alternate
+      // 16-column blocks; group 0 also writes the line-end rows
+      const int q = warp & 3;
+      const int grp = (warp - 8) >> 2;
+      const int ngrp = dense_epi_warps<XAX>() / 4;
+      const int stride = lg.stride();
+      int it = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int b = it % nbuf, use = it / nbuf;
+        if (!mbar_wait(tfull(b), (uint32_t)use & 1u, abort_flag)) break;
+        tc_fence_after();
+        const int L = tile * kBM + 32 * q + lane;
+        const bool lv = L < lg.nl;
+        const int lb = lv ? lg.base(L) : 0;
+        const uint32_t tl = tmem + (uint32_t)(b * tmem_cols) + ((uint32_t)(32 * q) << 16);
+        const int cls = phase == 2 ? line_class(L) : (int)kLineSkip;
+        float e0 = 0.f, eN = 0.f;
+        if (phase == 2 && lv) {
+          const float2 e = A.ends[L];
+          e0 = e.x;
+          eN = e.y;
+        }
+        float gl = 0.f;  // D u at point n-1 (xend)
+        if (xend) {
+          if (!mbar_wait(endb(b), (uint32_t)use & 1u, abort_flag)) break;
+          gl = gend[b * 128 + 32 * q + lane];
+        }
+        const int ncol = phase == 1 ? (xend ? n : nA) : n;
+        // The global operands of the epilogue (K in phase 1; the accumulated
+        // output or u in phase 2) are copied by cp.async two of this warp's
+        // blocks ahead into 3 slots of 16 points x 32 lines (over the staging
+        // area the x-lines use); each thread reads back only its own copies.
+        float* pf = stg + (warp - 8) * 1536;
+        constexpr int PD = 2, PS = 512, bw = 16;
+        const int nblk = (ncol + bw - 1) / bw;
+        const int nmy = (nblk - grp + ngrp - 1) / ngrp;  // this warp's blocks: grp, grp + ngrp, ...
+        auto prefetch = [&](int mb) {
+          const int c0 = (grp + mb * ngrp) * bw;
+          float* dst = pf + (mb % (PD + 1)) * PS;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int pt = c0 + j;
@@ -966,68 +1083,20 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
             }
             cp_async4(dst + j * 32 + lane, (v ? src : Kp) + (v ? lb + pt * stride : 0), v);
           }
-        }
-        cp_async_commit();
-      };
-      for (int pb = 0; pb < PD && pb < nmy; ++pb) prefetch(pb);
-      for (int mb = 0; mb < nmy; ++mb) {
-        const int blk = grp + mb * ngrp;
-        const int c0 = blk * bw;
-        // keep PD of this warp's blocks in flight: the copies of block mb are
-        // complete when at most (blocks issued after it) groups are pending
-        if (mb + PD < nmy) {
-          prefetch(mb + PD);
-          cp_async_wait<PD>();
-        } else if (XAX) {
-          cp_async_wait<0>();
-        } else {
-          if (nmy - 1 - mb >= 1) cp_async_wait<1>();
-          else cp_async_wait<0>();
-        }
-        const float* cur = pf + (mb % (PD + 1)) * PS;
-        if (XAX) {
-          // two 16-column TMEM loads staged as one 32 x 32 block (row = line)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int col = c0 + 16 * h;
-            float v[16];
-            if (col < nA) {
-              tmem_ld16(tl + (uint32_t)col, v);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) v[j] = (xend && col + j == n - 1) ? gl : 0.f;
-            }
-            if (phase == 1) {
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                if (col + j == 0) e0 = v[j];
-                if (col + j == n - 1) eN = v[j];
-              }
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) sw[lane * 32 + ((16 * h + j) ^ lane)] = v[j];
+          cp_async_commit();
+        };
+        for (int pb = 0; pb < PD && pb < nmy; ++pb) prefetch(pb);
+        for (int mb = 0; mb < nmy; ++mb) {
+          const int c0 = (grp + mb * ngrp) * bw;
+          if (mb + PD < nmy) {
+            prefetch(mb + PD);
+            cp_async_wait<PD>();
+          } else if (nmy - 1 - mb >= 1) {
+            cp_async_wait<1>();
+          } else {
+            cp_async_wait<0>();
           }
-          __syncwarp();
-          const int pt = c0 + lane;
-          const bool pin = pt > 0 && pt < n - 1;
-#pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const int Lr = Lw + r;
-            if (Lr >= lg.nl || pt >= n) continue;
-            const int idx = Lr * lg.nx + pt;
-            const float C = sw[r * 32 + (lane ^ r)];
-            const float ld = cur[r * 32 + lane];
-            if (phase == 1) {
-              __stcg(Qp + idx, ld * C);
-            } else if (pin) {
-              const int c = __float_as_int(endw[q * 32 + r].x);
-              if (c == kLineInterior) __stcg(outp + idx, ld - C);
-              else if (c == kLineCopyU) __stcg(outp + idx, ld);
-              else if (c == kLineZero) __stcg(outp + idx, 0.f);
-            }
-          }
-          __syncwarp();
-        } else {
+          const float* cur = pf + (mb % (PD + 1)) * PS;
           float v[16];
           if (c0 < nA) {
             tmem_ld16(tl + (uint32_t)c0, v);
@@ -1058,33 +1127,15 @@ __global__ void __launch_bounds__(dense_threads<XAX>(), 1)
             }
           }
         }
-      }
-      // accumulator drained: hand it back to the MMA issuer
-      tc_fence_before();
-      mbar_arrive(tempty(b));
-      if (phase == 1 && lv) {
-        float* ef = reinterpret_cast<float*>(A.ends + L);
-        if (grp == 0) ef[0] = e0;                                  // point 0 is in block 0
-        if (((n - 1) / bw) % ngrp == grp) ef[1] = eN;              // the block holding point n-1
-      }
-      if (phase == 2 && lv && grp == 0) {
-        // the two line ends: boundary nodes of this axis, owner rule per node
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-          const int pt = side ? n - 1 : 0;
-          int i, jj, k;
-          lg.node(L, pt, i, jj, k);
-          const int idx = lb + pt * stride;
-          const int o = bi.owner(i, jj, k);
-          if ((bi.dmask >> o) & 1) {
-            if (first) outp[idx] = up[idx];
-          } else if ((o >> 1) == lg.axis) {
-            // hi face (side 1) is line point 0, lo face (side 0) is point n - 1
-            outp[idx] = (o & 1) ? e0 : -eN;
-          } else if (first) {
-            outp[idx] = 0.f;  // Neumann row of another axis: written by that axis' pass
-          }
+        // accumulator drained: hand it back to the MMA issuer
+        tc_fence_before();
+        mbar_arrive(tempty(b));
+        if (phase == 1 && lv) {
+          float* ef = reinterpret_cast<float*>(A.ends + L);
+          if (grp == 0) ef[0] = e0;                        // point 0 is in block 0
+          if (((n - 1) / bw) % ngrp == grp) ef[1] = eN;    // the block holding point n-1
         }
+        if (phase == 2 && lv && grp == 0) line_ends(L, lb, stride, e0, eN);
       }
     }
   }
@@ -1217,8 +1268,9 @@ void tensor_apply_free(TensorApply* t) {
 template <bool XAX>
 static int launch_dense(const CUtensorMap& mh, const CUtensorMap& ml, const LineGeo& lg, const DenseArgs& A,
                         int nA, cudaStream_t s) {
+  const int nAx = dense_rows<XAX>(nA);
   int tmem_cols = 32;
-  while (tmem_cols < nA) tmem_cols *= 2;
+  while (tmem_cols < nAx) tmem_cols *= 2;
   const int nbuf = 2 * tmem_cols <= 512 ? 2 : 1;
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
@@ -1229,8 +1281,8 @@ static int launch_dense(const CUtensorMap& mh, const CUtensorMap& ml, const Line
   CHEB_CUDA(attr_err);
   const int ntiles = (lg.nl + kBM - 1) / kBM;
   const int grid = std::min(ntiles, sm_count());
-  dense_pass_kernel<XAX><<<grid, dense_threads<XAX>(), dense_smem_bytes(nA), s>>>(mh, ml, lg, A, nA,
-                                                                                 tmem_cols, nbuf);
+  dense_pass_kernel<XAX><<<grid, dense_threads<XAX>(), dense_smem_bytes(nAx), s>>>(mh, ml, lg, A, nA,
+                                                                                  tmem_cols, nbuf);
   CHEB_LAUNCH_CHECK("dense_pass_kernel");
   return CHEB_OK;
 }
@@ -1262,8 +1314,9 @@ int tensor_apply_pass(const cheb_plan_s* pc, int axis, bool first, const float* 
   for (int phase = 1; phase <= 2; ++phase) {
     const int nA = phase == 1 ? t.nA1[axis] : t.nA2[axis];
     CUtensorMap mh, ml;
-    if ((st = make_map(&mh, t.Dh[axis], t.Kp[axis], t.nA1[axis], nA / 2, kDK))) return st;
-    if ((st = make_map(&ml, t.Dl[axis], t.Kp[axis], t.nA1[axis], nA / 2, kDK))) return st;
+    const int rows = axis == 0 ? dense_rows<true>(nA) : nA;  // D rows per stage (boxes of rows / 2)
+    if ((st = make_map(&mh, t.Dh[axis], t.Kp[axis], t.nA1[axis], rows / 2, kDK))) return st;
+    if ((st = make_map(&ml, t.Dl[axis], t.Kp[axis], t.nA1[axis], rows / 2, kDK))) return st;
     A.phase = phase;
     A.src = phase == 1 ? u : t.Q;
     A.Dend = phase == 1 ? t.Dend[axis] : nullptr;
