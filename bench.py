@@ -497,11 +497,12 @@ def main():
             "kernel": ("dense_pass_kernel (tcgen05 split-TF32 FP32 apply, 6 launches per apply)"
                        if tensor_route else "tf_pass_kernel (FP32 apply, 3 launches per apply)"),
             "achieved": algo / per / 1e9, "peak": hbm, "unit": "GB/s", "frac": algo / per / 1e9 / hbm,
-            # DRAM bytes per launch from one ncu capture of the y-axis pair of
-            # this kernel (phase 1: 135.9 MB read + 14.0 MB written; phase 2:
-            # 136.5 + 27.5 MB; profiles/dense_pass_fp32_257.md); transform
-            # route: not captured
-            "traffic": 156.95e6 if tensor_route else None, "algorithmic_bytes_per_launch": algo,
+            # DRAM bytes per launch, averaged over one apply, from one ncu capture
+            # of this kernel (x phase 1: 136.5 MB read + 28.7 MB written; x
+            # phase 2: 77.8 + 12.8; y phase 1: 136.4 + 28.8, taken for the other
+            # three passes, which move the same words; profiles/dense_pass_fp32_257.md);
+            # transform route: not captured
+            "traffic": 152.8e6 if tensor_route else None, "algorithmic_bytes_per_launch": algo,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
             "apply_ms_finest": t32 * 1e3,
             "apply_ms_timed_solve_all_levels": (ph["ms"] / ph["count"]) if ph["count"] else None}
