@@ -9,15 +9,19 @@ elsewhere), mixed precision (FP32 inner LGMRES, FP64 refinement), stopping at
 a preconditioned relative residual of 1e-12.  The metric is the time to
 solve; the same line reports the operator apply throughput (GDOF/s) in FP32
 and FP64, the plain-FP64 time to solve, the roofline of the dominant
-kernel, the oracle timed on the host cores, and an end-to-end time through
-the public API with host buffers.
+kernel, an end-to-end time through the public API with host buffers, and
+(rank 0) the FP64 CPU oracle's own hierarchical solve of the same workload,
+run once on the host cores: its measured time is the CPU baseline and its
+solution gives the relative L2 error of the GPU solutions at every level.
 
-``--impl reference`` times the FP64 CPU oracle instead (bounded sample).
+``--impl reference`` runs that oracle solve alone (the reference arm).
 Multi-GPU: independent replicas (the single-grid solve does not shard).
 """
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import subprocess
@@ -43,7 +47,8 @@ def parse():
     ap.add_argument("--levels", default="65,129,257")
     ap.add_argument("--contrast", type=float, default=100.0)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison solve")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the oracle's hierarchical solve (CPU baseline and parity)")
     ap.add_argument("--reorth", type=int, default=0, help="Gram-Schmidt twice per Arnoldi step")
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--restart", type=int, default=30)
@@ -51,9 +56,10 @@ def parse():
                     help="hierarchy: the 257^3 hierarchical solve (the metric); batch: 16 uneven "
                          "lognormal Picard instances solved concurrently (a secondary line)")
     ap.add_argument("--use-graph", type=int, default=0)
-    ap.add_argument("--route32", default="tensor", choices=["transform", "tensor"],
-                    help="FP32 operator-apply route: FFT line transforms, or the dense "
-                         "derivative on the tensor cores (tcgen05)")
+    ap.add_argument("--route32", default="auto", choices=["auto", "transform", "tensor"],
+                    help="operator-apply routes: auto = the library's autotuner times every "
+                         "route each axis allows and keeps the fastest (per precision); "
+                         "transform / tensor force the FP32 route of every axis")
     ap.add_argument("--fdm-only", type=int, default=0, metavar="BITS",
                     help="only time the preconditioner at the finest level (profiling)")
     ap.add_argument("--apply-only", type=int, default=0, metavar="BITS",
@@ -85,15 +91,19 @@ def host_level(n, spheres, contrast, nodes):
 
 
 def set_routes(p, route32):
-    """FP32 apply route of every axis that allows it."""
+    """Routes of the plan's axes: chosen by the autotuner (``auto``), or the
+    FP32 route of every axis that allows it forced to ``tensor`` or
+    ``transform``."""
     import paper_2606_21410_b300 as P
-    if route32 != "tensor":
-        return
+    if route32 == "auto":
+        return p.autotune(None)
+    want = P.ROUTE_TENSOR if route32 == "tensor" else P.ROUTE_TRANSFORM
     for a in range(p.dim):
         try:
-            p.set_route32(a, P.ROUTE_TENSOR)
+            p.set_route32(a, want)
         except P.ChebError:
             pass
+    return None
 
 
 def setup_gpu(levels, contrast, route32="transform"):
@@ -104,7 +114,7 @@ def setup_gpu(levels, contrast, route32="transform"):
     plans, Ks, bs, hostK, hostb = [], [], [], [], []
     for n in levels:
         p = P.Plan((n, n, n), bc=BC)
-        set_routes(p, route32)
+        p.chosen_routes = set_routes(p, route32)
         K, faces = host_level(n, sp, contrast, [p.nodes(0), p.nodes(1), p.nodes(2)])
         Kd = torch.from_numpy(K).cuda()
         bd = p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"),
@@ -185,65 +195,108 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
-def oracle_iteration_seconds(n, contrast, reps=1):
-    """Seconds of one oracle GMRES iteration (dense Kronecker apply + the
-    oracle's constant-K preconditioner) at n^3, FP64, on the host cores."""
+def oracle_levels(levels, contrast):
+    """Per-level oracle grids, K and b, each sampled on the oracle's own nodes."""
     import oracle as O
+    sp = None
     import workloads as W
-    g = O.Grid((n,) * 3, bc=BC)
     sp = W.sphere_packing(0)
-    K, faces = host_level(n, sp, contrast, [g.nodes(0), g.nodes(1), g.nodes(2)])
-    b = O.rhs(np.zeros(g.shape), faces, g)
-    M = O.FDMPreconditioner(g, O.geometric_mean(K))
-    v = b / np.linalg.norm(b)
+    grids, Ks, bs = [], [], []
+    for n in levels:
+        g = O.Grid((n,) * 3, bc=BC)
+        K, faces = host_level(n, sp, contrast, [g.nodes(0), g.nodes(1), g.nodes(2)])
+        grids.append(g)
+        Ks.append(K)
+        bs.append(O.rhs(np.zeros(g.shape), faces, g))
+    return grids, Ks, bs
+
+
+def oracle_hierarchy(levels, contrast):
+    """The FP64 CPU oracle's hierarchical solve of the workload (Alg. 4 with
+    barycentric prolongation and preconditioned GMRES, rtol 1e-12), timed on
+    the host cores.  Returns (solutions, infos, e_ref, seconds)."""
+    import oracle as O
+    grids, Ks, bs = oracle_levels(levels, contrast)
     t0 = time.perf_counter()
-    for _ in range(reps):
-        v = M(O.apply(v, K, g))
-        v /= np.linalg.norm(v)
-    return (time.perf_counter() - t0) / reps
+    us, infos, eref = O.solve_hierarchy(Ks, bs, grids, rtol=1e-12)
+    return us, infos, eref, time.perf_counter() - t0
 
 
-def oracle_estimate(levels, contrast, its_per_level, reps=1):
-    """Oracle time-to-solve estimate: measured seconds per iteration at each
-    level times the iteration count of that level."""
-    per = [oracle_iteration_seconds(n, contrast, reps) for n in levels]
-    return sum(p * max(1, i) for p, i in zip(per, its_per_level)), per
+def oracle_sample_text(levels, infos, seconds):
+    its = [i["iterations"] for i in infos]
+    return (f"the whole workload once, not sampled: the oracle's hierarchical solve "
+            f"{'->'.join(f'{n}^3' for n in levels)} (dense Kronecker apply, constant-K "
+            f"preconditioner, GMRES(50) to a preconditioned relative residual of 1e-12, "
+            f"{its} iterations per level, {seconds:.1f} s)")
 
 
 def run_reference(args):
+    """Reference arm: the FP64 CPU oracle solving the same workload.  One
+    oracle solve takes minutes, so the timed region is one complete solve
+    (steps = 1); the warm-up steps are bounded samples (one oracle operator
+    application plus one preconditioner application at the coarsest level)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     levels = [int(v) for v in args.levels.split(",")]
     import oracle as O
-    import workloads as W
-    # iteration count from the oracle's own full solve at the coarsest level
-    n0 = levels[0]
-    g = O.Grid((n0,) * 3, bc=BC)
-    K, faces = host_level(n0, W.sphere_packing(0), args.contrast, [g.nodes(0), g.nodes(1), g.nodes(2)])
-    b = O.rhs(np.zeros(g.shape), faces, g)
-    t0 = time.perf_counter()
-    _, info = O.solve_preconditioned(K, b, g, rtol=1e-12)
-    t_coarse = time.perf_counter() - t0
-    its = info["iterations"]
-    times = []
-    for s in range(args.warmup + args.steps):
-        est, per = oracle_estimate(levels[1:], args.contrast, [its] * (len(levels) - 1))
-        if s >= args.warmup:
-            times.append(t_coarse + est)
-    v = float(np.mean(times))
+    grids, Ks, bs = oracle_levels(levels[:1], args.contrast)
+    M = O.FDMPreconditioner(grids[0], O.geometric_mean(Ks[0]))
+    for _ in range(args.warmup):
+        M(O.apply(bs[0], Ks[0], grids[0]))
+    us, infos, eref, v = oracle_hierarchy(levels, args.contrast)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+        "steps": 1, "steps_requested": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": workload_config(levels, args.contrast),
+        "iterations_per_level": [i["iterations"] for i in infos], "e_ref": eref,
+        "rel_residual_per_level": [i["rel_residual"] for i in infos],
         "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
-                         "sample": (f"oracle full preconditioned-GMRES solve at {n0}^3 ({its} "
-                                    f"iterations, {t_coarse:.1f} s) plus one timed iteration per "
-                                    f"finer level x {its} iterations")},
+                         "sample": oracle_sample_text(levels, infos, v)},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "note": ("one oracle solve takes minutes on the host cores, so the timed region is one "
+                 "complete solve (steps = 1) instead of the requested steps"),
     }
     print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# DRAM traffic of a kernel from a committed ncu summary
+# ----------------------------------------------------------------------------
+
+def _sha256(path):
+    h = hashlib.sha256()
+    with open(path, "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()
+
+
+def profile_record(kernel, workload):
+    """Counters of `kernel` on `workload` from a ``traffic-record:`` line of a
+    summary under profiles/ (one ncu capture: DRAM bytes read + written per
+    launch, and for FP64 kernels the executed FP64 flops per launch).  The
+    record names the kernel's source file and its SHA-256 at capture time;
+    when the source has changed since, the counters no longer describe the
+    kernel and are reported as null."""
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            if not line.startswith("traffic-record:"):
+                continue
+            try:
+                rec = json.loads(line.split(":", 1)[1])
+            except ValueError:
+                continue
+            if rec.get("kernel") != kernel or rec.get("workload") != workload:
+                continue
+            src = os.path.join(ROOT, rec["source"])
+            fresh = os.path.exists(src) and _sha256(src) == rec.get("source_sha256")
+            return {"bytes_per_launch": rec.get("dram_bytes_per_launch") if fresh else None,
+                    "fp64_flops_per_launch": rec.get("fp64_flops_per_launch") if fresh else None,
+                    "summary": os.path.relpath(path, ROOT), "fresh": fresh,
+                    "capture": rec.get("capture")}
+    return {"bytes_per_launch": None, "fp64_flops_per_launch": None, "summary": None, "fresh": False,
+            "capture": None}
 
 
 def apply_only(args, n):
@@ -374,7 +427,6 @@ def main():
 
     # ---- timed region
     import ctypes as C
-    lib.cheb_profile_enable(1)
     l0 = lib.cheb_launch_count()
     with ClockSampler(local) as clk:
         barrier()
@@ -387,10 +439,6 @@ def main():
         torch.cuda.synchronize()
         barrier()
     launches = lib.cheb_launch_count() - l0
-    ms = (C.c_double * 8)()
-    cnt = (C.c_longlong * 8)()
-    lib.cheb_profile_read(ms, cnt)
-    lib.cheb_profile_enable(0)
     elapsed = e0.elapsed_time(e1) / 1e3
     if world > 1:
         import torch.distributed as dist
@@ -398,8 +446,26 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
     per_step = elapsed / args.steps
-    phase = {nm: {"ms": ms[i] / args.steps, "count": cnt[i] // args.steps} for i, nm in enumerate(
+
+    # ---- phase split from one more step with the event profiler on (outside
+    # the timed region: the events add host work).  GPU time not inside any
+    # instrumented phase is idle time (host synchronisation, launch gaps).
+    lib.cheb_profile_enable(1)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms = (C.c_double * 8)()
+    cnt = (C.c_longlong * 8)()
+    lib.cheb_profile_read(ms, cnt)
+    lib.cheb_profile_enable(0)
+    prof_step_ms = p0.elapsed_time(p1)
+    phase = {nm: {"ms": ms[i], "count": cnt[i]} for i, nm in enumerate(
         ["apply64", "apply32", "prec64", "prec32", "orth64", "orth32", "prolong", "other"])}
+    phase["idle"] = {"ms": prof_step_ms - sum(ms[i] for i in range(8)), "count": 0}
+    phase["profiled_step_ms"] = prof_step_ms
 
     # ---- apply throughput at the finest level
     pf, nf = plans[-1], levels[-1]
@@ -425,12 +491,34 @@ def main():
     apply = {"fp32_gdofs": ntot / t32 / 1e9, "fp64_gdofs": ntot / t64 / 1e9,
              "fp32_ms": t32 * 1e3, "fp64_ms": t64 * 1e3}
 
+    # ---- measured FMA peaks of the CUDA cores, clocks sampled meanwhile
+    fma = {}
+    with ClockSampler(local) as clk_fma:
+        for nm, prec in (("fp64", P.FP64), ("fp32", P.FP32)):
+            tf, msl = C.c_double(), C.c_double()
+            P.check(lib.cheb_fma_peak(prec, C.byref(tf), C.byref(msl)), "cheb_fma_peak")
+            fma[nm + "_tflops"] = tf.value
+    fma["clocks"] = clk_fma.summary()
+    # FP64 apply (transform route, FP64-pipe bound) against the FP64 peak:
+    # executed FP64 flops per launch from one ncu capture of the kernel
+    rec64 = profile_record("tf_pass_kernel<double>", f"fp64 apply {nf}^3")
+    fl64 = rec64["fp64_flops_per_launch"]
+    fp64_roof = {"bound": "alu", "kernel": f"tf_pass_kernel<double> ({pf.dim} launches per apply)",
+                 "unit": "TFLOP/s", "peak": fma["fp64_tflops"],
+                 "peak_source": "measured FP64 FMA throughput (cheb_fma_peak, this run)",
+                 "achieved": (fl64 * pf.dim / t64 / 1e12) if fl64 else None,
+                 "frac": (fl64 * pf.dim / t64 / 1e12 / fma["fp64_tflops"]) if fl64 else None,
+                 "flops_source": rec64["summary"], "flops_fresh": rec64["fresh"],
+                 "dram_bytes_per_launch": rec64["bytes_per_launch"],
+                 "apply_ms": t64 * 1e3}
+
     # ---- plain FP64 comparison solve
     fp64 = None
     if not args.no_fp64:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        u64, infos64, _ = P.solve_hierarchy(plans, Ks, bs, mode=0, rtol=1e-12, check_status=False)
+        u64, infos64, _ = P.solve_hierarchy(plans, Ks, bs, mode=0, rtol=1e-12, check_status=False,
+                                            restart=args.restart)
         torch.cuda.synchronize()
         fp64 = {"time_to_solve_s": time.perf_counter() - t0,
                 "iterations": [i["iterations"] for i in infos64],
@@ -469,17 +557,15 @@ def main():
     tp32 = time_prec(torch.float32)
     apply["fdm_fp32_ms"] = tp32 * 1e3
 
-    # ---- roofline of the dominant kernel: the FP32 apply passes (the largest
-    # single-kernel share of the solve; the Arnoldi dot/axpy work is split
-    # over two kernels).  Per launch = the finest-level apply time (CUDA events
-    # on the plan stream around 20 applies, right after the timed region) /
-    # launches; the level-mixed per-apply time of the timed solve itself (phase
-    # profiler) is reported beside it.  Algorithmic bytes per apply (FP32
-    # words per DOF):
-    #   tensor route: x 3 + 2 (phase 1 reads u, K, writes Q; phase 2 of the
-    #   first axis reads Q, writes out), y and z 3 + 3 (phase 2 also reads the
-    #   accumulated out) = 17 words over 6 launches;
-    #   transform route: x 3, y 4, z 4 = 11 words over 3 launches.
+    # ---- roofline of the dominant kernel: the FP32 operator apply (the
+    # largest single-kernel share of the solve; the Arnoldi dot/axpy work is
+    # split over two kernels).  Unit: one apply at the finest level, timed with
+    # CUDA events on the plan stream around 20 applies right after the timed
+    # region (the level-mixed per-apply time inside the timed solve, from the
+    # phase profiler, is reported beside it).  Algorithmic bytes per apply,
+    # the floor of the operator: read u, read K, write Au = 3 FP32 words per
+    # DOF; the three-pass schedule (x pass reads u, K and writes the output,
+    # the y and z passes also read the accumulated output) moves 11 words.
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -487,28 +573,33 @@ def main():
         pass
     hbm = peaks.get("hbm_gbs", 6400.0)
     bf16 = peaks.get("bf16_tflops", 1800.0)
-    tensor_route = args.route32 == "tensor"
-    launches_per_apply = 6 if tensor_route else 3
-    words = 17.0 if tensor_route else 11.0
-    ph = phase.get("apply32", {"ms": 0.0, "count": 0})
-    per = t32 / launches_per_apply
-    algo = words * 4 * ntot / launches_per_apply
-    roof = {"bound": "hbm",
-            "kernel": ("dense_pass_kernel (tcgen05 split-TF32 FP32 apply, 6 launches per apply)"
-                       if tensor_route else "tf_pass_kernel (FP32 apply, 3 launches per apply)"),
-            "achieved": algo / per / 1e9, "peak": hbm, "unit": "GB/s", "frac": algo / per / 1e9 / hbm,
-            # DRAM bytes per launch, averaged over one apply, from one ncu capture
-            # of this kernel (x phase 1: 136.5 MB read + 28.7 MB written; x
-            # phase 2: 77.8 + 12.8; y phase 1: 136.4 + 28.8, taken for the other
-            # three passes, which move the same words; profiles/dense_pass_fp32_257.md);
-            # transform route: not captured
-            "traffic": 152.8e6 if tensor_route else None, "algorithmic_bytes_per_launch": algo,
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
+    tensor_route = all(pf.route32(a) == P.ROUTE_TENSOR for a in range(pf.dim))
+    launches_per_apply = 2 * pf.dim if tensor_route else pf.dim
+    kernel = "dense_pass_kernel" if tensor_route else "tf_pass_kernel<float>"
+    floor_bytes = 3 * 4 * ntot
+    achieved = floor_bytes / t32 / 1e9
+    tr = profile_record(kernel, f"fp32 apply {nf}^3")
+    traffic = tr["bytes_per_launch"]
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic,
+            "kernel": (f"{kernel} ({launches_per_apply} launches per apply; "
+                       + ("tcgen05 split-TF32 dense derivative)" if tensor_route else "FFT transform route)")),
+            "unit_of_work": f"one FP32 operator apply at {nf}^3 ({ntot} DOF)",
+            "algorithmic_bytes_per_apply": floor_bytes,
+            "algorithmic_bytes_per_launch": floor_bytes / launches_per_apply,
+            "achieved_11word_model_gbs": 11 * 4 * ntot / t32 / 1e9,
+            "frac_11word_model": 11 * 4 * ntot / t32 / 1e9 / hbm,
+            "dram_gbs": (traffic * launches_per_apply / t32 / 1e9) if traffic else None,
+            "traffic_source": tr["summary"], "traffic_capture": tr["capture"],
+            "traffic_fresh": tr["fresh"],
+            "peak_source": ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                            else "fallback 6400 GB/s"),
             "apply_ms_finest": t32 * 1e3,
-            "apply_ms_timed_solve_all_levels": (ph["ms"] / ph["count"]) if ph["count"] else None}
+            "apply_ms_timed_solve_all_levels": (phase["apply32"]["ms"] / phase["apply32"]["count"])
+            if phase["apply32"]["count"] else None}
     if tensor_route:
-        flops = 2.0 * ntot * levels[-1] * 6  # useful dense-D flops of one apply
-        roof["tensor_tflops_useful"] = flops / t32 / 1e12
+        flops = 2.0 * ntot * nf * 2 * pf.dim  # dense-D products of one apply (2 per axis)
+        roof["tensor_tflops_dense_d"] = flops / t32 / 1e12
         roof["tensor_frac_split_tf32"] = 3.0 * flops / t32 / 1e12 / (bf16 * 1.1 / 2.25)
     # preconditioner contractions beside it (tcgen05, tensor bound)
     m = nf - 2
@@ -519,18 +610,24 @@ def main():
                  "frac": fl / tp32 / 1e12 / tf32_peak,
                  "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 ratio)",
                  "note": "whole preconditioner time; split-TF32 issues 3 TF32 MMAs per useful flop"}
-    apply_roof = prec_roof
 
-    # ---- CPU baseline (oracle on the host cores, bounded sample)
-    cpu = None
+    # ---- the oracle's hierarchical solve on the host cores: CPU baseline and
+    # the relative L2 error of the GPU solutions at every level
+    cpu, parity = None, None
     if rank == 0 and not args.no_cpu:
-        its64 = fp64["iterations"] if fp64 else [i["iterations"] for i in infos]
-        est, per_it = oracle_estimate(levels, args.contrast, its64, reps=1)
-        cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": ("one timed oracle GMRES iteration (dense Kronecker apply + constant-K "
-                          f"preconditioner) per level {levels}, "
-                          f"{', '.join(f'{p:.2f}' for p in per_it)} s each, times the GPU FP64 "
-                          f"iteration counts {its64}")}
+        uo, io, eref_o, t_or = oracle_hierarchy(levels, args.contrast)
+        us_h = [u.cpu().numpy() for u in us]
+        parity = {"rel_err_vs_oracle_mixed": [float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                                               for a, b in zip(us_h, uo)],
+                  "oracle_iterations": [i["iterations"] for i in io],
+                  "oracle_rel_residual": [i["rel_residual"] for i in io],
+                  "oracle_e_ref": eref_o}
+        if fp64 is not None:
+            u64h = [u.cpu().numpy() for u in u64]
+            parity["rel_err_vs_oracle_fp64"] = [float(np.linalg.norm(a - b) / np.linalg.norm(b))
+                                                for a, b in zip(u64h, uo)]
+        cpu = {"value": t_or, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": oracle_sample_text(levels, io, t_or)}
 
     if rank == 0:
         line = {
@@ -543,7 +640,12 @@ def main():
             "refinements_per_level": [i["refinements"] for i in infos],
             "rel_residual": infos[-1]["rel_residual"], "e_ref": eref,
             "apply": apply, "fp64": fp64, "phase_ms_per_step": phase,
-            "roofline": roof, "prec_roofline": apply_roof, "fp32_route": args.route32,
+            "routes_per_level": [p.chosen_routes for p in plans],
+            "roofline": roof, "prec_roofline": prec_roof, "fp64_apply_roofline": fp64_roof,
+            "fma_peaks": fma,
+            "fp32_routes_finest": [pf.route32(a) for a in range(pf.dim)],
+            "rel_err_vs_oracle": parity["rel_err_vs_oracle_mixed"][-1] if parity else None,
+            "oracle_parity": parity,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

@@ -263,8 +263,9 @@ int cheb_prolong(cheb_plan coarse, cheb_plan fine, int prec, const void* u_c, vo
  * 65^3 -> 129^3 fit in FP64 and FP32, 129^3 -> 257^3 does not.  The first call on
  * a device looks up the array's device address for that device (a
  * cudaGetSymbolAddress call), so make that first call before any stream
- * capture.  All calls share the one array and nothing in it needs to start
- * at zero; calls that overlap on the GPU (other streams, other host
+ * capture.  The current device must be the one the plans were created on
+ * (else CHEB_ERR_ARG).  All calls share the one array and nothing in it needs
+ * to start at zero; calls that overlap on the GPU (other streams, other host
  * threads) race on it, so order them on one stream. */
 int cheb_prolong_noalloc(cheb_plan coarse, cheb_plan fine, int prec, const void* u_c, void* u_f);
 
@@ -305,6 +306,15 @@ int cheb_profile_enable(int on);
 /* Totals since enabling: ms[8] milliseconds and counts[8] timed intervals
  * (either may be NULL).  Waits for the recorded events. */
 int cheb_profile_read(double* ms, long long* counts);
+
+/* Measured throughput of the CUDA-core fused multiply-add pipe of the
+ * current device in precision prec (CHEB_FP64 or CHEB_FP32), in TFLOP/s
+ * (one FMA = two flops): independent FMA chains in every thread of a grid
+ * that fills every SM, about 20 ms per launch, five launches timed with CUDA
+ * events.  A measurement helper for the ALU-bound kernels' rooflines (the
+ * paper has no counterpart); allocates a few KB, synchronises its own
+ * stream.  ms_per_launch (nullable) receives the launch time. */
+int cheb_fma_peak(int prec, double* tflops, double* ms_per_launch);
 
 /* Human-readable text of a status code, and the message of the last failed
  * call on the calling thread. */

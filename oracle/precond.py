@@ -179,3 +179,30 @@ def solve_preconditioned(K: np.ndarray, b: np.ndarray, grid: Grid, x0=None, rtol
     info["plain_rel_residual"] = float(np.linalg.norm(r) / np.linalg.norm(b))
     info["kref"] = M.kref
     return u, info
+
+
+def solve_hierarchy(Ks, bs, grids, rtol: float = 1e-12, restart: int = 50, maxiter: int = 5000,
+                    x0=None):
+    """Hierarchical refinement (Alg. 4, Sec. 2.3.3) with the oracle's own pieces:
+    solve the coarsest level (from ``x0`` or zero), then for every finer level
+    prolong the previous solution by barycentric interpolation (the same
+    polynomial as the paper's coefficient zero-padding) and use it as the
+    initial guess of that level's preconditioned GMRES.
+
+    ``Ks``, ``bs``: per-level conductivity and right-hand side sampled on that
+    level's grid; ``grids``: oracle Grids of doubling N.  Returns (solutions,
+    infos, e_ref) with e_ref[l] = ||u_l - P u_{l-1}|| / ||u_l|| (e_ref[0] = 0)."""
+    from .core import e_ref as _e_ref, prolong
+    us, infos, eref = [], [], []
+    u0 = x0
+    for lvl, (K, b, g) in enumerate(zip(Ks, bs, grids)):
+        guess = None
+        if lvl > 0:
+            guess = prolong(us[-1], grids[lvl - 1], g)
+        elif u0 is not None:
+            guess = u0
+        u, info = solve_preconditioned(K, b, g, x0=guess, rtol=rtol, restart=restart, maxiter=maxiter)
+        us.append(u)
+        infos.append(info)
+        eref.append(0.0 if guess is None or lvl == 0 else _e_ref(u, guess))
+    return us, infos, eref

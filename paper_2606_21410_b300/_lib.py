@@ -98,6 +98,7 @@ _SIGS = {
     "cheb_solve_hierarchy": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo), f64p]),
     "cheb_launch_count": (C.c_longlong, []),
+    "cheb_fma_peak": (i32, [i32, f64p, f64p]),
     "cheb_profile_enable": (i32, [i32]),
     "cheb_profile_read": (i32, [f64p, C.POINTER(C.c_longlong)]),
     "cheb_status_str": (C.c_char_p, [i32]),

@@ -18,8 +18,6 @@
 // Dense route: f' = D f with D staged in shared memory.
 #include <cstdio>
 
-#include <atomic>
-
 #include "device.cuh"
 #include "umma.h"
 
@@ -579,23 +577,17 @@ template <> AxisK<float> axis_k<float>(const AxisTables& t) {
 template <typename T, int ROUTE, int P, int CM>
 static int launch_kernel(const Geom& g, int axis, int kind, const AxisK<T>& ak, const T* K,
                          const T* u, T* out, cudaStream_t s, int nblocks) {
-  static std::atomic<size_t> configured{0};  // per instantiation
+  int st;
   if constexpr (ROUTE == CHEB_ROUTE_TRANSFORM) {
     auto kern = tf_pass_kernel<T, P, CM>;
     constexpr size_t smem = tf_smem_bytes<T, P>();
-    if (smem > configured) {
-      CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      configured = smem;
-    }
+    if ((st = ensure_smem_attr((const void*)kern, smem))) return st;
     kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
     CHEB_LAUNCH_CHECK("tf_pass_kernel");
   } else {
     auto kern = line_pass_kernel<T, ROUTE, P, CM>;
     const size_t smem = pass_smem_bytes<T>(ROUTE, ak.n, P);
-    if (smem > configured) {
-      CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      configured = smem;
-    }
+    if ((st = ensure_smem_attr((const void*)kern, smem))) return st;
     kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
     CHEB_LAUNCH_CHECK("line_pass_kernel");
   }

@@ -71,6 +71,11 @@ namespace cheb {
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Raise the dynamic shared-memory limit of kernel `func` to at least `bytes`
+// on the current device.  The largest value set is remembered per (kernel,
+// device), so each device gets its own cudaFuncSetAttribute call.
+int ensure_smem_attr(const void* func, size_t bytes);
+
 #define CHEB_CUDA(call)                                   \
   do {                                                    \
     cudaError_t _e = (call);                              \

@@ -3,8 +3,10 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hostmath.h"
@@ -20,6 +22,22 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 int cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
   return e == cudaErrorMemoryAllocation ? CHEB_ERR_NOMEM : CHEB_ERR_CUDA;
+}
+
+namespace {
+std::mutex g_attr_mu;
+std::map<std::pair<const void*, int>, size_t> g_attr;  // (kernel, device) -> bytes set
+}  // namespace
+
+int ensure_smem_attr(const void* func, size_t bytes) {
+  int dev = 0;
+  CHEB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  size_t& have = g_attr[std::make_pair(func, dev)];
+  if (bytes <= have) return CHEB_OK;
+  CHEB_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  have = bytes;
+  return CHEB_OK;
 }
 
 int launch_rhs(const cheb_plan_s* p, const double* f, const double* const face_vals[6], double* b,

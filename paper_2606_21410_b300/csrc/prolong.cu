@@ -11,7 +11,6 @@
 #include <mutex>
 #include <string>
 
-#include <atomic>
 
 #include "device.cuh"
 #include "fdm.h"
@@ -140,11 +139,8 @@ static int launch_prolong_pass(int a, const int dims[3], const typename C2<T>::t
                                const typename C2<T>::t* twf, const T* in, T* out, cudaStream_t s) {
   auto kern = prolong_pass_kernel<T, PC>;
   const size_t smem = prolong_smem<T, PC>();
-  static std::atomic<size_t> configured{0};
-  if (smem > configured) {
-    CHEB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  int st;
+  if ((st = ensure_smem_attr((const void*)kern, smem))) return st;
   int nblocks;
   if (a == 0) nblocks = (dims[1] * dims[2] + kTileL - 1) / kTileL;
   else nblocks = ((dims[0] + kTileL - 1) / kTileL) * (a == 1 ? dims[2] : dims[1]);
@@ -261,6 +257,13 @@ extern "C" int cheb_prolong_noalloc(cheb_plan coarse, cheb_plan fine, int prec, 
     set_error("cheb_prolong_noalloc: the grids need " + std::to_string(off2 + n2 * esz) +
               " bytes of intermediate storage, above its fixed 16 MiB (use cheb_prolong)");
     return CHEB_ERR_UNSUPPORTED;
+  }
+  // the scratch address is per device: the plans' device must be current
+  int dev = 0;
+  CHEB_CUDA(cudaGetDevice(&dev));
+  if (dev != coarse->device || dev != fine->device) {
+    set_error("cheb_prolong_noalloc: the current device is not the plans' device");
+    return CHEB_ERR_ARG;
   }
   void* base = nullptr;
   if ((st = noalloc_scratch(&base))) return st;

@@ -389,21 +389,29 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
   while (true) {
     // ---- residual r = c - B x into V[0]
     if (zero) {
+      prof_begin(kProfOther, s);
       if ((st = k_scale<T>(Vp(0), c, 1.0, n, s))) return st;
+      prof_end(kProfOther, s);
     } else {
       if ((st = op_B<T>(p, w, o, K, x, Vp(0), B.tmp, s))) return st;
       stt.applies++;
+      prof_begin(kProfOther, s);
       if ((st = k_residual<T>(Vp(0), c, n, s))) return st;
+      prof_end(kProfOther, s);
     }
     const T* v0 = Vp(0);
+    prof_begin(Cat<T>::orth, s);
     if ((st = k_mdot<T>(w.rs, &v0, 0, Vp(0), n, true, dv, s))) return st;
+    prof_end(Cat<T>::orth, s);
     if ((st = sync_read(w, 1, s))) return st;
     const double beta = std::sqrt(hv[0]);
     stt.resid = beta;
     if (!std::isfinite(beta)) { set_error("non-finite residual"); return CHEB_ERR_NONFINITE; }
     if (beta <= o.tol_abs) { stt.converged = true; return CHEB_OK; }
     if (stt.iterations >= o.maxiter) return CHEB_ERR_NOT_CONVERGED;
+    prof_begin(Cat<T>::orth, s);
     if ((st = k_scale<T>(Vp(0), Vp(0), 1.0 / beta, n, s))) return st;
+    prof_end(Cat<T>::orth, s);
     stt.cycles++;
     // ---- Arnoldi: first m_eff Krylov directions, then the augmentation vectors
     const int m_eff = m + (kk - naug);
@@ -424,7 +432,9 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
         stt.applies++;
       } else {
         const int a = (next_slot - naug + (j - m_eff) + 4 * kk) % kk;  // oldest first
+        prof_begin(Cat<T>::orth, s);
         if ((st = k_scale<T>(wv, BZp(a), 1.0, n, s))) return st;
+        prof_end(Cat<T>::orth, s);
       }
       const T* src[kMaxVecs];
       for (int i = 0; i <= j; ++i) src[i] = Vp(i);
@@ -445,7 +455,9 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
       if (!std::isfinite(hn)) { set_error("non-finite Arnoldi norm"); return CHEB_ERR_NONFINITE; }
       H[(size_t)(j + 1) * nbasis + j] = hn;
       if (hn > 0) {
+        prof_begin(Cat<T>::orth, s);
         if ((st = k_scale_inv_norm<T>(wv, dv + kMaxVecs + 1, n, s))) return st;
+        prof_end(Cat<T>::orth, s);
       }
       // Givens: copy the column, apply previous rotations, make a new one
       for (int i = 0; i <= j + 1; ++i) Hr[(size_t)i * nbasis + j] = H[(size_t)i * nbasis + j];
@@ -474,6 +486,7 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
       y[i] = Hr[(size_t)i * nbasis + i] != 0.0 ? t / Hr[(size_t)i * nbasis + i] : 0.0;
     }
     // ---- dx = W y into tmp (with its norm), x += dx
+    prof_begin(kProfOther, s);
     {
       const T* src[kMaxVecs];
       double coef[kMaxVecs];
@@ -491,13 +504,16 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
         if ((st = k_maxpy<T>(w.rs, one, cone, 1, 1.0, x, n, nullptr, s))) return st;
       }
       zero = false;
+      prof_end(kProfOther, s);
       if (kk > 0) {
         if ((st = sync_read(w, kMaxVecs + 2, s))) return st;
         const double dxn = std::sqrt(std::max(0.0, hv[kMaxVecs + 1]));
         if (dxn > 0) {
           // store z = dx/|dx| and B z = V Hbar y / |dx| (linearity: B W = V Hbar)
           const int slot = next_slot;
+          prof_begin(kProfOther, s);
           if ((st = k_scale<T>(Zp(slot), B.tmp, 1.0 / dxn, n, s))) return st;
+          prof_end(kProfOther, s);
           double hy[kMaxVecs];
           const T* vs[kMaxVecs];
           for (int i = 0; i <= steps; ++i) {
@@ -507,7 +523,9 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
             hy[i] = t / dxn;
             vs[i] = Vp(i);
           }
+          prof_begin(kProfOther, s);
           if ((st = k_maxpy<T>(w.rs, vs, hy, steps + 1, 0.0, BZp(slot), n, nullptr, s))) return st;
+          prof_end(kProfOther, s);
           next_slot = (next_slot + 1) % kk;
           naug = std::min(naug + 1, kk);
         }
@@ -643,18 +661,28 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   double eta = 1.0;
   for (int it = 0; it <= o.max_refinements; ++it) {
     // r64 = b - A u (FP64)
+    prof_begin(kProfApply64, s);
     if ((st = transpose ? launch_adjoint_apply<double>(p, K, u, w.r64, s)
                         : launch_apply<double>(p, K, u, w.r64, s)))
       return st;
+    prof_end(kProfApply64, s);
     info.applies_fp64++;
+    prof_begin(kProfOther, s);
     if ((st = k_residual<double>(w.r64, b, n, s))) return st;
     const double sr = norm2_dev(w, w.r64, s, &st);
+    prof_end(kProfOther, s);
     if (st) return st;
     if (!std::isfinite(sr)) { set_error("non-finite residual"); return CHEB_ERR_NONFINITE; }
     if (sr == 0.0) { eta = 0.0; rc = CHEB_OK; break; }
+    prof_begin(kProfOther, s);
     if ((st = k_cast_scale<float, double>(B.tmp, w.r64, 1.0 / sr, n, s))) return st;
+    prof_end(kProfOther, s);
+    prof_begin(kProfPrec32, s);
     if ((st = precond<float>(p, w, lo, B.tmp, B.c, s))) return st;
+    prof_end(kProfPrec32, s);
+    prof_begin(kProfOther, s);
     const double cn = norm2_t<float>(w, B.c, s, &st);
+    prof_end(kProfOther, s);
     if (st) return st;
     eta = sr * cn / nb;
     if (o.verbose) fprintf(stderr, "[cheb] refinement %d: eta = %.3e\n", it, eta);
@@ -672,7 +700,9 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     info.graph_captures += stt.captures;
     info.refinements++;
     info.rel_residual_inner = stt.resid / cn;
+    prof_begin(kProfOther, s);
     if ((st = k_axpy64<float>(u, B.x, sr, n, s))) return st;
+    prof_end(kProfOther, s);
   }
   CHEB_CUDA(cudaStreamSynchronize(s));
   info.rel_residual = eta;

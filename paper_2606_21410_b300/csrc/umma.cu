@@ -525,13 +525,7 @@ int launch_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M
   if ((st = make_map(&mx, X, K, M, kBM, BK))) return st;
   if ((st = make_map(&mh, Wh, K, n_tile, n_tile, BK))) return st;
   if ((st = make_map(&ml, Wl, K, n_tile, n_tile, BK))) return st;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(umma_tf32x3_rot_kernel<BK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_bytes<BK>(256));
-  });
-  CHEB_CUDA(attr_err);
+  if ((st = ensure_smem_attr((const void*)umma_tf32x3_rot_kernel<BK>, smem_bytes<BK>(256)))) return st;
   const int ntiles = (M + kBM - 1) / kBM;
   const int grid = std::min(ntiles, sm_count());
   umma_tf32x3_rot_kernel<BK><<<grid, kUThreads, smem_bytes<BK>(n_tile), s>>>(mx, mh, ml, Y, M, N, K, n_tile,
@@ -1272,13 +1266,8 @@ static int launch_dense(const CUtensorMap& mh, const CUtensorMap& ml, const Line
   int tmem_cols = 32;
   while (tmem_cols < nAx) tmem_cols *= 2;
   const int nbuf = 2 * tmem_cols <= 512 ? 2 : 1;
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [] {
-    attr_err = cudaFuncSetAttribute(dense_pass_kernel<XAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)dense_smem_bytes(256));
-  });
-  CHEB_CUDA(attr_err);
+  int st;
+  if ((st = ensure_smem_attr((const void*)dense_pass_kernel<XAX>, dense_smem_bytes(256)))) return st;
   const int ntiles = (lg.nl + kBM - 1) / kBM;
   const int grid = std::min(ntiles, sm_count());
   dense_pass_kernel<XAX><<<grid, dense_threads<XAX>(), dense_smem_bytes(nAx), s>>>(mh, ml, lg, A, nA,

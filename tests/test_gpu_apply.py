@@ -3,11 +3,15 @@
 ragged tiles), their transposes, the operator apply with every boundary-type
 pattern, the adjoint apply, and the right-hand side.
 
-Tolerances (relative L2 of the whole field).  One derivative of the degree-N
-interpolant amplifies input rounding by ~||D|| ~ N^2, the apply applies two,
-so both are bounded by C N^2 eps relative to the output scale with
-C = 4 in FP64 (eps = 2.2e-16) and C = 8 in FP32 (eps = 1.2e-7); the apply is
-compared relative to ||D||-scaled magnitude max|K| ||D||^2 ||u||."""
+Tolerances: relative L2 error against the oracle's output, with uniform
+random input fields.  Their derivatives are dominated by the top Chebyshev
+modes, so the rounding of the line transforms stays at a few units of the
+working precision relative to the output (measured on B300: FP64 at most
+2.3e-15, FP32 at most 1.9e-7 for derivatives, applies and adjoint applies).
+The bounds, 1e-14 (FP64) and 1e-6 (FP32), sit about five times above that.
+Boundary rows are checked element-wise as well: Dirichlet rows are copies of
+u (bit-exact in FP64), Neumann rows are one derivative and carry the same
+relative error bound against the largest Neumann-row value."""
 import itertools
 
 import numpy as np
@@ -19,8 +23,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-EPS = {torch.float64: 2.2e-16, torch.float32: 1.2e-7}
-C_TOL = {torch.float64: 4.0, torch.float32: 8.0}
+TOL = {torch.float64: 1e-14, torch.float32: 1e-6}
 
 
 def _plan(n, lo=(-1, -1, -1), hi=(1, 1, 1), bc=(0,) * 6):
@@ -34,10 +37,6 @@ def _dev(a, dtype=torch.float64):
 
 def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def _tol(N, dtype):
-    return C_TOL[dtype] * N * N * EPS[dtype]
 
 
 CASES = [
@@ -59,11 +58,10 @@ def test_deriv_transform_route_matches_dense_D(case, dtype):
         assert p.route(a) == 0
         ref = O.grad(u, g, a)
         got = p.deriv(ud, a).double().cpu().numpy()
-        N = n[a] - 1
-        assert _rel(got, ref) < _tol(N, dtype), (a, _rel(got, ref))
+        assert _rel(got, ref) < TOL[dtype], (a, _rel(got, ref))
         refT = np.moveaxis(np.tensordot(g.D(a).T, u, axes=([1], [2 - a])), 0, 2 - a)
         gotT = p.deriv(ud, a, transpose=True).double().cpu().numpy()
-        assert _rel(gotT, refT) < _tol(N, dtype), (a, "T", _rel(gotT, refT))
+        assert _rel(gotT, refT) < TOL[dtype], (a, "T", _rel(gotT, refT))
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -75,10 +73,10 @@ def test_deriv_dense_route_any_size(dtype):
     for a in range(3):
         assert p.route(a) == 1
         got = p.deriv(_dev(u, dtype), a).double().cpu().numpy()
-        assert _rel(got, O.grad(u, g, a)) < _tol(n[a] - 1, dtype)
+        assert _rel(got, O.grad(u, g, a)) < TOL[dtype], (a, _rel(got, O.grad(u, g, a)))
         gotT = p.deriv(_dev(u, dtype), a, transpose=True).double().cpu().numpy()
         refT = np.moveaxis(np.tensordot(g.D(a).T, u, axes=([1], [2 - a])), 0, 2 - a)
-        assert _rel(gotT, refT) < _tol(n[a] - 1, dtype)
+        assert _rel(gotT, refT) < TOL[dtype], (a, "T", _rel(gotT, refT))
 
 
 def test_dense_and_transform_routes_agree():
@@ -107,9 +105,19 @@ def test_deriv_exact_on_chebyshev_polynomials():
         assert np.abs(d - ex).max() < 1e-13 * max(1, k * k) * N
 
 
-def _apply_scale(K, u, g):
-    s = np.abs(K).max() * np.linalg.norm(u)
-    return s * max(np.abs(g.D(a)).max() ** 2 for a in g.axes)
+def _check_boundary_rows(got, ref, u, g, bc, dtype):
+    """Dirichlet rows copy u (exactly in FP64); Neumann rows element-wise
+    against the oracle relative to their largest value."""
+    own = O.owners(g)
+    dmask = np.isin(own, [f for f in range(2 * g.dim) if bc[f] == 0])
+    if dtype == torch.float64:
+        assert np.array_equal(got[dmask], u[dmask])
+    else:
+        assert np.array_equal(got[dmask], u.astype(np.float32).astype(np.float64)[dmask])
+    nmask = np.isin(own, [f for f in range(2 * g.dim) if bc[f] == 1])
+    if nmask.any():
+        err = np.abs(got[nmask] - ref[nmask]).max() / np.abs(ref[nmask]).max()
+        assert err < TOL[dtype], ("Neumann rows", err)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -122,13 +130,11 @@ def test_apply_every_bc_pattern(bc, dtype):
     K = W.random_positive_field(g.shape, 202)
     ref = O.apply(u, K, g)
     got = p.apply(_dev(K, dtype), _dev(u, dtype)).double().cpu().numpy()
-    err = np.linalg.norm(got - ref) / _apply_scale(K, u, g)
-    assert err < _tol(32, dtype), err
-    # boundary rows exactly: Dirichlet rows copy u
-    own = O.owners(g)
-    dmask = np.isin(own, [f for f in range(6) if bc[f] == 0])
-    if dtype == torch.float64:
-        assert np.array_equal(got[dmask], u[dmask])
+    err = _rel(got, ref)
+    assert err < TOL[dtype], err
+    interior = O.owners(g) < 0
+    assert np.abs(got[interior] - ref[interior]).max() / np.abs(ref[interior]).max() < TOL[dtype]
+    _check_boundary_rows(got, ref, u, g, bc, dtype)
 
 
 @pytest.mark.parametrize("dim,n", [(1, (33,)), (2, (17, 65)), (3, (5, 9, 3))])
@@ -140,7 +146,8 @@ def test_apply_lower_dimensions(dim, n):
     K = W.random_positive_field(g.shape, 310 + dim)
     ref = O.apply(u, K, g)
     got = p.apply(_dev(K), _dev(u)).cpu().numpy()
-    assert np.linalg.norm(got - ref) / _apply_scale(K, u, g) < _tol(max(n) - 1, torch.float64)
+    assert _rel(got, ref) < TOL[torch.float64], _rel(got, ref)
+    _check_boundary_rows(got, ref, u, g, bc, torch.float64)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -153,7 +160,7 @@ def test_adjoint_apply_matches_oracle_and_dot_product(dtype):
     K = W.random_positive_field(g.shape, 402)
     ref = O.adjoint_apply(lam, K, g)
     got = p.adjoint_apply(_dev(K, dtype), _dev(lam, dtype)).double().cpu().numpy()
-    assert np.linalg.norm(got - ref) / _apply_scale(K, lam, g) < _tol(32, dtype)
+    assert _rel(got, ref) < TOL[dtype], _rel(got, ref)
     if dtype == torch.float64:
         x = W.random_field(g.shape, 403)
         Ax = p.apply(_dev(K), _dev(x)).cpu().numpy()
@@ -197,8 +204,10 @@ def _line_apply_samples(u, K, g, pts):
 
 @pytest.mark.parametrize("nn", [129, 257])
 def test_apply_full_size_sampled(nn):
-    """At 129^3 and 257^3 (the solve sizes), sampled interior rows against
-    the oracle's per-line dense evaluation, FP64 and FP32."""
+    """At 129^3 and 257^3 (the solve sizes): the FP64 apply at sampled
+    interior rows against the oracle's per-line dense evaluation, and the
+    FP32 apply over the whole field against the FP64 apply, for a smooth
+    field with noise and for a random field, on the two-phase medium."""
     bc = [0, 0, 1, 1, 1, 1]
     g = O.Grid((nn,) * 3, bc=bc)
     p = _plan((nn,) * 3, bc=bc)
@@ -208,11 +217,21 @@ def test_apply_full_size_sampled(nn):
     rng = W.rng(602)
     pts = [tuple(int(v) for v in rng.integers(1, nn - 1, size=3)) for _ in range(200)]
     ref = _line_apply_samples(u, K, g, pts)
-    scale = np.abs(ref).max()
-    for dtype in (torch.float64, torch.float32):
-        got = p.apply(_dev(K, dtype), _dev(u, dtype)).double().cpu().numpy()
-        vals = np.array([got[k, j, i] for (k, j, i) in pts])
-        assert np.abs(vals - ref).max() / scale < 20 * _tol(nn - 1, dtype), dtype
+    got64 = p.apply(_dev(K), _dev(u)).cpu().numpy()
+    vals = np.array([got64[k, j, i] for (k, j, i) in pts])
+    err64 = np.abs(vals - ref).max() / np.abs(ref).max()
+    assert err64 < 1e-12, err64
+    # FP32 against FP64 over the whole field: smooth + noise (the output
+    # is small against ||D||^2 ||u||, so the FP32 rounding shows, measured
+    # 1.0e-5 at 257^3 with contrast 100) and random (measured 2.5e-7)
+    got32 = p.apply(_dev(K, torch.float32), _dev(u, torch.float32)).double().cpu().numpy()
+    e32 = _rel(got32, got64)
+    assert e32 < 5e-5, e32
+    ur = W.random_field(g.shape, 603)
+    r64 = p.apply(_dev(K), _dev(ur)).cpu().numpy()
+    r32 = p.apply(_dev(K, torch.float32), _dev(ur, torch.float32)).double().cpu().numpy()
+    er = _rel(r32, r64)
+    assert er < TOL[torch.float32], er
 
 
 def test_autotuner_picks_a_route_and_caches(tmp_path):
@@ -236,4 +255,4 @@ def test_autotuner_picks_a_route_and_caches(tmp_path):
     K = W.random_positive_field(g.shape, 72)
     got = p.apply(_dev(K), _dev(u)).cpu().numpy()
     ref = O.apply(u, K, g)
-    assert np.linalg.norm(got - ref) / _apply_scale(K, u, g) < _tol(64, torch.float64)
+    assert _rel(got, ref) < TOL[torch.float64], _rel(got, ref)

@@ -72,25 +72,36 @@ def test_prolong_1d_2d_and_full_size_sampled():
 
 def test_hierarchy_spheres_matches_oracle():
     """Alg. 4 on the seeded sphere microstructure (contrast 100), 9^3 -> 17^3
-    -> 33^3, mixed precision; the final level against the oracle's solve."""
+    -> 33^3, mixed precision, against the oracle's own hierarchy (its
+    barycentric prolongation and preconditioned GMRES, K and b sampled on
+    its own grids): every level's solution and every level's refinement
+    indicator e_ref."""
     import paper_2606_21410_b300 as P
     bc = [0, 0, 1, 1, 1, 1]
     sp = W.sphere_packing(0)
+    xbc = lambda X, Y, Z: (X, (np.ones_like(X), 0 * X, 0 * X), 0 * X)
     plans, Ks, bs = [], [], []
+    grids, Ko, bo = [], [], []
     for n in (9, 17, 33):
         p = P.Plan((n,) * 3, bc=bc)
         X, Y, Z = p.mesh()
         K = W.two_phase_conductivity(X, Y, Z, sp, 1.0, 100.0)
-        faces = W.face_values(bc, p.nodes(0), p.nodes(1), p.nodes(2),
-                              lambda X, Y, Z: (X, (np.ones_like(X), 0 * X, 0 * X), 0 * X))
+        faces = W.face_values(bc, p.nodes(0), p.nodes(1), p.nodes(2), xbc)
         b = p.rhs(_dev(np.zeros(p.shape)), [_dev(f) for f in faces])
         plans.append(p)
         Ks.append(_dev(K))
         bs.append(b)
+        g = O.Grid((n,) * 3, bc=bc)
+        Xo, Yo, Zo = g.mesh()
+        grids.append(g)
+        Ko.append(W.two_phase_conductivity(Xo, Yo, Zo, sp, 1.0, 100.0))
+        bo.append(O.rhs(np.zeros(g.shape), W.face_values(bc, g.nodes(0), g.nodes(1), g.nodes(2), xbc), g))
     us, infos, eref = P.solve_hierarchy(plans, Ks, bs, mode=1, rtol=1e-12)
-    g = O.Grid((33,) * 3, bc=bc)
-    uo, _ = O.solve_preconditioned(Ks[-1].cpu().numpy(), bs[-1].cpu().numpy(), g, rtol=1e-13)
-    assert _rel(us[-1].cpu().numpy(), uo) < 1e-10
-    assert eref[0] == 0.0 and eref[1] > 0 and eref[2] > 0
-    # the prolonged guess already carries the coarse solution: e_ref is small
+    uo, io, eref_o = O.solve_hierarchy(Ko, bo, grids, rtol=1e-13)
+    for lvl in range(3):
+        assert _rel(us[lvl].cpu().numpy(), uo[lvl]) < 1e-10, lvl
+    assert eref[0] == 0.0 and eref_o[0] == 0.0
+    for lvl in (1, 2):
+        # e_ref differences of solutions that agree to 1e-10 relative
+        assert abs(eref[lvl] - eref_o[lvl]) <= 1e-8 * eref_o[lvl], (lvl, eref[lvl], eref_o[lvl])
     assert eref[2] < 0.5

@@ -131,6 +131,74 @@ def test_spheres_33_vs_oracle_gmres(mode):
     assert _rel(u.cpu().numpy(), uo) < 1e-10, (info, io["iterations"])
 
 
+def _two_phase_level(n, contrast, nodes):
+    """K and b of the two-phase problem on one grid (f = 0, u = x on x = +-1,
+    zero normal derivative elsewhere), from the given node arrays."""
+    bc = [0, 0, 1, 1, 1, 1]
+    X, Y, Z = W.mesh(*nodes)
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, contrast)
+    faces = W.face_values(bc, nodes[0], nodes[1], nodes[2],
+                          lambda X, Y, Z: (X, (np.ones_like(X), 0 * X, 0 * X), 0 * X))
+    return bc, K, faces
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_config3_129_two_phase_vs_oracle(mode):
+    """The 129^3 two-phase configuration (seeded spheres, 20% inclusions at
+    contrast 10, f = 0, u = x on x = +-1, zero flux elsewhere) against the
+    oracle's preconditioned GMRES solution: relative L2 error <= 1e-8, the
+    accuracy the hierarchical target asks of the finest level.  Each side
+    samples K and builds b on the grid it computes itself."""
+    import paper_2606_21410_b300 as P
+    n = (129, 129, 129)
+    g = O.Grid(n, bc=[0, 0, 1, 1, 1, 1])
+    bc, Ko, faces_o = _two_phase_level(129, 10.0, [g.nodes(0), g.nodes(1), g.nodes(2)])
+    bo = O.rhs(np.zeros(g.shape), faces_o, g)
+    uo, io = O.solve_preconditioned(Ko, bo, g, rtol=1e-12)
+    p = _plan(n, bc=bc)
+    _, Kp, faces_p = _two_phase_level(129, 10.0, [p.nodes(0), p.nodes(1), p.nodes(2)])
+    b = p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"), [_dev(f) for f in faces_p])
+    u, info = p.solve(_dev(Kp), b, mode=mode, rtol=1e-12)
+    err = _rel(u.cpu().numpy(), uo)
+    assert err <= 1e-8, (err, info, io["iterations"])
+
+
+def test_rel_diff_is_e_ref():
+    """cheb_rel_diff computes the refinement indicator of Sec. 2.3.3,
+    ||a - b|| / ||a||, the oracle's e_ref, on independent random fields."""
+    import paper_2606_21410_b300 as P
+    p = _plan((33, 17, 9))
+    a = W.random_field(p.shape, 81)
+    b = a + 1e-3 * W.random_field(p.shape, 82)
+    got = P.rel_diff(p, _dev(a), _dev(b))
+    assert abs(got - O.e_ref(a, b)) <= 1e-12 * O.e_ref(a, b)
+    got2 = P.rel_diff(p, _dev(b), _dev(a))
+    assert abs(got2 - O.e_ref(b, a)) <= 1e-12 * O.e_ref(b, a) and got2 != got
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_nonfinite_input_reports_status(mode):
+    """A NaN in the right-hand side or in K stops the solve with
+    CHEB_ERR_NONFINITE (-4) rather than returning a wrong answer."""
+    import paper_2606_21410_b300 as P
+    p = _plan((17, 17, 17), bc=[0, 0, 1, 1, 1, 1])
+    K = np.ones(p.shape)
+    b = W.random_field(p.shape, 83)
+    bn = b.copy()
+    bn[8, 8, 8] = np.nan
+    with pytest.raises(P.ChebError) as e:
+        p.solve(_dev(K), _dev(bn), mode=mode)
+    assert e.value.status == -4
+    Kn = K.copy()
+    Kn[3, 4, 5] = np.nan
+    with pytest.raises(P.ChebError) as e:
+        p.solve(_dev(Kn), _dev(b), mode=mode, kref=1.0)
+    assert e.value.status == -4
+    # the plan stays usable
+    u, info = p.solve(_dev(K), _dev(b), mode=mode)
+    assert info["status"] == 0
+
+
 def test_mixed_and_fp64_agree_and_mixed_uses_fp32():
     bc = [0, 0, 1, 1, 1, 1]
     n = (33, 17, 33)

@@ -105,11 +105,14 @@ def test_tcgen05_precond_full_size(nn):
 
 
 # ------------------------------------------------ tensor-core route of the apply
+#
+# Tolerances of the split-TF32 route: relative L2 against the oracle with
+# random inputs, measured 1.1e-6 .. 2.2e-6 on B300 (the three TF32 products
+# carry about 2^-22 relative rounding each, accumulated over n terms in
+# FP32); bound 1e-5.  Neumann rows element-wise against their largest value
+# (measured up to 1.9e-6), same bound; Dirichlet rows exact copies of u.
 
-def _apply_scale(K, u, g):
-    s = np.abs(K).max() * np.linalg.norm(u)
-    return s * max(np.abs(g.D(a)).max() ** 2 for a in g.axes)
-
+TENSOR_TOL = 1e-5
 
 TENSOR_CASES = [
     ((33, 40, 65), [0, 1, 1, 0, 0, 1]),   # ragged 128-line tiles, n = 40 off the transform sizes
@@ -132,13 +135,15 @@ def test_tensor_route_apply_matches_oracle(n, bc):
     K = W.random_positive_field(g.shape, 32)
     ref = O.apply(u, K, g)
     got = p.apply(_dev(K, torch.float32), _dev(u, torch.float32)).double().cpu().numpy()
-    N = max(n) - 1
-    err = np.linalg.norm(got - ref) / _apply_scale(K, u, g)
-    assert err < 8 * N * N * 1.2e-7, err
-    # boundary rows: Dirichlet rows copy u exactly (in FP32)
+    err = _rel(got, ref)
+    assert err < TENSOR_TOL, err
     own = O.owners(g)
     dmask = np.isin(own, [f for f in range(2 * g.dim) if bc[f] == 0])
     assert np.array_equal(got[dmask], u.astype(np.float32).astype(np.float64)[dmask])
+    nmask = np.isin(own, [f for f in range(2 * g.dim) if bc[f] == 1])
+    if nmask.any():
+        en = np.abs(got[nmask] - ref[nmask]).max() / np.abs(ref[nmask]).max()
+        assert en < TENSOR_TOL, en
 
 
 def test_tensor_route_unsupported_sizes_are_refused():
@@ -152,41 +157,31 @@ def test_tensor_route_unsupported_sizes_are_refused():
 
 
 @pytest.mark.parametrize("nn", [129, 257])
-def test_tensor_route_full_size_against_transform_and_samples(nn):
-    """At the solve sizes: the tensor route against the FP32 transform route
-    over the whole field and against the oracle's per-line evaluation at
-    sampled interior nodes."""
+def test_tensor_route_full_size_against_fp64(nn):
+    """At the solve sizes, over the whole field: the tensor route against
+    the FP64 transform-route apply (itself checked against the oracle at
+    sampled rows in test_gpu_apply), on the two-phase medium at contrast
+    100, for the bench's smooth-plus-noise field (measured 5.4e-6 at 257^3,
+    6.0e-6 at 129^3) and a random field (measured 2.6e-6); and the FP32
+    transform route beside it."""
     import paper_2606_21410_b300 as P
     bc = [0, 0, 1, 1, 1, 1]
     g = O.Grid((nn,) * 3, bc=bc)
     X, Y, Z = g.mesh()
-    u = np.sin(2 * X + Y) * np.cos(3 * Z) + 0.01 * W.random_field(g.shape, 33)
     K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 100.0)
     pt = _plan((nn,) * 3, bc)
     pc = _plan((nn,) * 3, bc)
     for a in range(3):
         pc.set_route32(a, P.ROUTE_TENSOR)
-    Kd, ud = _dev(K, torch.float32), _dev(u, torch.float32)
-    a_tr = pt.apply(Kd, ud).double().cpu().numpy()
-    a_tc = pc.apply(Kd, ud).double().cpu().numpy()
-    scale = _apply_scale(K, u, g)
-    N = nn - 1
-    assert np.linalg.norm(a_tc - a_tr) / scale < 8 * N * N * 1.2e-7
-    rng = W.rng(34)
-    pts = [tuple(int(v) for v in rng.integers(1, nn - 1, size=3)) for _ in range(100)]
-    ref = []
-    for (k, j, i) in pts:
-        v = 0.0
-        idx = {0: i, 1: j, 2: k}
-        for a in g.axes:
-            D = g.D(a)
-            sl = [k, j, i]
-            sl[2 - a] = slice(None)
-            v -= D[idx[a]] @ (K[tuple(sl)] * (D @ u[tuple(sl)]))
-        ref.append(v)
-    ref = np.array(ref)
-    vals = np.array([a_tc[k, j, i] for (k, j, i) in pts])
-    assert np.abs(vals - ref).max() / np.abs(ref).max() < 20 * 8 * N * N * 1.2e-7
+    for u, tol in ((np.sin(2 * X + Y) * np.cos(3 * Z) + 0.01 * W.random_field(g.shape, 33), 3e-5),
+                   (W.random_field(g.shape, 36), 1.5e-5)):
+        a64 = pt.apply(_dev(K), _dev(u)).cpu().numpy()
+        Kd, ud = _dev(K, torch.float32), _dev(u, torch.float32)
+        a_tc = pc.apply(Kd, ud).double().cpu().numpy()
+        a_tr = pt.apply(Kd, ud).double().cpu().numpy()
+        e_tc, e_tr = _rel(a_tc, a64), _rel(a_tr, a64)
+        assert e_tc < tol, (e_tc, e_tr)
+        assert e_tr < 2 * tol, (e_tc, e_tr)
 
 
 def test_tensor_route_mixed_solve_matches_fp64():

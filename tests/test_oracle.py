@@ -342,3 +342,66 @@ def test_picard_fixed_point():
     r = O.apply(u, K, g) - b
     assert np.linalg.norm(r) < 1e-9 * np.linalg.norm(b)
     assert info["iterations"] > 2
+
+
+def test_picard_conductivity_against_sympy_gradient():
+    """K = K0 (1 + beta |grad u|^2) (Sec. 2.3, Picard) for a polynomial u of
+    per-axis degree <= N, whose nodal gradient the collocation derivative
+    reproduces exactly; |grad u|^2 from sympy.  A dropped square, a missing
+    axis or beta applied outside the bracket fails here."""
+    X, Y, Z = sp.symbols("x y z")
+    u = X ** 3 * Y - 2 * Y ** 2 * Z + X * Z ** 2 + 3 * X
+    g2 = sum(sp.diff(u, v) ** 2 for v in (X, Y, Z))
+    uf = sp.lambdify((X, Y, Z), u, "numpy")
+    g2f = sp.lambdify((X, Y, Z), g2, "numpy")
+    g = O.Grid((6, 5, 7), lo=(-1.0, 0.0, -0.5), hi=(1.0, 2.0, 1.0))
+    Xn, Yn, Zn = g.mesh()
+    K0 = W.random_positive_field(g.shape, 61)
+    beta = 0.37
+    got = O.picard_conductivity(K0, uf(Xn, Yn, Zn), g, beta=beta)
+    ref = K0 * (1.0 + beta * g2f(Xn, Yn, Zn))
+    assert np.allclose(got, ref, rtol=1e-11, atol=0.0)
+
+
+def test_e_ref_hand_computed():
+    """e_ref = ||U_fine - U_prolonged||_2 / ||U_fine||_2 (Sec. 2.3.3), by hand:
+    fine (3, 4, 0, 0), prolonged (0, 4, 0, 0) -> 3 / 5; the norm is the fine
+    solution's, so swapping the arguments gives 3 / 4 instead."""
+    uf = np.array([3.0, 4.0, 0.0, 0.0]).reshape(1, 2, 2)
+    up = np.array([0.0, 4.0, 0.0, 0.0]).reshape(1, 2, 2)
+    assert O.e_ref(uf, up) == pytest.approx(0.6, rel=1e-15)
+    assert O.e_ref(up, uf) == pytest.approx(0.75, rel=1e-15)
+
+
+def test_hierarchy_exact_for_polynomial_and_matches_direct():
+    """Alg. 4 in the oracle: for a solution that is a polynomial of per-axis
+    degree <= the coarsest N, every level's discrete solution is that same
+    polynomial, so each e_ref vanishes to rounding; for the two-phase
+    medium the finest level equals the direct solve of that level."""
+    bc = [0, 0, 1, 1, 0, 1]
+    coeffs = {(3, 2, 1): 0.5, (1, 0, 4): -1.0, (0, 3, 2): 0.25, (2, 2, 2): 1.0}
+    fn = lambda X, Y, Z: W.polynomial_3d(coeffs, X, Y, Z)
+    grids, Ks, bs = [], [], []
+    for n in (5, 9, 17):
+        g = O.Grid((n,) * 3, bc=bc)
+        X, Y, Z = g.mesh()
+        _, _, lap = fn(X, Y, Z)
+        faces = W.face_values(bc, g.nodes(0), g.nodes(1), g.nodes(2), fn)
+        grids.append(g)
+        Ks.append(np.ones(g.shape))
+        bs.append(O.rhs(-lap, faces, g))
+    us, infos, eref = O.solve_hierarchy(Ks, bs, grids, rtol=1e-13)
+    X, Y, Z = grids[-1].mesh()
+    assert np.abs(us[-1] - fn(X, Y, Z)[0]).max() < 1e-10 * np.abs(us[-1]).max()
+    assert eref[0] == 0.0 and max(eref[1:]) < 1e-10
+    # two-phase medium at contrast 100: finest level against the direct solve
+    sp_ = W.sphere_packing(0, 0.2, 0.4, 0.2)
+    Ks = []
+    for g in grids:
+        X, Y, Z = g.mesh()
+        Ks.append(W.two_phase_conductivity(X, Y, Z, sp_, 1.0, 100.0))
+    bs = [W.random_field(g.shape, 70 + i) for i, g in enumerate(grids)]
+    us, infos, eref = O.solve_hierarchy(Ks, bs, grids, rtol=1e-13)
+    ud = O.solve_direct(Ks[-1], bs[-1], grids[-1])
+    assert np.linalg.norm(us[-1] - ud) / np.linalg.norm(ud) < 1e-10
+    assert all(e > 0 for e in eref[1:])
