@@ -284,6 +284,14 @@ int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const
                          const double* const* b, double* const* u, const cheb_solve_opts* opts,
                          cheb_solve_info* infos, double* e_ref);
 
+/* Volume-averaged flux of the homogenisation study (Sec. 3.3, effective
+ * conductivity): out = (1/|Omega|) int_Omega K d_axis u, the integral by the
+ * tensor Clenshaw-Curtis rule on the CGL nodes (exact for the interpolant's
+ * polynomial degree), d_axis u by one FP64 line pass.  With q = -K grad u and
+ * the imposed macroscopic gradient G along axis, K_num = -<q_axis>/G =
+ * out / G.  K, u: FP64 device fields; synchronises the plan's stream. */
+int cheb_flux_average(cheb_plan plan, int axis, const double* K, const double* u, double* out);
+
 /* z = M^{-T} y (transposed FDM preconditioner, used by the adjoint solve). */
 int cheb_precond_apply_t(cheb_plan plan, int prec, double kref, const void* y, void* z);
 

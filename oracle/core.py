@@ -27,7 +27,8 @@ __all__ = [
     "grad", "interior_operator", "owners", "apply", "rhs", "assemble",
     "solve_direct", "gmres", "solve", "barycentric_matrix", "prolong", "e_ref",
     "adjoint_apply", "adjoint_solve_direct", "grad_K", "picard_conductivity",
-    "picard_solve", "eliminate_solve", "restrict_inject",
+    "picard_solve", "eliminate_solve", "restrict_inject", "volume_average",
+    "effective_conductivity", "maxwell_estimate",
 ]
 
 DIRICHLET = 0
@@ -530,3 +531,33 @@ def eliminate_solve(K: np.ndarray, f: np.ndarray, faces, grid: Grid) -> np.ndarr
     x[k_idx] = xk
     x[r_idx] = G @ xk + H @ g
     return x.reshape(grid.shape)
+
+
+# ----------------------------------------------------------------------------
+# homogenised response (Sec. 3.3, effective conductivity and the contrast study)
+# ----------------------------------------------------------------------------
+
+def volume_average(v: np.ndarray, grid: Grid) -> float:
+    """<v> = (1/|Omega|) integral of v, by the tensor Clenshaw-Curtis rule on
+    the CGL nodes (exact for polynomials of per-axis degree <= N)."""
+    w = [cc_weights(grid.n[a] - 1, grid.lo[a], grid.hi[a]) if a < grid.dim else np.ones(1)
+         for a in range(3)]
+    vol = 1.0
+    for a in grid.axes:
+        vol *= grid.hi[a] - grid.lo[a]
+    return float(np.einsum("k,j,i,kji->", w[2], w[1], w[0], np.asarray(v, float)) / vol)
+
+
+def effective_conductivity(u: np.ndarray, K: np.ndarray, grid: Grid, G: float, axis: int = 0) -> float:
+    """K_num = -<q_a> / G with the flux q = -K grad u (Sec. 3.3): the volume
+    average of K d_a u over the imposed macroscopic gradient G.  The paper
+    writes q_y and L_y while imposing u = -+g on the x faces; the gradient is
+    taken along the axis that carries the Dirichlet data (here ``axis``), with
+    G = 2 g / L_axis."""
+    return volume_average(np.asarray(K, float) * grad(u, grid, axis), grid) / G
+
+
+def maxwell_estimate(k_m: float, k_i: float, phi: float) -> float:
+    """Maxwell's dilute estimate of the effective conductivity of spheres of
+    conductivity k_i at volume fraction phi in a matrix k_m (Sec. 3.3)."""
+    return k_m * (2 * k_m + k_i + 2 * phi * (k_i - k_m)) / (2 * k_m + k_i - phi * (k_i - k_m))

@@ -259,6 +259,16 @@ class Plan:
             raise ChebError(st, "cheb_adjoint_solve")
         return lam, dJdK, info.as_dict()
 
+    def flux_average(self, K: torch.Tensor, u: torch.Tensor, axis: int = 0) -> float:
+        """(1/|Omega|) int K d_axis u by Clenshaw-Curtis quadrature
+        (``cheb_flux_average``); K_num = flux_average / G."""
+        K = self._field(K, "K", torch.float64)
+        u = self._field(u, "u", torch.float64)
+        out = C.c_double()
+        self._sync_stream()
+        check(lib.cheb_flux_average(self._h, int(axis), _vp(K), _vp(u), C.byref(out)), "cheb_flux_average")
+        return out.value
+
     def precond_apply_t(self, y: torch.Tensor, kref: float, out=None) -> torch.Tensor:
         """z = M^{-T} y (``cheb_precond_apply_t``)."""
         y = self._field(y, "y")

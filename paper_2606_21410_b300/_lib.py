@@ -97,6 +97,7 @@ _SIGS = {
     "cheb_rel_diff": (i32, [vp, vp, vp, f64p]),
     "cheb_solve_hierarchy": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo), f64p]),
+    "cheb_flux_average": (i32, [vp, i32, vp, vp, f64p]),
     "cheb_launch_count": (C.c_longlong, []),
     "cheb_fma_peak": (i32, [i32, f64p, f64p]),
     "cheb_profile_enable": (i32, [i32]),

@@ -687,6 +687,15 @@ static int along(const Fdm& f, int a, const T* Mat, const T* MatT, const T* in, 
   return gemm_any<T>(pz, py * px, pz, Mat, pz, 0, in, py * px, 0, out, py * px, 0, 1, s);
 }
 
+int fdm_clear(const Fdm& f, cudaStream_t s) {
+  const size_t ptot = (size_t)f.mp[0] * f.mp[1] * f.mp[2];
+  for (int i = 0; i < 2; ++i) {
+    if (f.U64[i]) CHEB_CUDA(cudaMemsetAsync(f.U64[i], 0, sizeof(double) * ptot, s));
+    if (f.U32[i]) CHEB_CUDA(cudaMemsetAsync(f.U32[i], 0, sizeof(float) * ptot, s));
+  }
+  return CHEB_OK;
+}
+
 template <typename T>
 static int ensure_compact(Fdm& f, T** U, cudaStream_t s) {
   if (U[0]) return CHEB_OK;

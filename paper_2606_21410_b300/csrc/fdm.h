@@ -41,6 +41,11 @@ struct Fdm {
 
 int fdm_setup(const cheb_plan_s* p, Fdm& f);
 void fdm_free(Fdm& f);
+// Re-zero the compact work arrays (both precisions, where allocated).  Their
+// zero padding is what the contractions read past the interior; a non-finite
+// input leaves 0 * inf = NaN there, so every solve and every direct
+// preconditioner call starts from cleared arrays.
+int fdm_clear(const Fdm& f, cudaStream_t s);
 // x = M^{-1} r with M the constant-kref collocation operator (same boundary rows).
 template <typename T>
 int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaStream_t s);

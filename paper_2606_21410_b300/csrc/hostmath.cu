@@ -12,6 +12,25 @@
 
 namespace cheb {
 
+// Clenshaw-Curtis quadrature: integrate the degree-N interpolant.  With the
+// interpolant's Chebyshev coefficients a_k = (c_k / N) sum_n m_n f_n
+// cos(pi k n / N) (m = 1 at the ends, 2 inside; c = 1/2 at k = 0, N, else 1)
+// and int_{-1}^{1} T_k = 2 / (1 - k^2) for even k (0 for odd k), the weight
+// of node n is w_n = (m_n / N) sum_{even k} c_k cos(pi k n / N) 2 / (1 - k^2).
+std::vector<double> cc_weights(int N, double half_len) {
+  std::vector<double> w(N + 1, 0.0);
+  for (int n = 0; n <= N; ++n) {
+    double s = 0.0;
+    for (int k = 0; k <= N; k += 2) {
+      const double ck = (k == 0 || k == N) ? 0.5 : 1.0;
+      s += ck * std::cos(M_PI * (double)((long long)k * n % (2 * N)) / N) * 2.0 / (1.0 - (double)k * k);
+    }
+    const double mn = (n == 0 || n == N) ? 1.0 : 2.0;
+    w[n] = mn / N * s * half_len;
+  }
+  return w;
+}
+
 std::vector<double> dense_deriv_matrix(int N, double scale) {
   // D e_col for every unit vector, by the transform-route definition:
   // F = DCT-I(e_col), G_k = k c_k scale F_k / N, beta_k = sum_{j>k, j-k odd} G_j,

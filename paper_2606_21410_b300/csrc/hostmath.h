@@ -7,6 +7,8 @@ namespace cheb {
 
 // Row-major (N+1) x (N+1) derivative matrix on an interval with 2/(hi-lo) = scale.
 std::vector<double> dense_deriv_matrix(int N, double scale);
+// Clenshaw-Curtis weights at the N + 1 CGL nodes of [-1, 1] times half_len.
+std::vector<double> cc_weights(int N, double half_len);
 // C (m x n) = A (m x k) B (k x n), row-major.
 std::vector<double> matmul(const std::vector<double>& A, const std::vector<double>& B, int m, int k,
                            int n);

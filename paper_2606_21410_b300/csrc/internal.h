@@ -31,6 +31,7 @@ struct AxisTables {
   float2* tw32 = nullptr;
   double* D64 = nullptr;   // row-major D (n x n)
   float* D32 = nullptr;
+  double* cc64 = nullptr;  // Clenshaw-Curtis weights of the axis (n, physical length)
 };
 
 // Geometry passed by value to kernels.

@@ -312,6 +312,36 @@ int k_sum_log(const ReduceScratch& rs, const double* K, size_t n, double* out_de
   return CHEB_OK;
 }
 
+// out = sum_{i,j,k} wx[i] wy[j] wz[k] a[c] b[c] over the field (c = (k ny + j)
+// nx + i); a unit weight stands in for the weights of unused axes.
+__global__ void __launch_bounds__(kRedThreads)
+wsum3_kernel(const double* __restrict__ a, const double* __restrict__ b, const double* __restrict__ wx,
+             const double* __restrict__ wy, const double* __restrict__ wz, int nx, int ny, size_t n,
+             double* part, unsigned* counter, double* out) {
+  double acc[1] = {0.0};
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t nxy = (size_t)nx * ny;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+    const size_t k = e / nxy;
+    const size_t r = e - k * nxy;
+    const size_t j = r / nx;
+    const size_t i = r - j * nx;
+    double w = wx[i];
+    if (wy) w *= wy[j];
+    if (wz) w *= wz[k];
+    acc[0] += w * a[e] * b[e];
+  }
+  block_reduce_store<double, 1>(acc, 1, false, part, counter, out);
+}
+
+int k_wsum3(const ReduceScratch& rs, const double* a, const double* b, const double* wx, const double* wy,
+            const double* wz, int nx, int ny, size_t n, double* out_dev, cudaStream_t s) {
+  wsum3_kernel<<<red_blocks(n), kRedThreads, 0, s>>>(a, b, wx, wy, wz, nx, ny, n, rs.part, rs.counter,
+                                                     out_dev);
+  CHEB_LAUNCH_CHECK("wsum3_kernel");
+  return CHEB_OK;
+}
+
 template <typename T>
 int k_scale(T* y, const T* x, double sc, size_t n, cudaStream_t s) {
   scale_kernel<T><<<elem_blocks(n), 256, 0, s>>>(y, x, sc, n);

@@ -32,6 +32,9 @@ int k_maxpy_dev(const ReduceScratch& rs, const T* const* src, const double* coef
 template <typename T>
 int k_scale_inv_norm(T* y, const double* norm2_dev, size_t n, cudaStream_t s);
 int k_sum_log(const ReduceScratch& rs, const double* K, size_t n, double* out_dev, cudaStream_t s);
+// out = sum of wx[i] wy[j] wz[k] a b over the field (wy / wz may be null: weight 1)
+int k_wsum3(const ReduceScratch& rs, const double* a, const double* b, const double* wx, const double* wy,
+            const double* wz, int nx, int ny, size_t n, double* out_dev, cudaStream_t s);
 template <typename T>
 int k_scale(T* y, const T* x, double sc, size_t n, cudaStream_t s);
 template <typename To, typename Ti>

@@ -164,12 +164,17 @@ static int build_axis(cheb_plan_s* p, int a) {
     set_error("axis size supported by neither route");
     return CHEB_ERR_UNSUPPORTED;
   }
+  {
+    const std::vector<double> w = cc_weights(t.N, 0.5 * (p->hi[a] - p->lo[a]));
+    CHEB_CUDA(cudaMalloc(&t.cc64, sizeof(double) * w.size()));
+    CHEB_CUDA(cudaMemcpy(t.cc64, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice));
+  }
   return CHEB_OK;
 }
 
 static void free_axis(AxisTables& t) {
-  cudaFree(t.tw64); cudaFree(t.tw32); cudaFree(t.D64); cudaFree(t.D32);
-  t.tw64 = nullptr; t.tw32 = nullptr; t.D64 = nullptr; t.D32 = nullptr;
+  cudaFree(t.tw64); cudaFree(t.tw32); cudaFree(t.D64); cudaFree(t.D32); cudaFree(t.cc64);
+  t.tw64 = nullptr; t.tw32 = nullptr; t.D64 = nullptr; t.D32 = nullptr; t.cc64 = nullptr;
 }
 
 }  // namespace cheb

@@ -603,6 +603,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   lo.use_graph = o.use_graph != 0;
   if (o.precond == CHEB_PRECOND_FDM) {
     if ((st = fdm_setup(p, w.fdm))) return st;
+    if ((st = fdm_clear(w.fdm, s))) return st;
     if (o.kref > 0) lo.kref = o.kref;
     else {
       if ((st = k_sum_log(w.rs, K, n, w.dscal, s))) return st;
@@ -950,6 +951,7 @@ int cheb_precond_apply_t(cheb_plan p, int prec, double kref, const void* y, void
   int st;
   if ((st = ensure_ws(p))) return st;
   if ((st = fdm_setup(p, p->ws->fdm))) return st;
+  if ((st = fdm_clear(p->ws->fdm, p->stream))) return st;
   if (prec == CHEB_FP64) return fdm_apply_t<double>(p, p->ws->fdm, kref, (const double*)y, (double*)z, p->stream);
   if (prec == CHEB_FP32) {
     st = fdm_apply_t<float>(p, p->ws->fdm, kref, (const float*)y, (float*)z, p->stream);
@@ -1057,11 +1059,31 @@ int cheb_picard_batched(int count, const cheb_plan* plans, const double* const* 
   return batched(count, plans, K0, b, u, opts, infos, beta, omega, tol, maxit, picard_iters, true);
 }
 
+int cheb_flux_average(cheb_plan p, int axis, const double* K, const double* u, double* out) {
+  if (!p || !K || !u || !out || axis < 0 || axis >= p->dim) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  Workspace& w = *p->ws;
+  if (!w.adj[0])
+    for (int i = 0; i < 3; ++i) CHEB_CUDA(cudaMalloc(&w.adj[i], sizeof(double) * w.n));
+  cudaStream_t s = p->stream;
+  if ((st = launch_pass<double>(p, axis, kDeriv, nullptr, u, w.adj[0], s))) return st;
+  if ((st = k_wsum3(w.rs, K, w.adj[0], p->ax[0].cc64, p->dim > 1 ? p->ax[1].cc64 : nullptr,
+                    p->dim > 2 ? p->ax[2].cc64 : nullptr, p->n[0], p->n[1], w.n, w.dscal, s)))
+    return st;
+  if ((st = sync_read(w, 1, s))) return st;
+  double vol = 1.0;
+  for (int a = 0; a < p->dim; ++a) vol *= p->hi[a] - p->lo[a];
+  *out = w.hscal[0] / vol;
+  return CHEB_OK;
+}
+
 int cheb_precond_apply(cheb_plan p, int prec, double kref, const void* r, void* z) {
   if (!p || !r || !z || !(kref > 0)) { set_error("bad argument"); return CHEB_ERR_ARG; }
   int st;
   if ((st = ensure_ws(p))) return st;
   if ((st = fdm_setup(p, p->ws->fdm))) return st;
+  if ((st = fdm_clear(p->ws->fdm, p->stream))) return st;
   if (prec == CHEB_FP64) return fdm_apply<double>(p, p->ws->fdm, kref, (const double*)r, (double*)z, p->stream);
   if (prec == CHEB_FP32) {
     st = fdm_apply<float>(p, p->ws->fdm, kref, (const float*)r, (float*)z, p->stream);

@@ -405,3 +405,64 @@ def test_hierarchy_exact_for_polynomial_and_matches_direct():
     ud = O.solve_direct(Ks[-1], bs[-1], grids[-1])
     assert np.linalg.norm(us[-1] - ud) / np.linalg.norm(ud) < 1e-10
     assert all(e > 0 for e in eref[1:])
+
+
+# ---------------------------------------------------------------- homogenisation
+
+def test_volume_average_exact_for_polynomials():
+    """Tensor Clenshaw-Curtis average of a polynomial of per-axis degree <= N
+    equals its exact mean over the box (sympy)."""
+    X, Y, Z = sp.symbols("x y z")
+    p = X ** 3 * Y ** 2 - 2 * Z ** 4 + X * Y * Z + 1
+    lo, hi = (0.0, -1.0, 0.5), (1.0, 2.0, 1.5)
+    exact = sp.integrate(p, (X, lo[0], hi[0]), (Y, lo[1], hi[1]), (Z, lo[2], hi[2]))
+    exact = float(exact) / ((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]))
+    g = O.Grid((7, 6, 9), lo, hi)
+    Xn, Yn, Zn = g.mesh()
+    v = sp.lambdify((X, Y, Z), p, "numpy")(Xn, Yn, Zn)
+    assert abs(O.volume_average(v, g) - exact) < 1e-13 * max(1.0, abs(exact))
+
+
+def _unit_cell(N, K_fn, g_val=1.0):
+    """Sec. 3.3 unit cell (0,1)^3: u = -g on x = 0, +g on x = 1, zero normal
+    derivative elsewhere, f = 0."""
+    bc = [0, 0, 1, 1, 1, 1]
+    g = O.Grid((N + 1,) * 3, (0, 0, 0), (1, 1, 1), bc)
+    X, Y, Z = g.mesh()
+    K = K_fn(X, Y, Z)
+    faces = W.face_values(bc, g.nodes(0), g.nodes(1), g.nodes(2),
+                          lambda X, Y, Z: (np.where(X > 0.5, g_val, -g_val) * np.ones_like(X),
+                                           (0 * X, 0 * X, 0 * X), 0 * X))
+    return g, K, O.rhs(np.zeros(g.shape), faces, g)
+
+
+def test_effective_conductivity_parallel_and_series_laminates():
+    """K_num = <K d_x u> / G (Sec. 3.3): a laminate K(y, z) carries the exact
+    linear solution, so K_num is the volume average of K (parallel bound); a
+    smooth series profile K(x) = 1 + x/2 gives the harmonic mean
+    1 / int_0^1 dx / K = 1 / (2 ln 1.5)."""
+    g, K, b = _unit_cell(10, lambda X, Y, Z: 1.0 + 0.5 * np.cos(3 * Y) * (1 + Z ** 2))
+    u = O.solve_direct(K, b, g)
+    assert abs(O.effective_conductivity(u, K, g, G=2.0) - O.volume_average(K, g)) < 1e-11
+    g, K, b = _unit_cell(12, lambda X, Y, Z: 1.0 + 0.5 * X + 0 * Y)
+    u = O.solve_direct(K, b, g)
+    assert abs(O.effective_conductivity(u, K, g, G=2.0) - 1.0 / (2.0 * math.log(1.5))) < 1e-10
+
+
+def test_maxwell_estimate_closed_form():
+    """Maxwell's estimate (Sec. 3.3): k_m at phi = 0 or k_i = k_m, and by hand
+    for k_m = 1, k_i = 10, phi = 0.0335: (12 + 0.603) / (12 - 0.3015)."""
+    assert O.maxwell_estimate(2.0, 7.0, 0.0) == pytest.approx(2.0, rel=1e-15)
+    assert O.maxwell_estimate(3.0, 3.0, 0.4) == pytest.approx(3.0, rel=1e-15)
+    assert O.maxwell_estimate(1.0, 10.0, 0.0335) == pytest.approx(12.603 / 11.6985, rel=1e-12)
+
+
+def test_centred_sphere_matches_maxwell():
+    """The paper's unit-cell check (Sec. 3.3): one centred sphere of radius
+    0.2 (phi = 0.0335) at contrast 10 reproduces Maxwell's estimate to below
+    1e-3 (measured 1.7e-4 at N = 32)."""
+    g, K, b = _unit_cell(32, lambda X, Y, Z: W.two_phase_conductivity(X, Y, Z, W.single_sphere(), 1.0, 10.0))
+    u, info = O.solve_preconditioned(K, b, g, rtol=1e-12)
+    kn = O.effective_conductivity(u, K, g, G=2.0)
+    km = O.maxwell_estimate(1.0, 10.0, 4.0 / 3.0 * math.pi * 0.2 ** 3)
+    assert abs(kn - km) / km < 1e-3, (kn, km)

@@ -209,6 +209,19 @@ def sphere_packing(seed: int = 0, rmin: float = 0.08, rmax: float = 0.15,
     return spheres
 
 
+def single_sphere(center=(0.5, 0.5, 0.5), radius: float = 0.2) -> np.ndarray:
+    """One sphere (the centred inclusion of the unit-cell study, Sec. 3.3)."""
+    return np.array([[center[0], center[1], center[2], radius]], dtype=float)
+
+
+def corner_spheres(radius: float = 0.2, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """Spheres centred on the eight corners of the box [lo, hi]^3: inside the
+    box they form the corner-inclusion arrangement of Sec. 3.3, with the same
+    inclusion volume as one sphere of that radius."""
+    c = [lo, hi]
+    return np.array([[x, y, z, radius] for x in c for y in c for z in c], dtype=float)
+
+
 def two_phase_conductivity(X, Y, Z, spheres: np.ndarray, k_matrix: float, k_incl: float) -> np.ndarray:
     """k = k_incl at points inside (inclusive) any sphere, else k_matrix.
 
