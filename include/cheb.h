@@ -188,6 +188,10 @@ typedef struct cheb_solve_info {
   double seconds;          /* wall time of the call */
   double kref;             /* FDM conductivity used */
   int graph_captures;      /* Arnoldi-cycle graphs captured (use_graph) */
+  int host_syncs;          /* host synchronisations of the LGMRES cycles
+                              (residual norm, Arnoldi checkpoints, update norm) */
+  int discarded_steps;     /* Arnoldi steps run past the converged one (their
+                              work is discarded; see cheb_solve) */
 } cheb_solve_info;
 
 /* Defaults: MIXED, rtol 1e-12, restart 30, augment 3, maxiter 2000,
@@ -202,7 +206,13 @@ void cheb_solve_opts_default(cheb_solve_opts* opts);
  * CHEB_ERR_NOT_CONVERGED (u holds the last iterate) or an error.  The plan
  * allocates its Krylov workspace at the first solve (about
  * (restart + 2 augment + 5) fields of the working precision) and keeps it.
- * Synchronises the plan's stream once per Arnoldi step. */
+ * The Hessenberg matrix and its Givens rotations are updated on the device
+ * (FP64); the host reads them at checkpoints: at the end of every LGMRES
+ * cycle, and earlier only when the residual estimates, extrapolated at
+ * their observed reduction rate, reach the tolerance.  A cycle far from the
+ * tolerance therefore costs one synchronisation; a few Arnoldi steps past
+ * the converged one may run and are discarded.  (With use_graph the cycles
+ * run as captured graphs, one synchronisation each.) */
 int cheb_solve(cheb_plan plan, const double* K, const double* b, double* u,
                const cheb_solve_opts* opts, cheb_solve_info* info);
 

@@ -9,9 +9,10 @@ Index and face conventions
   x_j = cos(pi j / N) (Sec. 2.2), mapped affinely to [lo, hi] (Sec. 2.2,
   affine mapping), so node 0 is the ``hi`` end and node N the ``lo`` end.
 * Face id f = 2a + side, side 0 = ``lo``, side 1 = ``hi`` (x-, x+, y-, y+, z-, z+).
-  Neumann data is the outward normal derivative n . grad u.
+  Neumann data is the outward normal derivative n . grad u; flux data (the
+  heat-flux condition of Sec. 3.4) is -K n . grad u.
 * Every boundary node has one owner face: a Dirichlet face beats a Neumann
-  face, and among faces of one type the lowest axis wins.  (The paper only
+  or flux face, and among the others the lowest axis wins.  (The paper only
   says the equations at boundary nodes are replaced by the boundary
   conditions, Sec. 2 "Extension to the three-dimensional setting"; it does
   not say which face owns an edge or corner node.)
@@ -23,16 +24,18 @@ import math
 import numpy as np
 
 __all__ = [
-    "DIRICHLET", "NEUMANN", "Grid", "cgl_nodes", "diff_matrix", "cc_weights",
+    "DIRICHLET", "NEUMANN", "FLUX", "Grid", "cgl_nodes", "diff_matrix", "cc_weights",
     "grad", "interior_operator", "owners", "apply", "rhs", "assemble",
     "solve_direct", "gmres", "solve", "barycentric_matrix", "prolong", "e_ref",
     "adjoint_apply", "adjoint_solve_direct", "grad_K", "picard_conductivity",
     "picard_solve", "eliminate_solve", "restrict_inject", "volume_average",
-    "effective_conductivity", "maxwell_estimate",
+    "effective_conductivity", "maxwell_estimate", "reciprocal_law", "jacobian_apply",
+    "newton_residual", "newton_solve",
 ]
 
 DIRICHLET = 0
 NEUMANN = 1
+FLUX = 2   # flux data: -K (n . grad u) = g, the heat-flux condition of Sec. 3.4
 
 
 # ----------------------------------------------------------------------------
@@ -155,16 +158,16 @@ def interior_operator(u: np.ndarray, K: np.ndarray, grid: Grid) -> np.ndarray:
 def owners(grid: Grid) -> np.ndarray:
     """Owner face id of every node (-1 for interior nodes).
 
-    Dirichlet faces are claimed before Neumann faces; within one type, axes in
-    increasing order.  Node index 0 lies on the ``hi`` face (side 1), index
+    Dirichlet faces are claimed before Neumann and flux faces; within each
+    rank, axes in increasing order.  Node index 0 lies on the ``hi`` face (side 1), index
     n - 1 on the ``lo`` face (side 0).
     """
     own = -np.ones(grid.shape, dtype=np.int64)
-    for kind in (DIRICHLET, NEUMANN):
+    for rank in (0, 1):   # Dirichlet faces first, then Neumann and flux faces
         for a in grid.axes:
             for side in (0, 1):
                 f = 2 * a + side
-                if grid.bc[f] != kind:
+                if (grid.bc[f] == DIRICHLET) != (rank == 0):
                     continue
                 sl = [slice(None)] * 3
                 sl[2 - a] = grid.n[a] - 1 if side == 0 else 0
@@ -177,7 +180,8 @@ def apply(u: np.ndarray, K: np.ndarray, grid: Grid) -> np.ndarray:
     """A u: collocation rows L(u) at interior nodes (Eq. (eq:residualN)); at a
     boundary node the row is replaced by its owner face's condition
     (Eq. (eq:boundaryN)): Dirichlet u_p, Neumann s (d_a u)_p with s = +1 on the
-    ``hi`` face and -1 on the ``lo`` face (outward normal)."""
+    ``hi`` face and -1 on the ``lo`` face (outward normal), flux -K_p s (d_a u)_p
+    (Sec. 3.4, q_N = -k grad T . n)."""
     out = interior_operator(u, K, grid)
     own = owners(grid)
     out[own >= 0] = 0.0
@@ -190,7 +194,8 @@ def apply(u: np.ndarray, K: np.ndarray, grid: Grid) -> np.ndarray:
         else:
             a, side = divmod(f, 2)
             s = 1.0 if side == 1 else -1.0
-            out[m] = s * grad(u, grid, a)[m]
+            row = s * grad(u, grid, a)[m]
+            out[m] = -np.asarray(K, float)[m] * row if grid.bc[f] == FLUX else row
     return out
 
 
@@ -240,6 +245,8 @@ def assemble(K: np.ndarray, grid: Grid) -> np.ndarray:
             a, side = divmod(f, 2)
             s = 1.0 if side == 1 else -1.0
             A[rows, :] = s * Dh[a][rows, :]
+            if grid.bc[f] == FLUX:
+                A[rows, :] *= -np.asarray(K, float).ravel()[rows][:, None]
     return A
 
 
@@ -406,7 +413,8 @@ def adjoint_apply(lam: np.ndarray, K: np.ndarray, grid: Grid) -> np.ndarray:
     """A^T lam for A = P_int L + R_bc:
     -sum_a D_a^T (K * D_a^T (P_int lam)) + P_dir lam + sum_a D_a^T (S_a lam),
     with S_a = +-1 on Neumann rows owned by an axis-a face (sign of the
-    outward normal), P_int / P_dir the interior / Dirichlet-row masks."""
+    outward normal; -+K_p on flux rows), P_int / P_dir the interior /
+    Dirichlet-row masks."""
     own = owners(grid)
     lam = np.asarray(lam, float)
     lam_int = np.where(own < 0, lam, 0.0)
@@ -422,7 +430,8 @@ def adjoint_apply(lam: np.ndarray, K: np.ndarray, grid: Grid) -> np.ndarray:
         else:
             a, side = divmod(f, 2)
             s = 1.0 if side == 1 else -1.0
-            out += _grad_T(np.where(m, s * lam, 0.0), grid, a)
+            w = -np.asarray(K, float) * lam if grid.bc[f] == FLUX else lam
+            out += _grad_T(np.where(m, s * w, 0.0), grid, a)
     return out
 
 
@@ -438,12 +447,21 @@ def adjoint_solve_direct(K: np.ndarray, dJdu: np.ndarray, grid: Grid) -> np.ndar
 def grad_K(u: np.ndarray, lam: np.ndarray, grid: Grid) -> np.ndarray:
     """dJ/dK for J(u(K)) with A(K) u = b and A^T lam = dJ/du (no explicit K in J):
     dJ/dK_p = -lam^T (dA/dK_p) u = sum_a (D_a^T P_int lam)_p (D_a u)_p, because
-    A depends on K only through the interior rows -sum_a D_a diag(K) D_a."""
+    A depends on K through the interior rows -sum_a D_a diag(K) D_a, plus
+    s lam_p (D_a u)_p on flux rows (row -K_p s (D_a u)_p)."""
     own = owners(grid)
     lam_int = np.where(own < 0, np.asarray(lam, float), 0.0)
     g = np.zeros(grid.shape)
     for a in grid.axes:
         g += _grad_T(lam_int, grid, a) * grad(u, grid, a)
+    # flux rows -K_p s (d_a u)_p depend on K_p too: -lam_p * (-s (d_a u)_p)
+    for f in range(2 * grid.dim):
+        if grid.bc[f] != FLUX:
+            continue
+        m = own == f
+        a, side = divmod(f, 2)
+        s = 1.0 if side == 1 else -1.0
+        g[m] += s * np.asarray(lam, float)[m] * grad(u, grid, a)[m]
     return g
 
 
@@ -519,6 +537,8 @@ def eliminate_solve(K: np.ndarray, f: np.ndarray, faces, grid: Grid) -> np.ndarr
         else:
             a, side = divmod(int(fce), 2)
             B[row] = (1.0 if side == 1 else -1.0) * Dh[a][p]
+            if grid.bc[fce] == FLUX:
+                B[row] *= -float(np.asarray(K, float).ravel()[p])
         g[row] = gfull[p]
     Bk, Br = B[:, k_idx], B[:, r_idx]
     Br_inv = np.linalg.inv(Br)
@@ -561,3 +581,90 @@ def maxwell_estimate(k_m: float, k_i: float, phi: float) -> float:
     """Maxwell's dilute estimate of the effective conductivity of spheres of
     conductivity k_i at volume fraction phi in a matrix k_m (Sec. 3.3)."""
     return k_m * (2 * k_m + k_i + 2 * phi * (k_i - k_m)) / (2 * k_m + k_i - phi * (k_i - k_m))
+
+
+# ----------------------------------------------------------------------------
+# Newton's method for a temperature-dependent conductivity (Sec. 2.3 Newton,
+# Sec. 3.4): k(T) = K0 / (1 + alpha T)
+# ----------------------------------------------------------------------------
+
+def reciprocal_law(K0, T, alpha: float):
+    """k(T) = K0 / (1 + alpha T) and dk/dT = -alpha K0 / (1 + alpha T)^2
+    (the normalised reciprocal law of Sec. 3.4, with a nodal prefactor K0)."""
+    d = 1.0 + alpha * np.asarray(T, float)
+    k = np.asarray(K0, float) / d
+    return k, -alpha * k / d
+
+
+def newton_residual(T, K0, alpha: float, b, grid: Grid) -> np.ndarray:
+    """R(T) = A(k(T)) T - b: the collocation rows with the conductivity
+    evaluated at T, boundary rows included (flux rows carry k(T_p))."""
+    k, _ = reciprocal_law(K0, T, alpha)
+    return apply(np.asarray(T, float), k, grid) - np.asarray(b, float)
+
+
+def jacobian_apply(dT, T, K0, alpha: float, grid: Grid) -> np.ndarray:
+    """J(T) dT, the derivative of R at T along dT (Sec. 3.4, Jacobian action
+    div(-k grad dT - k' dT grad T)): A(k(T)) dT plus, with h = k'(T) dT,
+    -sum_a D_a (h D_a T) on interior rows and -s h_p (D_a T)_p on flux rows."""
+    T = np.asarray(T, float)
+    dT = np.asarray(dT, float)
+    k, dk = reciprocal_law(K0, T, alpha)
+    h = dk * dT
+    out = apply(dT, k, grid)
+    own = owners(grid)
+    extra = np.zeros(grid.shape)
+    for a in grid.axes:
+        extra -= grad(h * grad(T, grid, a), grid, a)
+    out[own < 0] += extra[own < 0]
+    for f in range(2 * grid.dim):
+        if grid.bc[f] != FLUX:
+            continue
+        m = own == f
+        a, side = divmod(f, 2)
+        s = 1.0 if side == 1 else -1.0
+        out[m] += -s * h[m] * grad(T, grid, a)[m]
+    return out
+
+
+def _jacobian_dense(T, K0, alpha: float, grid: Grid) -> np.ndarray:
+    """J(T) assembled column by column from jacobian_apply (tiny grids)."""
+    n = grid.size
+    J = np.zeros((n, n))
+    e = np.zeros(n)
+    for c in range(n):
+        e[c] = 1.0
+        J[:, c] = jacobian_apply(e.reshape(grid.shape), T, K0, alpha, grid).ravel()
+        e[c] = 0.0
+    return J
+
+
+def newton_solve(K0, alpha: float, b, grid: Grid, T0=None, tol: float = 1e-13, maxit: int = 30,
+                 lin_rtol: float = 1e-13):
+    """Newton's method (Sec. 2.3 and Sec. 3.4): J(T^m) dT = -R(T^m),
+    T^{m+1} = T^m + dT, until ||dT||_inf <= tol max(||T||_inf, 1).  Each
+    linear solve is direct on tiny grids, else GMRES on the Jacobian action
+    preconditioned by the constant-coefficient inverse at the geometric mean
+    of k(T^m).  Returns (T, info) with the iteration count and the history of
+    ||dT||_inf."""
+    T = np.zeros(grid.shape) if T0 is None else np.array(T0, float)
+    hist = []
+    it = 0
+    for it in range(1, maxit + 1):
+        R = newton_residual(T, K0, alpha, b, grid)
+        if grid.size <= 4096:
+            J = _jacobian_dense(T, K0, alpha, grid)
+            s = 1.0 / np.abs(J).max(axis=1)
+            dT = np.linalg.solve(J * s[:, None], -R.ravel() * s).reshape(grid.shape)
+        else:
+            from .precond import FDMPreconditioner, geometric_mean
+            k, _ = reciprocal_law(K0, T, alpha)
+            M = FDMPreconditioner(grid, geometric_mean(k))
+            dT, _ = gmres(lambda v: M(jacobian_apply(v, T, K0, alpha, grid)), M(-R),
+                          rtol=lin_rtol, restart=50)
+        T = T + dT
+        step = float(np.abs(dT).max())
+        hist.append(step)
+        if step <= tol * max(float(np.abs(T).max()), 1.0):
+            break
+    return T, {"iterations": it, "history": hist}

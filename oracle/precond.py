@@ -8,7 +8,8 @@ M^{-1} b, with M the collocation operator for a constant conductivity
 ``kref`` and the same boundary rows.  The oracle's answer is still checked
 only through its plain dense ``apply``; M merely accelerates convergence.
 
-M^{-1} r, written with dense numpy operations:
+M^{-1} r, written with dense numpy operations (a flux row -kref s (d_a u) = r
+is the Neumann row with datum -r / kref, so flux rows are rescaled first):
 1. per axis, the two end rows of every line (Dirichlet: u = g, Neumann:
    +-(D u) = g) give the end values from the line interior,
    u_b = G u_int + Binv g (the boundary elimination of Sec. 2.3.1 in 1-D);
@@ -24,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 
-from .core import DIRICHLET, Grid, apply, owners
+from .core import DIRICHLET, FLUX, Grid, apply, owners
 
 
 def _axis_tables(grid: Grid, a: int):
@@ -107,6 +108,10 @@ class FDMPreconditioner:
     def __call__(self, r: np.ndarray) -> np.ndarray:
         g, kref = self.g, self.kref
         r = np.asarray(r, float)
+        # a flux row -kref s (d_a u) = r_p is the Neumann row s (d_a u) = -r_p / kref
+        flux = np.isin(self.own, [f for f in range(2 * g.dim) if g.bc[f] == FLUX])
+        if flux.any():
+            r = np.where(flux, -r / kref, r)
         x = np.zeros(g.shape)
         I = self._interior()
         rhs = r[I].copy()

@@ -58,6 +58,8 @@ class SolveInfo(C.Structure):
         ("seconds", C.c_double),
         ("kref", C.c_double),
         ("graph_captures", i32),
+        ("host_syncs", i32),
+        ("discarded_steps", i32),
     ]
 
     def as_dict(self):

@@ -161,6 +161,8 @@ struct LgOpts {
 
 struct LgStats {
   int iterations = 0, cycles = 0, applies = 0, captures = 0;
+  int syncs = 0;      // host synchronisations of the Arnoldi cycles
+  int overshoot = 0;  // Arnoldi steps run past the converged one (discarded)
   double resid = 0.0;  // last true preconditioned residual norm
   bool converged = false;
 };
@@ -249,6 +251,16 @@ __global__ void copy_slot_kernel(T* __restrict__ w, const T* __restrict__ BZ, co
     w[c] = src[c];
 }
 
+static int ensure_hess(Workspace& w) {
+  if (w.dhess) return CHEB_OK;
+  HessLayout Lmax{kMaxVecs};
+  CHEB_CUDA(cudaMalloc(&w.dhess, sizeof(double) * Lmax.total()));
+  CHEB_CUDA(cudaMallocHost(&w.hhess, sizeof(double) * Lmax.total()));
+  CHEB_CUDA(cudaMalloc(&w.dorder, sizeof(int) * kMaxVecs));
+  CHEB_CUDA(cudaMallocHost(&w.horder, sizeof(int) * kMaxVecs));
+  return CHEB_OK;
+}
+
 // One Arnoldi cycle as a CUDA graph: captured once per cycle shape and
 // operator (K, kref, options), replayed afterwards.  The host reads the
 // Hessenberg state once at the end and keeps the steps up to the first one
@@ -263,13 +275,8 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
   KrylovBufs<T>& B = bufs<T>(w);
   const int kk = o.k;
   HessLayout L{nbasis};
-  if (!w.dhess) {
-    HessLayout Lmax{kMaxVecs};
-    CHEB_CUDA(cudaMalloc(&w.dhess, sizeof(double) * Lmax.total()));
-    CHEB_CUDA(cudaMallocHost(&w.hhess, sizeof(double) * Lmax.total()));
-    CHEB_CUDA(cudaMalloc(&w.dorder, sizeof(int) * kMaxVecs));
-    CHEB_CUDA(cudaMallocHost(&w.horder, sizeof(int) * kMaxVecs));
-  }
+  int st0;
+  if ((st0 = ensure_hess(w))) return st0;
   // per-cycle inputs: g = (beta, 0, ...), augmentation order (oldest first)
   std::fill(w.hhess, w.hhess + L.total(), 0.0);
   w.hhess[L.g()] = beta;
@@ -345,6 +352,8 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
     if (!std::isfinite(r) || r <= o.tol_abs || stt.iterations + j + 1 >= o.maxiter) { steps = j + 1; break; }
   }
   if (!std::isfinite(hh[L.res() + steps - 1])) { set_error("non-finite Arnoldi residual"); return CHEB_ERR_NONFINITE; }
+  stt.syncs++;
+  stt.overshoot += steps_max - steps;
   stt.iterations += steps;
   stt.applies += std::min(steps, m_eff);
   for (size_t i = 0; i < (size_t)(nbasis + 1) * nbasis; ++i) {
@@ -385,6 +394,7 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
   double* hv = w.hscal;
   bool zero = x_is_zero;
   bool last_full = false;  // previous cycle ran all its steps (graph replay pays off)
+  double lg_rate = 0.0;     // observed residual reduction per Arnoldi step
   stt = LgStats();
   while (true) {
     // ---- residual r = c - B x into V[0]
@@ -404,6 +414,7 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
     if ((st = k_mdot<T>(w.rs, &v0, 0, Vp(0), n, true, dv, s))) return st;
     prof_end(Cat<T>::orth, s);
     if ((st = sync_read(w, 1, s))) return st;
+    stt.syncs++;
     const double beta = std::sqrt(hv[0]);
     stt.resid = beta;
     if (!std::isfinite(beta)) { set_error("non-finite residual"); return CHEB_ERR_NONFINITE; }
@@ -425,58 +436,91 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
                                stt, steps, s)))
         return st;
     }
-    for (int j = 0; j < (graph ? 0 : steps_max); ++j) {
-      T* wv = Vp(j + 1);
-      if (j < m_eff) {
-        if ((st = op_B<T>(p, w, o, K, Vp(j), wv, B.tmp, s))) return st;
-        stt.applies++;
-      } else {
-        const int a = (next_slot - naug + (j - m_eff) + 4 * kk) % kk;  // oldest first
-        prof_begin(Cat<T>::orth, s);
-        if ((st = k_scale<T>(wv, BZp(a), 1.0, n, s))) return st;
-        prof_end(Cat<T>::orth, s);
-      }
-      const T* src[kMaxVecs];
-      for (int i = 0; i <= j; ++i) src[i] = Vp(i);
-      // classical Gram-Schmidt (twice if requested): h = V^T w, w -= V h, |w|^2;
-      // the axpy reads h on the device, one synchronisation per pass
-      for (int pass = 0; pass < (o.reorth ? 2 : 1); ++pass) {
-        prof_begin(Cat<T>::orth, s);
-        if ((st = k_mdot<T>(w.rs, src, j + 1, wv, n, false, dv, s))) return st;
-        if ((st = k_maxpy_dev<T>(w.rs, src, dv, -1.0, j + 1, 1.0, wv, n, dv + kMaxVecs + 1, s))) return st;
-        prof_end(Cat<T>::orth, s);
-        if ((st = sync_read(w, kMaxVecs + 2, s))) return st;
-        for (int i = 0; i <= j; ++i) {
-          if (pass == 0) H[(size_t)i * nbasis + j] = hv[i];
-          else H[(size_t)i * nbasis + j] += hv[i];
+    if (!graph) {
+      // Arnoldi steps with the Hessenberg column and its Givens rotation on
+      // the device (hcol_kernel, givens_kernel): nothing returns to the host
+      // per step.  The host reads the device state at checkpoints only: the
+      // end of the cycle, and earlier when the residual estimates predict
+      // convergence (from the reduction rate seen so far), so a cycle far
+      // from the tolerance costs one synchronisation.  Steps run past the
+      // first converged one are discarded (counted in stt.overshoot).
+      if ((st = ensure_hess(w))) return st;
+      HessLayout L{nbasis};
+      const int budget = std::min(steps_max, std::max(1, o.maxiter - stt.iterations));
+      std::fill(w.hhess, w.hhess + L.total(), 0.0);
+      w.hhess[L.g()] = beta;
+      CHEB_CUDA(cudaMemcpyAsync(w.dhess, w.hhess, sizeof(double) * L.total(), cudaMemcpyHostToDevice, s));
+      // Arnoldi steps to go until r <= tol_abs at the observed rate (8 without one)
+      auto predict = [&](double r) -> int {
+        if (!(lg_rate > 0.0 && lg_rate < 1.0) || !(r > o.tol_abs)) return 8;
+        const double k = std::ceil(std::log(o.tol_abs / r) / std::log(lg_rate));
+        return (int)std::max(1.0, std::min(k, 1e6));
+      };
+      int next_check = std::min(budget, predict(beta));
+      int checked = 0;  // steps already inspected on the host
+      steps = -1;
+      for (int j = 0; j < budget; ++j) {
+        T* wv = Vp(j + 1);
+        if (j < m_eff) {
+          if ((st = op_B<T>(p, w, o, K, Vp(j), wv, B.tmp, s))) return st;
+          stt.applies++;
+        } else {
+          const int a = (next_slot - naug + (j - m_eff) + 4 * kk) % kk;  // oldest first
+          prof_begin(Cat<T>::orth, s);
+          if ((st = k_scale<T>(wv, BZp(a), 1.0, n, s))) return st;
+          prof_end(Cat<T>::orth, s);
         }
-      }
-      const double hn = std::sqrt(std::max(0.0, hv[kMaxVecs + 1]));
-      if (!std::isfinite(hn)) { set_error("non-finite Arnoldi norm"); return CHEB_ERR_NONFINITE; }
-      H[(size_t)(j + 1) * nbasis + j] = hn;
-      if (hn > 0) {
+        const T* src[kMaxVecs];
+        for (int i = 0; i <= j; ++i) src[i] = Vp(i);
+        // classical Gram-Schmidt (twice if requested): h = V^T w, w -= V h, |w|^2
         prof_begin(Cat<T>::orth, s);
+        for (int pass = 0; pass < (o.reorth ? 2 : 1); ++pass) {
+          if ((st = k_mdot<T>(w.rs, src, j + 1, wv, n, false, dv, s))) return st;
+          if ((st = k_maxpy_dev<T>(w.rs, src, dv, -1.0, j + 1, 1.0, wv, n, dv + kMaxVecs + 1, s))) return st;
+          hcol_kernel<<<1, 64, 0, s>>>(w.dhess, L, j, pass, dv);
+          CHEB_LAUNCH_CHECK("hcol_kernel");
+        }
         if ((st = k_scale_inv_norm<T>(wv, dv + kMaxVecs + 1, n, s))) return st;
+        givens_kernel<<<1, 32, 0, s>>>(w.dhess, L, j, dv + kMaxVecs + 1);
+        CHEB_LAUNCH_CHECK("givens_kernel");
         prof_end(Cat<T>::orth, s);
+        if (j + 1 < next_check && j + 1 < budget) continue;
+        // ---- checkpoint: read the Hessenberg state
+        CHEB_CUDA(cudaMemcpyAsync(w.hhess, w.dhess, sizeof(double) * L.total(), cudaMemcpyDeviceToHost, s));
+        CHEB_CUDA(cudaStreamSynchronize(s));
+        stt.syncs++;
+        const double* hh = w.hhess;
+        for (int i = checked; i <= j; ++i) {
+          const double r = hh[L.res() + i];
+          if (!std::isfinite(r)) { set_error("non-finite Arnoldi residual"); return CHEB_ERR_NONFINITE; }
+          if (r <= o.tol_abs) { steps = i + 1; break; }
+        }
+        if (steps < 0 && j + 1 >= 2) {
+          // reduction rate per step over the steps of this cycle so far
+          const double r1 = hh[L.res() + j], r0 = j >= 4 ? hh[L.res() + j - 4] : beta;
+          const int span = j >= 4 ? 4 : j + 1;
+          if (r1 > 0.0 && r0 > 0.0 && r1 < r0) lg_rate = std::pow(r1 / r0, 1.0 / span);
+        }
+        checked = j + 1;
+        if (steps >= 0) { stt.overshoot += j + 1 - steps; break; }
+        if (j + 1 >= budget) { steps = j + 1; break; }
+        next_check = std::min(budget, j + 1 + predict(hh[L.res() + j]));
       }
-      // Givens: copy the column, apply previous rotations, make a new one
-      for (int i = 0; i <= j + 1; ++i) Hr[(size_t)i * nbasis + j] = H[(size_t)i * nbasis + j];
-      for (int i = 0; i < j; ++i) {
-        const double a = Hr[(size_t)i * nbasis + j], b = Hr[(size_t)(i + 1) * nbasis + j];
-        Hr[(size_t)i * nbasis + j] = cs[i] * a + sn[i] * b;
-        Hr[(size_t)(i + 1) * nbasis + j] = -sn[i] * a + cs[i] * b;
+      const double* hh = w.hhess;
+      for (size_t i = 0; i < (size_t)(nbasis + 1) * nbasis; ++i) {
+        H[i] = hh[L.H() + i];
+        Hr[i] = hh[L.R() + i];
       }
-      const double a = Hr[(size_t)j * nbasis + j], b = Hr[(size_t)(j + 1) * nbasis + j];
-      const double den = std::hypot(a, b);
-      cs[j] = den > 0 ? a / den : 1.0;
-      sn[j] = den > 0 ? b / den : 0.0;
-      Hr[(size_t)j * nbasis + j] = den;
-      Hr[(size_t)(j + 1) * nbasis + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      steps = j + 1;
-      stt.iterations++;
-      if (std::fabs(g[j + 1]) <= o.tol_abs || hn == 0.0 || stt.iterations >= o.maxiter) break;
+      // the rotated right-hand side after `steps` rotations (later steps of
+      // the cycle only touched entries beyond it)
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      for (int j = 0; j < steps; ++j) {
+        const double c = hh[L.cs() + j], sn = hh[L.sn() + j];
+        g[j + 1] = -sn * g[j];
+        g[j] = c * g[j];
+      }
+      stt.iterations += steps;
     }
     last_full = steps == steps_max && std::fabs(g[steps]) > o.tol_abs;
     // ---- least squares: R y = g
@@ -507,6 +551,7 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
       prof_end(kProfOther, s);
       if (kk > 0) {
         if ((st = sync_read(w, kMaxVecs + 2, s))) return st;
+        stt.syncs++;
         const double dxn = std::sqrt(std::max(0.0, hv[kMaxVecs + 1]));
         if (dxn > 0) {
           // store z = dx/|dx| and B z = V Hbar y / |dx| (linearity: B W = V Hbar)
@@ -634,6 +679,8 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     info.cycles = stt.cycles;
     info.applies_fp64 = stt.applies;
     info.graph_captures = stt.captures;
+    info.host_syncs = stt.syncs;
+    info.discarded_steps = stt.overshoot;
     info.rel_residual = stt.resid / nb;
     info.seconds = now_s() - t0;
     info.status = rc;
@@ -699,6 +746,8 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     info.cycles += stt.cycles;
     info.applies_fp32 += stt.applies;
     info.graph_captures += stt.captures;
+    info.host_syncs += stt.syncs;
+    info.discarded_steps += stt.overshoot;
     info.refinements++;
     info.rel_residual_inner = stt.resid / cn;
     prof_begin(kProfOther, s);
@@ -821,6 +870,8 @@ static int picard_impl(cheb_plan_s* p, const double* K0, const double* b, double
     tot.refinements += li.refinements;
     tot.applies_fp64 += li.applies_fp64;
     tot.applies_fp32 += li.applies_fp32;
+    tot.host_syncs += li.host_syncs;
+    tot.discarded_steps += li.discarded_steps;
     tot.rel_residual = li.rel_residual;
     tot.kref = li.kref;
     if (r < 0) return r;

@@ -199,6 +199,26 @@ def test_nonfinite_input_reports_status(mode):
     assert info["status"] == 0
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_host_synchronisations_per_cycle(mode):
+    """The Hessenberg / Givens update runs on the device: an LGMRES cycle
+    synchronises with the host for its residual norm, its update norm and the
+    Arnoldi checkpoints (one per cycle far from the tolerance, a few more
+    near it), so the count is a small multiple of the cycles, not one per
+    Arnoldi step; the steps run past convergence stay a small share."""
+    bc = [0, 0, 1, 1, 1, 1]
+    n = (33, 33, 33)
+    p = _plan(n, bc=bc)
+    X, Y, Z = p.mesh()
+    K = _dev(W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 100.0))
+    b = _dev(W.random_field(p.shape, 62))
+    u, info = p.solve(K, b, mode=mode, rtol=1e-12)
+    assert info["status"] == 0
+    assert info["host_syncs"] <= 5 * info["cycles"], info
+    assert info["host_syncs"] < info["iterations"] / 3, info
+    assert info["discarded_steps"] <= 0.15 * info["iterations"] + 4, info
+
+
 def test_mixed_and_fp64_agree_and_mixed_uses_fp32():
     bc = [0, 0, 1, 1, 1, 1]
     n = (33, 17, 33)

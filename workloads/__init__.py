@@ -37,6 +37,7 @@ import numpy as np
 
 DIRICHLET = 0
 NEUMANN = 1
+FLUX = 2
 
 
 def rng(seed: int) -> np.random.Generator:
@@ -120,6 +121,26 @@ def sin_cos_exp_3d(X, Y, Z):
     return u, grad, lap
 
 
+def paper_nonlinear_3d(X, Y, Z, alpha: float = 0.5):
+    """The manufactured nonlinear heat problem of Sec. 3.4 on (0,1)^3:
+    Phi = sin(pi x) sin(pi y) sin(pi z), T = (exp(alpha Phi) - 1) / alpha solves
+    -div(k(T) grad T) = f with k(T) = 1 / (1 + alpha T) and f = -lap Phi =
+    3 pi^2 Phi.  Returns (T, grad T, f) -- the third entry is the source term
+    of this nonlinear problem, not a Laplacian."""
+    sx, sy, sz = np.sin(np.pi * X), np.sin(np.pi * Y), np.sin(np.pi * Z)
+    cx, cy, cz = np.cos(np.pi * X), np.cos(np.pi * Y), np.cos(np.pi * Z)
+    phi = sx * sy * sz
+    e = np.exp(alpha * phi)
+    T = (e - 1.0) / alpha
+    grad = (e * np.pi * cx * sy * sz, e * np.pi * sx * cy * sz, e * np.pi * sx * sy * cz)
+    return T, grad, 3.0 * np.pi ** 2 * phi
+
+
+def reciprocal_conductivity(alpha: float = 0.5):
+    """k(T) = 1 / (1 + alpha T) as a face-data helper ``k_fn(X, Y, Z, T)``."""
+    return lambda X, Y, Z, T: 1.0 / (1.0 + alpha * T)
+
+
 def polynomial_3d(coeffs: dict, X, Y, Z):
     """u = sum c * x^i y^j z^k for ``coeffs = {(i, j, k): c}``; returns u, grad, lap."""
     u = np.zeros_like(X)
@@ -142,12 +163,13 @@ def polynomial_3d(coeffs: dict, X, Y, Z):
     return u, (gx, gy, gz), lap
 
 
-def face_values(bc, x, y, z, u_fn, dim: int = 3):
+def face_values(bc, x, y, z, u_fn, dim: int = 3, k_fn=None):
     """Boundary data of the analytic field ``u_fn`` on the six faces.
 
     Dirichlet faces carry ``u``; Neumann faces carry the outward normal
     derivative ``n . grad u`` (``-d_a u`` on the low face of axis a, ``+d_a u`` on
-    the high face).  The face of axis a lies at ``min`` (side 0) or ``max``
+    the high face); flux faces (type 2) carry ``-k n . grad u`` with
+    ``k = k_fn(X, Y, Z, u)``.  The face of axis a lies at ``min`` (side 0) or ``max``
     (side 1) of that axis' node array.  Returns a list of six arrays shaped
     like a (nz, ny, nx) field with axis a removed; faces of unused axes are
     returned as zero arrays of that shape.
@@ -170,6 +192,8 @@ def face_values(bc, x, y, z, u_fn, dim: int = 3):
             v = u
         else:
             v = grad[a] if side else -grad[a]
+            if bc[f] == FLUX:
+                v = -k_fn(X, Y, Z, u) * v
         out.append(np.take(v, 0, axis=npax).copy())
     return out
 
