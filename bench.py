@@ -52,10 +52,17 @@ def parse():
     ap.add_argument("--reorth", type=int, default=0, help="Gram-Schmidt twice per Arnoldi step")
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--restart", type=int, default=30)
-    ap.add_argument("--workload", default="hierarchy", choices=["hierarchy", "batch"],
+    ap.add_argument("--workload", default="hierarchy", choices=["hierarchy", "batch", "newton"],
                     help="hierarchy: the 257^3 hierarchical solve (the metric); batch: 16 uneven "
-                         "lognormal Picard instances solved concurrently (a secondary line)")
+                         "lognormal Picard instances solved concurrently (a secondary line); newton: the "
+                         "paper's Table 1 nonlinear problem by hierarchical Newton (a secondary line)")
     ap.add_argument("--use-graph", type=int, default=0)
+    ap.add_argument("--coarse-rtol", type=float, default=0.0,
+                    help="relative tolerance of the hierarchy's coarse levels (0: the same 1e-12)")
+    ap.add_argument("--recycle", type=int, default=0,
+                    help="carry LGMRES augmentation vectors across refinement steps (1) or not (0)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 16-instance batch keys")
+    ap.add_argument("--no-newton", action="store_true", help="skip the Table 1 Newton keys")
     ap.add_argument("--route32", default="auto", choices=["auto", "transform", "tensor"],
                     help="operator-apply routes: auto = the library's autotuner times every "
                          "route each axis allows and keeps the fastest (per precision); "
@@ -339,11 +346,12 @@ def apply_only(args, n):
     print(json.dumps(rec), flush=True)
 
 
-def batch_workload(args):
-    """16 instances, sizes U{33..97} (seed 1), K = K0 (1 + 0.5 |grad u|^2) with
-    lognormal K0 (sigma 0.5, correlation 0.2), Dirichlet u = x on x = +-1 and
-    z = -1, Neumann 0 elsewhere; relaxed Picard (omega 0.5) to 1e-9, inner
-    mixed-precision solves; all instances concurrently (one thread/stream each)."""
+def batch_run(steps=1, warmup=1, use_graph=0):
+    """The batched configuration: 16 instances, sizes U{33..97} (seed 1),
+    K = K0 (1 + 0.5 |grad u|^2) with lognormal K0 (sigma 0.5, correlation 0.2),
+    Dirichlet u = x on x = +-1 and z = -1, Neumann 0 elsewhere; relaxed Picard
+    (omega 0.5) to a relative change of 1e-9, inner mixed-precision solves; all
+    instances concurrently (cheb_picard_batched).  Returns a summary dict."""
     import torch
     import paper_2606_21410_b300 as P
     import workloads as W
@@ -358,23 +366,76 @@ def batch_workload(args):
         bs.append(p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"),
                         [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in faces]))
         plans.append(p)
-    kw = dict(beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1, rtol=1e-10, use_graph=args.use_graph)
-    for _ in range(max(1, args.warmup)):
+    kw = dict(beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1, rtol=1e-10, use_graph=use_graph)
+    for _ in range(max(1, warmup)):
         us, infos, its = P.picard_batched(plans, K0, bs, check_status=False, **kw)
     torch.cuda.synchronize()
     l0 = P.lib.cheb_launch_count()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         us, infos, its = P.picard_batched(plans, K0, bs, check_status=False, **kw)
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / args.steps
+    dt = (time.perf_counter() - t0) / steps
     dofs = sum(n ** 3 for n in sizes)
-    print(json.dumps({"workload": "picard batch", "sizes": sizes, "dofs": dofs, "s_per_batch": dt,
-                      "gdofs_solved_per_s": dofs / dt / 1e9, "picard_iters": its,
-                      "inner_iterations": [i["iterations"] for i in infos],
-                      "status": [i["status"] for i in infos], "use_graph": args.use_graph,
-                      "gpu_launches_per_batch": (P.lib.cheb_launch_count() - l0) // args.steps}),
-          flush=True)
+    return {"workload": "16 uneven lognormal Picard instances, concurrent", "sizes": sizes, "dofs": dofs,
+            "s_per_batch": dt, "gdofs_solved_per_s": dofs / dt / 1e9, "picard_iters": its,
+            "inner_iterations": [i["iterations"] for i in infos],
+            "status": [i["status"] for i in infos], "use_graph": use_graph,
+            "gpu_launches_per_batch": (P.lib.cheb_launch_count() - l0) // steps}
+
+
+# the paper's Table 1 (Sec. 3.4; Python/scipy, FP64, MacBook Pro M2 CPU):
+# N -> (max error against the exact temperature, wall seconds); context only
+PAPER_TABLE1 = {4: (7.352339e-2, 0.035), 8: (4.903119e-4, 0.114), 16: (6.270730e-9, 0.873),
+                32: (1.272603e-9, 2.008), 64: (8.182031e-10, 47.908), 128: (7.737196e-10, 557.870),
+                256: (7.734714e-10, 5245.951)}
+
+
+def newton_table(Ns=(4, 8, 16, 32, 64, 128, 256), mode=1):
+    """The paper's manufactured nonlinear heat problem (Sec. 3.4, Table 1):
+    k(T) = 1 / (1 + T/2) on (0,1)^3, T = 2 (exp(Phi/2) - 1), Dirichlet T = 0
+    on x = 0 and y = 0, flux data on the other faces; hierarchical Newton
+    (prolonged guess per level, cheb_newton_solve).  Per level: Newton steps,
+    LGMRES iterations, max error against the exact T, e_ref, and the level's
+    wall time (the paper's printed error and M2 time beside it)."""
+    import torch
+    import paper_2606_21410_b300 as P
+    import workloads as W
+    alpha = 0.5
+    bc = [0, 2, 0, 2, 2, 2]
+    sol = lambda X, Y, Z: W.paper_nonlinear_3d(X, Y, Z, alpha)
+    rows, prev = [], None
+    total = 0.0
+    for N in Ns:
+        p = P.Plan((N + 1,) * 3, (0, 0, 0), (1, 1, 1), bc)
+        X, Y, Z = p.mesh()
+        T, _, f = sol(X, Y, Z)
+        faces = W.face_values(bc, p.nodes(0), p.nodes(1), p.nodes(2), sol, k_fn=W.reciprocal_conductivity(alpha))
+        b = p.rhs(torch.from_numpy(f).cuda(), [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in faces])
+        K0 = torch.ones(p.shape, dtype=torch.float64, device="cuda")
+        u = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if prev is not None:
+            P.prolong(prev[0], p, prev[1], u)
+        guess = u.clone() if prev is not None else None
+        u, info, its, d = p.newton_solve(K0, b, u, alpha=alpha, tol=1e-13, maxit=30, mode=mode,
+                                         inner_rtol=1e-6, check_status=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        total += dt
+        err = float(np.abs(u.cpu().numpy() - T).max())
+        rows.append({"N": N, "newton_steps": its, "lgmres_iterations": info["iterations"], "max_error": err,
+                     "e_ref": P.rel_diff(p, u, guess) if guess is not None else None,
+                     "seconds": dt, "status": info["status"],
+                     "paper_max_error": PAPER_TABLE1[N][0], "paper_seconds_m2_cpu": PAPER_TABLE1[N][1]})
+        prev = (p, u)
+    return {"workload": "paper Table 1: nonlinear heat, hierarchical Newton N = 4 .. 256, flux faces",
+            "mode": "mixed" if mode == 1 else "fp64", "levels": rows, "total_seconds": total}
+
+
+def batch_workload(args):
+    print(json.dumps(batch_run(args.steps, args.warmup, args.use_graph)), flush=True)
 
 
 def workload_config(levels, contrast):
@@ -408,9 +469,13 @@ def main():
     if args.workload == "batch":
         batch_workload(args)
         return
+    if args.workload == "newton":
+        print(json.dumps(newton_table()), flush=True)
+        return
     plans, Ks, bs, hostK, hostb = setup_gpu(levels, args.contrast, args.route32)
     opts = dict(mode=1, rtol=1e-12, reorth=args.reorth, inner_rtol=args.inner_rtol,
-                restart=args.restart, use_graph=args.use_graph)
+                restart=args.restart, use_graph=args.use_graph, recycle=args.recycle,
+                coarse_rtol=args.coarse_rtol)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -518,7 +583,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         u64, infos64, _ = P.solve_hierarchy(plans, Ks, bs, mode=0, rtol=1e-12, check_status=False,
-                                            restart=args.restart)
+                                            restart=args.restart, coarse_rtol=args.coarse_rtol)
         torch.cuda.synchronize()
         fp64 = {"time_to_solve_s": time.perf_counter() - t0,
                 "iterations": [i["iterations"] for i in infos64],
@@ -537,6 +602,15 @@ def main():
     e2e_t = time.perf_counter() - t0
     h2d = sum(k.numel() * 8 + b.numel() * 8 for k, b in zip(hostK, hostb))
     d2h = out_host.numel() * 8
+
+    # ---- the batched configuration (secondary keys of the line)
+    batch = None
+    if not args.no_batch:
+        batch = batch_run(steps=1, warmup=1)
+    newton = None
+    if not args.no_newton:
+        newton_table(Ns=(4, 8, 16))            # warm-up of the level plans' kernels
+        newton = newton_table()
 
     # ---- finest-level timing of the preconditioner (the dominant phase)
     def time_prec(dtype, reps=10):
@@ -634,15 +708,18 @@ def main():
             "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": per_step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-            "config": workload_config(levels, args.contrast),
+            "config": dict(workload_config(levels, args.contrast),
+                           coarse_rtol=args.coarse_rtol or 1e-12, recycle=args.recycle,
+                           inner_rtol=args.inner_rtol),
             "solves_per_s": world * args.steps / elapsed,
             "iterations_per_level": [i["iterations"] for i in infos],
+            "seconds_per_level": [i["seconds"] for i in infos],
             "refinements_per_level": [i["refinements"] for i in infos],
             "rel_residual": infos[-1]["rel_residual"], "e_ref": eref,
             "apply": apply, "fp64": fp64, "phase_ms_per_step": phase,
             "routes_per_level": [p.chosen_routes for p in plans],
             "roofline": roof, "prec_roofline": prec_roof, "fp64_apply_roofline": fp64_roof,
-            "fma_peaks": fma,
+            "fma_peaks": fma, "batch": batch, "newton_table1": newton,
             "fp32_routes_finest": [pf.route32(a) for a in range(pf.dim)],
             "rel_err_vs_oracle": parity["rel_err_vs_oracle_mixed"][-1] if parity else None,
             "oracle_parity": parity,

@@ -24,9 +24,10 @@
  *  - Boundary rows (Sec. 2 "Extension to the three-dimensional setting":
  *    equations at boundary nodes are replaced by the boundary conditions):
  *    each boundary node has ONE owner face; Dirichlet faces beat Neumann
- *    faces, and among faces of one type the lowest axis wins.  A Dirichlet
+ *    and flux faces, and among the others the lowest axis wins.  A Dirichlet
  *    row reads u_p = g; a Neumann row reads n.grad u = g with n the outward
- *    normal (+d_a u on the hi face, -d_a u on the lo face).
+ *    normal (+d_a u on the hi face, -d_a u on the lo face); a flux row reads
+ *    -K_p n.grad u = g.
  *  - Streams: every call is ordered on the plan's stream.  Calls that
  *    return data to the host (solves, norms) synchronise that stream.
  *  - Errors: every function returns a cheb_status; no call aborts the
@@ -44,7 +45,10 @@ extern "C" {
 
 typedef struct cheb_plan_s* cheb_plan;
 
-enum cheb_bc { CHEB_DIRICHLET = 0, CHEB_NEUMANN = 1 };
+/* Face types: Dirichlet u = g; Neumann n.grad u = g; flux -K n.grad u = g
+ * (the heat-flux condition q_N = -k grad T . n of Sec. 3.4, with the
+ * conductivity at the boundary node). */
+enum cheb_bc { CHEB_DIRICHLET = 0, CHEB_NEUMANN = 1, CHEB_FLUX = 2 };
 
 /* arithmetic of an operator application (buffer element type) */
 enum cheb_prec { CHEB_FP64 = 0, CHEB_FP32 = 1 };
@@ -79,12 +83,13 @@ enum cheb_status {
  *            (route TRANSFORM needs n - 1 a power of two, 4 <= n - 1 <= 256;
  *             route DENSE needs n <= 129; every axis needs one of them)
  *   lo, hi   interval of each axis (hi > lo); entries of unused axes ignored
- *   bc_type  six CHEB_DIRICHLET / CHEB_NEUMANN values, faces x-,x+,y-,y+,z-,z+
+ *   bc_type  six CHEB_DIRICHLET / CHEB_NEUMANN / CHEB_FLUX values, faces
+ *            x-,x+,y-,y+,z-,z+ (flux faces exclude CHEB_ROUTE_TENSOR)
  *   stream   cudaStream_t to order the plan's work on (NULL = legacy stream)
  * The plan owns its device tables and, once a solve runs, its Krylov
  * workspace; cheb_plan_destroy frees them.  A pure-Neumann set is accepted
  * here (cheb_apply is defined for it) but cheb_solve rejects it with
- * CHEB_ERR_SINGULAR_BC. */
+ * CHEB_ERR_SINGULAR_BC (also when every face is Neumann or flux). */
 int cheb_plan_create(cheb_plan* out, int dim, const int n[3], const double lo[3],
                      const double hi[3], const int bc_type[6], void* stream);
 int cheb_plan_destroy(cheb_plan plan);
@@ -100,14 +105,22 @@ int cheb_plan_get_route(cheb_plan plan, int axis, int* route);
 int cheb_plan_set_route32(cheb_plan plan, int axis, int route);
 int cheb_plan_get_route32(cheb_plan plan, int axis, int* route);
 
-/* Autotuner: for every active axis whose size allows more than one route,
- * time the operator line pass with each of them - transform, dense and,
- * for FP32, tensor (CHEB_ROUTE_TENSOR) - FP64 and FP32 separately, on the
- * plan's grid and stream, and keep the fastest.  cache_path (nullable) names a text file of earlier decisions,
- * one line per (GPU name, axis size, precision); hits skip the timing and
- * new decisions are appended.  routes_out[6] (nullable) receives the FP64
- * routes of axes x, y, z then the FP32 routes.  Allocates three temporary
- * fields when timing; synchronises the plan's stream. */
+/* Line-tile height of the transform and dense line passes of one axis in
+ * precision prec: 8 or 16 lines per CTA (default 16; 8 doubles the CTA count
+ * of small grids).  The tensor route has its own tiling. */
+int cheb_plan_set_tile(cheb_plan plan, int axis, int prec, int lines);
+int cheb_plan_get_tile(cheb_plan plan, int axis, int prec, int* lines);
+
+/* Autotuner: for every active axis whose size allows more than one choice,
+ * time the operator line pass with each route the size allows - transform
+ * and dense, each with line tiles of 8 and 16 lines, and for FP32 tensor
+ * (CHEB_ROUTE_TENSOR) - FP64 and FP32 separately, on the plan's grid and
+ * stream, and keep the fastest (route, tile).  cache_path (nullable) names a
+ * text file of earlier decisions, one line per (GPU name, axis size,
+ * precision); hits skip the timing and new decisions are appended.
+ * routes_out[6] (nullable) receives the FP64 routes of axes x, y, z then the
+ * FP32 routes (cheb_plan_get_tile reports the tiles).  Allocates three
+ * temporary fields when timing; synchronises the plan's stream. */
 int cheb_autotune(cheb_plan plan, const char* cache_path, int routes_out[6]);
 
 /* Host copy of the CGL coordinates of one axis (n[axis] doubles, node 0 =
@@ -129,7 +142,8 @@ int cheb_deriv_t(cheb_plan plan, int prec, int axis, const void* u, void* du);
 
 /* Operator apply with boundary rows (Alg. 3; Eq. (eq1) of Sec. 3.3):
  *   interior node p:  (Au)_p = -sum_a [D_a (K * D_a u)]_p
- *   boundary node p:  Dirichlet u_p, Neumann +-(D_a u)_p (owner face's axis)
+ *   boundary node p:  Dirichlet u_p, Neumann +-(D_a u)_p, flux -+K_p (D_a u)_p
+ *                     (owner face's axis and outward sign)
  * K, u, Au: device fields of type prec.  Au must not alias K or u. */
 int cheb_apply(cheb_plan plan, int prec, const void* K, const void* u, void* Au);
 
@@ -154,6 +168,17 @@ int cheb_rhs(cheb_plan plan, const double* f, const double* const face_vals[6], 
  * diagonalization; the solve runs on M^{-1} A u = M^{-1} b. */
 enum cheb_precond { CHEB_PRECOND_NONE = 0, CHEB_PRECOND_FDM = 2 };
 
+/* System the Krylov solver works on.  REPLACE: the boundary equations
+ * replace the collocation rows at boundary nodes (cheb_apply).  ELIMINATE:
+ * the paper's formulation (Sec. 2.3.1): the boundary unknowns are eliminated
+ * through the boundary rows, x_r = G x_k + H g, and the solver runs on the
+ * reduced interior system (A_kk + A_kr G) x_k = f_k - A_kr H g, applied
+ * matrix-free (the boundary values of a Krylov vector come from the per-line
+ * elimination of the preconditioner's tables); FP64 forward solves only.
+ * Both give the same discrete solution; the reduced system is better
+ * conditioned. */
+enum cheb_formulation { CHEB_FORM_REPLACE = 0, CHEB_FORM_ELIMINATE = 1 };
+
 typedef struct cheb_solve_opts {
   int mode;            /* CHEB_SOLVE_FP64 or CHEB_SOLVE_MIXED */
   double rtol;         /* stop when ||M^{-1}(b - A u)|| <= rtol ||M^{-1} b|| (M = I
@@ -171,9 +196,17 @@ typedef struct cheb_solve_opts {
   double kref;         /* FDM conductivity; <= 0: geometric mean of K */
   int verbose;         /* 1: progress lines on stderr */
   int use_graph;       /* 1: Arnoldi cycles after a full-length cycle run as captured
-                          CUDA graphs with the Hessenberg / Givens update on the
-                          device (one host synchronisation per cycle instead of
-                          per step); graphs are cached per operator and shape */
+                          CUDA graphs (one host synchronisation per cycle); graphs
+                          are cached per operator and shape */
+  int recycle;         /* MIXED: 1 = each refinement's FP32 inner solve starts with
+                          the augmentation vectors (and their images under the
+                          preconditioned operator) of the previous one; the
+                          operator is the same within one solve, so they remain
+                          valid.  0 = every inner solve starts without them (the
+                          default: measured faster on the two-phase hierarchy) */
+  int formulation;     /* CHEB_FORM_REPLACE or CHEB_FORM_ELIMINATE */
+  double coarse_rtol;  /* hierarchies: rtol of the levels below the finest (their
+                          solutions only start the next level); 0 = rtol */
 } cheb_solve_opts;
 
 typedef struct cheb_solve_info {
@@ -196,7 +229,7 @@ typedef struct cheb_solve_info {
 
 /* Defaults: MIXED, rtol 1e-12, restart 30, augment 3, maxiter 2000,
  * inner_rtol 1e-4, inner_maxiter 400, max_refinements 30, FDM, kref auto,
- * use_graph 0. */
+ * use_graph 0, recycle 0, formulation REPLACE, coarse_rtol 0 (= rtol). */
 void cheb_solve_opts_default(cheb_solve_opts* opts);
 
 /* Solve A u = b (Alg. 2 with the Krylov solver LGMRES; boundary rows as in
@@ -228,6 +261,42 @@ int cheb_solve(cheb_plan plan, const double* K, const double* b, double* u,
 int cheb_picard_solve(cheb_plan plan, const double* K0, const double* b, double* u, double beta,
                       double omega, double tol, int maxit, const cheb_solve_opts* opts,
                       cheb_solve_info* info, int* picard_iters, double* picard_delta);
+
+/* Jacobian action of Newton's linearisation (Sec. 2.3, Newton; Sec. 3.4):
+ *   interior node p:  (J du)_p = -sum_a [D_a (K * D_a du + C_a * du)]_p
+ *   boundary node p:  Dirichlet du_p, Neumann +-(D_a du)_p, flux
+ *                     -+(K_p (D_a du)_p + C_a,p du_p) (owner face's axis, outward sign)
+ * For a conductivity law k(u) this is the derivative of A(k(u)) u at u along
+ * du when K = k(u) and C_a = k'(u) d_a u (the paper's J(T) dT =
+ * div(-k grad dT - k' dT grad T)).  K, du, Jdu and C[a] for a < dim: device
+ * fields of type prec (entries of unused axes ignored); Jdu must not alias K
+ * or du.  Axes on CHEB_ROUTE_TENSOR use their transform or dense route here. */
+int cheb_jacobian_apply(cheb_plan plan, int prec, const void* K, const void* const C[3], const void* du,
+                        void* Jdu);
+
+/* Newton's method for the temperature-dependent conductivity
+ * k(u) = K0 / (1 + alpha u) (Sec. 2.3, Newton; the reciprocal law of Sec. 3.4)
+ * with boundary rows as in cheb_apply at K = k(u) (a flux face imposes
+ * -k(u) n.grad u = g).  Repeat: K = k(u^m), C_a = k'(u^m) d_a u^m; solve
+ * J(u^m) du = b - A(K) u^m (cheb_jacobian_apply) by LGMRES left-preconditioned
+ * with the constant-coefficient inverse at the geometric mean of K, to a
+ * relative tolerance of opts->inner_rtol (MIXED: FP32 LGMRES whose error the
+ * next step's FP64 nonlinear residual corrects; FP64: FP64 LGMRES); then
+ * u^{m+1} = u^m + du; until ||du|| / ||u^{m+1}|| <= tol, or until the
+ * preconditioned nonlinear residual ||M^{-1} R(u)|| <= opts->rtol ||M^{-1} b||
+ * before a step (a prolonged guess that already resolves the solution costs
+ * no linear solve), or maxit steps.  alpha = 0 is the linear problem.  K0, b:
+ * FP64 device fields; u: FP64 device field, in: initial guess (e.g. a
+ * prolonged coarse solution, Alg. 4), out: last iterate.  info sums the linear
+ * solves (rel_residual: the last preconditioned relative nonlinear residual);
+ * newton_iters / newton_delta (nullable) receive the step count and the last
+ * relative step (0 when the residual test stopped it).  Returns
+ * CHEB_ERR_NOT_CONVERGED at maxit.
+ * Allocates six FP64 fields of scratch for the call (and four FP32 fields in
+ * MIXED), plus the plan's Krylov workspace. */
+int cheb_newton_solve(cheb_plan plan, const double* K0, double alpha, const double* b, double* u, double tol,
+                      int maxit, const cheb_solve_opts* opts, cheb_solve_info* info, int* newton_iters,
+                      double* newton_delta);
 
 /* Batches of independent instances (each its own plan, any sizes), solved
  * concurrently: one host thread per instance orders its work on its plan's
@@ -302,6 +371,19 @@ int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const
  * out / G.  K, u: FP64 device fields; synchronises the plan's stream. */
 int cheb_flux_average(cheb_plan plan, int axis, const double* K, const double* u, double* out);
 
+/* Hierarchical refinement driven by the finest level's data alone: the
+ * coarse levels' K and b are recomputed from the fine K and b by injection
+ * (CGL grids nest: coarse node j is fine node 2j per level, with the same
+ * owner face), solved as in cheb_solve_hierarchy from a zero coarsest guess,
+ * and kept only in the coarse plans' workspaces; u (fine, FP64) receives the
+ * finest solution.  plans: `levels` plans of doubling N (as for
+ * cheb_prolong), the last one the fine grid of K, b, u.  The solution does
+ * not depend on the coarse levels (they only start the iterations), so its
+ * derivatives are those of the fine solve: cheb_adjoint_solve on the fine
+ * plan gives them.  infos, e_ref: arrays of `levels` entries (nullable). */
+int cheb_solve_hierarchy_fine(int levels, const cheb_plan* plans, const double* K, const double* b, double* u,
+                              const cheb_solve_opts* opts, cheb_solve_info* infos, double* e_ref);
+
 /* z = M^{-T} y (transposed FDM preconditioner, used by the adjoint solve). */
 int cheb_precond_apply_t(cheb_plan plan, int prec, double kref, const void* y, void* z);
 
@@ -333,6 +415,16 @@ int cheb_profile_read(double* ms, long long* counts);
  * paper has no counterpart); allocates a few KB, synchronises its own
  * stream.  ms_per_launch (nullable) receives the launch time. */
 int cheb_fma_peak(int prec, double* tflops, double* ms_per_launch);
+
+/* Failure-detection self-test of the tensor-core kernels' bounded waits:
+ * one CTA allocates tensor memory like the contraction kernels, waits on a
+ * barrier that nothing completes with a limit of wait_cycles SM clocks
+ * (1 .. 2^31), gives up, raises the device error word and frees its tensor
+ * memory.  Returns CHEB_ERR_CUDA with the same message a real give-up
+ * produces (the expected outcome), CHEB_OK if the wait did not give up.
+ * The context stays usable.  Runs on the legacy stream and synchronises
+ * it.  A test hook; the paper has no counterpart. */
+int cheb_selftest_bounded_wait(long long wait_cycles);
 
 /* Human-readable text of a status code, and the message of the last failed
  * call on the calling thread. */

@@ -19,5 +19,5 @@ map.  Functions without an independent pin say "parity unpinned".
 """
 from .core import *  # noqa: F401,F403
 from .core import __all__  # noqa: F401
-from .precond import (FDMPreconditioner, geometric_mean, solve_hierarchy,  # noqa: F401,E402
-                      solve_preconditioned)
+from .precond import (FDMPreconditioner, adjoint_solve_preconditioned,  # noqa: F401,E402
+                      geometric_mean, solve_hierarchy, solve_preconditioned)

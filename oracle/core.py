@@ -30,7 +30,7 @@ __all__ = [
     "adjoint_apply", "adjoint_solve_direct", "grad_K", "picard_conductivity",
     "picard_solve", "eliminate_solve", "restrict_inject", "volume_average",
     "effective_conductivity", "maxwell_estimate", "reciprocal_law", "jacobian_apply",
-    "newton_residual", "newton_solve",
+    "newton_residual", "newton_solve", "linearized_apply", "eliminated_system",
 ]
 
 DIRICHLET = 0
@@ -506,13 +506,12 @@ def picard_solve(K0: np.ndarray, b: np.ndarray, grid: Grid, tol: float = 1e-11,
 # the paper's own BC formulation (Sec. 2.3.1) on tiny grids
 # ----------------------------------------------------------------------------
 
-def eliminate_solve(K: np.ndarray, f: np.ndarray, faces, grid: Grid) -> np.ndarray:
-    """Solve by eliminating the boundary unknowns (Eqs. (eq:BuildSystemBCs),
-    (eq:ReducedSystemBCs), (eq:RestrictBCs)): B x = g split as
-    x_r = G x_k + H g with G = -B_r^{-1} B_k, H = B_r^{-1}; reduced system
-    (A_kk + A_kr G) x_k = f_k - A_kr H g; then x_r recovered.  A is the
-    collocation operator without row replacement, B the boundary rows (one
-    per boundary node, from its owner face)."""
+def _elimination_parts(K: np.ndarray, grid: Grid):
+    """Pieces of the paper's boundary elimination (Eqs. (eq:BuildSystemBCs),
+    (eq:ReducedSystemBCs), (eq:RestrictBCs)): the collocation operator A
+    without row replacement, the boundary rows B (one per boundary node, from
+    its owner face), the index sets of boundary (r) and interior (k) nodes,
+    and G = -B_r^{-1} B_k, H = B_r^{-1} so that x_r = G x_k + H g."""
     nx, ny, nz = grid.n
     I = [np.eye(nx), np.eye(ny), np.eye(nz)]
     Dh = []
@@ -528,8 +527,6 @@ def eliminate_solve(K: np.ndarray, f: np.ndarray, faces, grid: Grid) -> np.ndarr
     r_idx = np.nonzero(own >= 0)[0]
     k_idx = np.nonzero(own < 0)[0]
     B = np.zeros((r_idx.size, grid.size))
-    g = np.zeros(r_idx.size)
-    gfull = rhs(np.zeros(grid.shape), faces, grid).ravel()
     for row, p in enumerate(r_idx):
         fce = own[p]
         if grid.bc[fce] == DIRICHLET:
@@ -539,11 +536,30 @@ def eliminate_solve(K: np.ndarray, f: np.ndarray, faces, grid: Grid) -> np.ndarr
             B[row] = (1.0 if side == 1 else -1.0) * Dh[a][p]
             if grid.bc[fce] == FLUX:
                 B[row] *= -float(np.asarray(K, float).ravel()[p])
-        g[row] = gfull[p]
-    Bk, Br = B[:, k_idx], B[:, r_idx]
-    Br_inv = np.linalg.inv(Br)
-    G = -Br_inv @ Bk
-    H = Br_inv
+    Br_inv = np.linalg.inv(B[:, r_idx])
+    G = -Br_inv @ B[:, k_idx]
+    return A, B, r_idx, k_idx, G, Br_inv
+
+
+def eliminated_system(K: np.ndarray, grid: Grid) -> np.ndarray:
+    """The reduced interior operator A_kk + A_kr G of the elimination
+    formulation (tiny grids), for conditioning comparisons with the
+    row-replaced matrix of ``assemble``."""
+    A, _, r_idx, k_idx, G, _ = _elimination_parts(K, grid)
+    return A[np.ix_(k_idx, k_idx)] + A[np.ix_(k_idx, r_idx)] @ G
+
+
+def eliminate_solve(K: np.ndarray, f: np.ndarray, faces, grid: Grid) -> np.ndarray:
+    """Solve by eliminating the boundary unknowns (Eqs. (eq:BuildSystemBCs),
+    (eq:ReducedSystemBCs), (eq:RestrictBCs)): B x = g split as
+    x_r = G x_k + H g with G = -B_r^{-1} B_k, H = B_r^{-1}; reduced system
+    (A_kk + A_kr G) x_k = f_k - A_kr H g; then x_r recovered.  A is the
+    collocation operator without row replacement, B the boundary rows (one
+    per boundary node, from its owner face)."""
+    A, B, r_idx, k_idx, G, H = _elimination_parts(K, grid)
+    own = owners(grid).ravel()
+    gfull = rhs(np.zeros(grid.shape), faces, grid).ravel()
+    g = gfull[r_idx]
     Akk, Akr = A[np.ix_(k_idx, k_idx)], A[np.ix_(k_idx, r_idx)]
     fk = np.asarray(f, float).ravel()[k_idx]
     xk = np.linalg.solve(Akk + Akr @ G, fk - Akr @ (H @ g))
@@ -624,6 +640,27 @@ def jacobian_apply(dT, T, K0, alpha: float, grid: Grid) -> np.ndarray:
         a, side = divmod(f, 2)
         s = 1.0 if side == 1 else -1.0
         out[m] += -s * h[m] * grad(T, grid, a)[m]
+    return out
+
+
+def linearized_apply(du, K, C, grid: Grid) -> np.ndarray:
+    """The linearised operator with given coefficient fields: A(K) du, plus
+    -sum_a D_a (C_a du) on interior rows and -s C_a,p du_p on flux rows of
+    axis a.  jacobian_apply is this operator at K = k(T), C_a = k'(T) d_a T."""
+    du = np.asarray(du, float)
+    out = apply(du, K, grid)
+    own = owners(grid)
+    extra = np.zeros(grid.shape)
+    for a in grid.axes:
+        extra -= grad(np.asarray(C[a], float) * du, grid, a)
+    out[own < 0] += extra[own < 0]
+    for f in range(2 * grid.dim):
+        if grid.bc[f] != FLUX:
+            continue
+        m = own == f
+        a, side = divmod(f, 2)
+        s = 1.0 if side == 1 else -1.0
+        out[m] += -s * (np.asarray(C[a], float) * du)[m]
     return out
 
 

@@ -167,6 +167,74 @@ class FDMPreconditioner:
         return x
 
 
+    def transpose(self, y: np.ndarray) -> np.ndarray:
+        """z = M^{-T} y: the transposes of the steps of __call__ in reverse
+        order (edge and corner rows, face values, interior eigen-solve with
+        its lifting, flux-row scaling).  Pinned against the dense transpose of
+        M^{-1} in tests/test_oracle_precond.py."""
+        g, kref = self.g, self.kref
+        y = np.array(y, float, copy=True)
+        I = self._interior()
+        zr = np.zeros(g.shape)          # adjoint of r' (the flux-scaled input)
+        # edge / corner rows: xE = A22^{-1} (r'[E] - sum_q s Drow[q] x[q]) over
+        # the non-edge nodes q of each edge row's owner-axis line
+        if self.lu is not None:
+            yE = np.array([y[k, j, i] for (k, j, i) in self.E])
+            wE = sla.lu_solve(self.lu, yE, trans=1)
+            for rr, (k, j, i) in enumerate(self.E):
+                zr[k, j, i] += wE[rr]
+                y[k, j, i] = 0.0
+                row = self.rows[rr]
+                if row is None:
+                    continue
+                s, Drow, line = row
+                for q, node in enumerate(line):
+                    if not self.edge[node]:
+                        y[node] -= s * Drow[q] * wE[rr]
+        # face values: x[e0] = G[0] v + Binv[0,0] g0 + Binv[0,1] gN, x[eN] likewise,
+        # with g0, gN the face values of r'
+        vbar = y[I].copy()
+        for a in g.axes:
+            t = self.t[a]
+            npax = 2 - a
+            e0 = list(I)
+            e0[npax] = 0
+            eN = list(I)
+            eN[npax] = -1
+            y0, yN = y[tuple(e0)], y[tuple(eN)]
+            vbar += np.moveaxis(np.multiply.outer(t["G"][0], y0) + np.multiply.outer(t["G"][1], yN), 0, npax)
+            zr[tuple(e0)] += t["Binv"][0, 0] * y0 + t["Binv"][1, 0] * yN
+            zr[tuple(eN)] += t["Binv"][0, 1] * y0 + t["Binv"][1, 1] * yN
+        # v = S_all diag(1 / (kref lam)) S_all^{-1} rhs  ->  rhs_bar = S_all^{-T} diag S_all^T vbar
+        v = vbar
+        for a in g.axes:
+            v = np.moveaxis(np.tensordot(self.t[a]["S"].T, v, axes=([1], [2 - a])), 0, 2 - a)
+        lam = np.zeros(v.shape)
+        for a in g.axes:
+            shp = [1, 1, 1]
+            shp[2 - a] = -1
+            lam = lam + self.t[a]["lam"].reshape(shp)
+        v = v / (kref * lam)
+        for a in g.axes:
+            v = np.moveaxis(np.tensordot(self.t[a]["Sinv"].T, v, axes=([1], [2 - a])), 0, 2 - a)
+        # rhs = r'[I] + sum_a kref (Lh[:, 0] g0 + Lh[:, 1] gN) along a
+        zr[I] += v
+        for a in g.axes:
+            t = self.t[a]
+            npax = 2 - a
+            e0 = list(I)
+            e0[npax] = 0
+            eN = list(I)
+            eN[npax] = -1
+            vm = np.moveaxis(v, npax, 0)
+            zr[tuple(e0)] += kref * np.tensordot(t["Lh"][:, 0], vm, axes=([0], [0]))
+            zr[tuple(eN)] += kref * np.tensordot(t["Lh"][:, 1], vm, axes=([0], [0]))
+        flux = np.isin(self.own, [f for f in range(2 * g.dim) if g.bc[f] == FLUX])
+        if flux.any():
+            zr = np.where(flux, -zr / kref, zr)
+        return zr
+
+
 def geometric_mean(K: np.ndarray) -> float:
     return float(np.exp(np.log(np.asarray(K, float)).mean()))
 
@@ -211,3 +279,17 @@ def solve_hierarchy(Ks, bs, grids, rtol: float = 1e-12, restart: int = 50, maxit
         infos.append(info)
         eref.append(0.0 if guess is None or lvl == 0 else _e_ref(u, guess))
     return us, infos, eref
+
+
+def adjoint_solve_preconditioned(K: np.ndarray, c: np.ndarray, grid: Grid, x0=None, rtol: float = 1e-13,
+                                 restart: int = 50, maxiter: int = 5000, kref: float | None = None):
+    """A^T lam = c by GMRES on M^{-T} A^T lam = M^{-T} c (FP64; the discrete
+    adjoint of the collocation system).  info reports the plain relative
+    residual ||c - A^T lam|| / ||c|| beside the preconditioned one."""
+    from .core import adjoint_apply, gmres
+    M = FDMPreconditioner(grid, geometric_mean(K) if kref is None else kref)
+    lam, info = gmres(lambda v: M.transpose(adjoint_apply(v, K, grid)), M.transpose(c), x0, rtol=rtol,
+                      restart=restart, maxiter=maxiter)
+    r = c - adjoint_apply(lam, K, grid)
+    info["plain_rel_residual"] = float(np.linalg.norm(r) / np.linalg.norm(c))
+    return lam, info

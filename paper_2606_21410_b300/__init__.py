@@ -11,17 +11,19 @@ package fails when the library is missing.
 from __future__ import annotations
 
 import ctypes as C
+import ctypes as C_
 
 import numpy as np
 import torch
 
 from ._lib import ChebError, SolveInfo, SolveOpts, check, lib  # noqa: F401
 
-DIRICHLET, NEUMANN = 0, 1
+DIRICHLET, NEUMANN, FLUX = 0, 1, 2
 FP64, FP32 = 0, 1
 SOLVE_FP64, SOLVE_MIXED = 0, 1
 ROUTE_AUTO, ROUTE_TRANSFORM, ROUTE_DENSE, ROUTE_TENSOR = -1, 0, 1, 2
 PRECOND_NONE, PRECOND_FDM = 0, 2
+FORM_REPLACE, FORM_ELIMINATE = 0, 1
 
 
 def solve_opts(**kw) -> SolveOpts:
@@ -116,7 +118,18 @@ class Plan:
         check(lib.cheb_autotune(self._h, cache.encode() if cache else None, out), "cheb_autotune")
         names = {0: "transform", 1: "dense", 2: "tensor"}
         return {"fp64": [names[out[a]] for a in range(self.dim)],
-                "fp32": [names[out[3 + a]] for a in range(self.dim)]}
+                "fp32": [names[out[3 + a]] for a in range(self.dim)],
+                "tile64": [self.tile(a, FP64) for a in range(self.dim)],
+                "tile32": [self.tile(a, FP32) for a in range(self.dim)]}
+
+    def set_tile(self, axis: int, prec: int, lines: int):
+        """Lines per CTA (8 or 16) of the line passes of one axis (``cheb_plan_set_tile``)."""
+        check(lib.cheb_plan_set_tile(self._h, axis, prec, lines), "cheb_plan_set_tile")
+
+    def tile(self, axis: int, prec: int) -> int:
+        r = C.c_int()
+        check(lib.cheb_plan_get_tile(self._h, axis, prec, C.byref(r)), "cheb_plan_get_tile")
+        return r.value
 
     def route(self, axis: int) -> int:
         r = C.c_int()
@@ -233,6 +246,40 @@ class Plan:
             raise ChebError(st, "cheb_picard_solve")
         return u, info.as_dict(), its.value, dlt.value
 
+    def jacobian_apply(self, K: torch.Tensor, C, du: torch.Tensor, out=None) -> torch.Tensor:
+        """J du of Newton's linearisation (``cheb_jacobian_apply``): K = k(u),
+        C = [k'(u) d_a u for each axis]."""
+        du = self._field(du, "du")
+        K = self._field(K, "K", du.dtype)
+        Cs = [self._field(c, "C", du.dtype) for c in C[: self.dim]]
+        out = self._out(out, du)
+        ptrs = (C_.c_void_p * 3)(*[c.data_ptr() for c in Cs] + [Cs[0].data_ptr()] * (3 - len(Cs)))
+        self._sync_stream()
+        check(lib.cheb_jacobian_apply(self._h, _PREC[du.dtype], _vp(K), ptrs, _vp(du), _vp(out)),
+              "cheb_jacobian_apply")
+        return out
+
+    def newton_solve(self, K0: torch.Tensor, b: torch.Tensor, u: torch.Tensor | None = None,
+                     alpha: float = 0.5, tol: float = 1e-12, maxit: int = 30, check_status: bool = True,
+                     **opts):
+        """Newton's method for k(u) = K0 / (1 + alpha u) (``cheb_newton_solve``).
+        Returns (u, info, newton iterations, last relative step)."""
+        K0 = self._field(K0, "K0", torch.float64)
+        b = self._field(b, "b", torch.float64)
+        if u is None:
+            u = torch.zeros(self.shape, dtype=torch.float64, device=b.device)
+        u = self._field(u, "u", torch.float64)
+        o = solve_opts(**opts)
+        info = SolveInfo()
+        its, dlt = C.c_int(), C.c_double()
+        self._sync_stream()
+        st = lib.cheb_newton_solve(self._h, _vp(K0), float(alpha), _vp(b), _vp(u), float(tol), int(maxit),
+                                   C.byref(o), C.byref(info), C.byref(its), C.byref(dlt))
+        check(st, "cheb_newton_solve")
+        if check_status and st != 0:
+            raise ChebError(st, "cheb_newton_solve")
+        return u, info.as_dict(), its.value, dlt.value
+
     def adjoint_solve(self, K: torch.Tensor, dJdu: torch.Tensor, u: torch.Tensor | None = None,
                       lam: torch.Tensor | None = None, dJdK: torch.Tensor | None = None,
                       check_status: bool = True, **opts):
@@ -331,6 +378,29 @@ def solve_hierarchy(plans, K, b, u0=None, check_status: bool = True, **opts):
     if check_status and st != 0:
         raise ChebError(st, "cheb_solve_hierarchy")
     return us, [i.as_dict() for i in infos], list(eref)
+
+
+def solve_hierarchy_fine(plans, K, b, u=None, check_status: bool = True, **opts):
+    """Hierarchical refinement from the finest level's K and b alone
+    (``cheb_solve_hierarchy_fine``: coarse levels recomputed by injection).
+    Returns (fine solution, infos, e_ref)."""
+    L = len(plans)
+    pf = plans[-1]
+    K = pf._field(K, "K", torch.float64)
+    b = pf._field(b, "b", torch.float64)
+    if u is None:
+        u = torch.zeros(pf.shape, dtype=torch.float64, device="cuda")
+    u = pf._field(u, "u", torch.float64)
+    for p in plans:
+        p._sync_stream()
+    hp = (C.c_void_p * L)(*[p.handle.value for p in plans])
+    infos = (SolveInfo * L)()
+    eref = (C.c_double * L)()
+    st = lib.cheb_solve_hierarchy_fine(L, hp, _vp(K), _vp(b), _vp(u), C.byref(solve_opts(**opts)), infos, eref)
+    check(st, "cheb_solve_hierarchy_fine")
+    if check_status and st != 0:
+        raise ChebError(st, "cheb_solve_hierarchy_fine")
+    return u, [i.as_dict() for i in infos], list(eref)
 
 
 def _batch_args(plans, A, b, u):

@@ -41,6 +41,9 @@ class SolveOpts(C.Structure):
         ("kref", C.c_double),
         ("verbose", i32),
         ("use_graph", i32),
+        ("recycle", i32),
+        ("formulation", i32),
+        ("coarse_rtol", C.c_double),
     ]
 
 
@@ -74,6 +77,8 @@ _SIGS = {
     "cheb_plan_get_route": (i32, [vp, i32, i32p]),
     "cheb_plan_set_route32": (i32, [vp, i32, i32]),
     "cheb_plan_get_route32": (i32, [vp, i32, i32p]),
+    "cheb_plan_set_tile": (i32, [vp, i32, i32, i32]),
+    "cheb_plan_get_tile": (i32, [vp, i32, i32, i32p]),
     "cheb_nodes": (i32, [vp, i32, f64p]),
     "cheb_autotune": (i32, [vp, C.c_char_p, i32p]),
     "cheb_plan_size": (C.c_size_t, [vp]),
@@ -100,6 +105,12 @@ _SIGS = {
     "cheb_solve_hierarchy": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
                                    C.POINTER(SolveOpts), C.POINTER(SolveInfo), f64p]),
     "cheb_flux_average": (i32, [vp, i32, vp, vp, f64p]),
+    "cheb_jacobian_apply": (i32, [vp, i32, vp, C.POINTER(vp), vp, vp]),
+    "cheb_newton_solve": (i32, [vp, vp, C.c_double, vp, vp, C.c_double, i32, C.POINTER(SolveOpts),
+                                C.POINTER(SolveInfo), i32p, f64p]),
+    "cheb_solve_hierarchy_fine": (i32, [i32, C.POINTER(vp), vp, vp, vp, C.POINTER(SolveOpts),
+                                        C.POINTER(SolveInfo), f64p]),
+    "cheb_selftest_bounded_wait": (i32, [C.c_longlong]),
     "cheb_launch_count": (C.c_longlong, []),
     "cheb_fma_peak": (i32, [i32, f64p, f64p]),
     "cheb_profile_enable": (i32, [i32]),

@@ -1,10 +1,11 @@
 // Line passes of the collocation operator (Alg. 1 and Alg. 3 of the paper,
 // Sec. 2.2 / Sec. 2.3.2) and the right-hand side with boundary rows.
 //
-// One CTA owns a tile of kTileL lines along one axis.  The tile is staged in
-// shared memory with coalesced loads: for the x axis the lines are
-// contiguous in memory, for y and z the tile holds kTileL x-adjacent lines
-// so every row of the tile is a contiguous run of kTileL elements.
+// One CTA owns a tile of TL lines along one axis (TL = 8 or 16, chosen per
+// axis and precision by the plan's autotuner; 16 TL threads, two lines per
+// warp).  The tile is staged in shared memory with coalesced loads: for the
+// x axis the lines are contiguous in memory, for y and z the tile holds TL
+// x-adjacent lines so every row of the tile is a contiguous run of TL elements.
 //
 // Line derivative, transform route (N = n - 1, P = 2N a power of two):
 //   F = DCT-I(f) as the real part of a length-P FFT of the even extension
@@ -33,23 +34,23 @@ struct AxisK {
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Shared-memory layout of a line pass: X (tile), ends (2 x kTileL x 2),
+// Shared-memory layout of a line pass: X (tile), ends (2 x TL x 2),
 // then the route's buffers.
 template <typename T>
-static size_t pass_smem_bytes(int route, int n, int P) {
+static size_t pass_smem_bytes(int route, int n, int P, int TL) {
   const int ldx = n | 1;
-  size_t b = align16(sizeof(T) * kTileL * ldx) + align16(sizeof(T) * kTileL * 4);
+  size_t b = align16(sizeof(T) * TL * ldx) + align16(sizeof(T) * TL * 4);
   if (route == CHEB_ROUTE_TRANSFORM) {
-    b += align16(2 * sizeof(T) * (size_t)(kTileL / 2) * P) + align16(2 * sizeof(T) * (size_t)P);
+    b += align16(2 * sizeof(T) * (size_t)(TL / 2) * P) + align16(2 * sizeof(T) * (size_t)P);
   } else {
-    b += align16(sizeof(T) * kTileL * ldx) + align16(sizeof(T) * (size_t)n * n);
+    b += align16(sizeof(T) * TL * ldx) + align16(sizeof(T) * (size_t)n * n);
   }
   return b;
 }
 
 // Tile <-> global mapping of element (lane l, point pt).
 struct TileMap {
-  int axis, nx, ny, nz;
+  int axis, nx, ny, nz, TL;
   int line0;      // axis 0: first line of the tile
   int i0, outer;  // axes 1, 2: first x index, fixed k (axis 1) or j (axis 2)
   __device__ __forceinline__ bool at(int l, int pt, size_t& gidx, int& i, int& j, int& k) const {
@@ -70,7 +71,7 @@ struct TileMap {
   // element e of the tile in a coalesced enumeration order
   __device__ __forceinline__ void split(int e, int n, int& l, int& pt) const {
     if (axis == 0) { l = e / n; pt = e - l * n; }
-    else { pt = e / kTileL; l = e - pt * kTileL; }
+    else { pt = e / TL; l = e - pt * TL; }
   }
 };
 
@@ -156,10 +157,10 @@ __device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* 
 // ---------------------------------------------------------------------------
 // block-wide dense derivative X <- D X (or D^T X), tile lines as rows
 // ---------------------------------------------------------------------------
-template <typename T, bool TRANSPOSE>
+template <typename T, bool TRANSPOSE, int TL>
 __device__ __forceinline__ void block_deriv_dense(T* X, T* tmp, int ldx, const T* Dm, int n) {
   constexpr int G = 4;                  // lines per work item
-  const int items = n * (kTileL / G);
+  const int items = n * (TL / G);
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int i = it % n;
     const int l0 = (it / n) * G;
@@ -175,11 +176,11 @@ __device__ __forceinline__ void block_deriv_dense(T* X, T* tmp, int ldx, const T
     for (int g = 0; g < G; ++g) tmp[(l0 + g) * ldx + i] = acc[g];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kTileL * ldx; e += blockDim.x) X[e] = tmp[e];
+  for (int e = threadIdx.x; e < TL * ldx; e += blockDim.x) X[e] = tmp[e];
   __syncthreads();
 }
 
-template <typename T, int ROUTE, int P, int CM, bool TRANSPOSE>
+template <typename T, int ROUTE, int P, int CM, bool TRANSPOSE, int TL>
 __device__ __forceinline__ void tile_deriv(T* X, T* tmp, int ldx, typename C2<T>::t* Cb,
                                            const typename C2<T>::t* tw, const T* Dm, int n,
                                            T scale) {
@@ -190,46 +191,46 @@ __device__ __forceinline__ void tile_deriv(T* X, T* tmp, int ldx, typename C2<T>
     __syncthreads();
   } else {
     __syncthreads();
-    block_deriv_dense<T, TRANSPOSE>(X, tmp, ldx, Dm, n);
+    block_deriv_dense<T, TRANSPOSE, TL>(X, tmp, ldx, Dm, n);
   }
 }
 
 // ---------------------------------------------------------------------------
 // the line-pass kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ROUTE, int P, int CM>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, int ROUTE, int P, int CM, int TL>
+__global__ void __launch_bounds__(TL * 16)
 line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
-                 const T* __restrict__ u, T* __restrict__ out) {
+                 const T* __restrict__ u, T* __restrict__ out, const T* __restrict__ Cj) {
   typedef typename C2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = ax.n, N = ax.N;
   const int ldx = n | 1;
   unsigned char* p = smem_raw;
-  T* X = (T*)p;            p += align16(sizeof(T) * kTileL * ldx);
-  T* ends = (T*)p;         p += align16(sizeof(T) * kTileL * 4);
+  T* X = (T*)p;            p += align16(sizeof(T) * TL * ldx);
+  T* ends = (T*)p;         p += align16(sizeof(T) * TL * 4);
   C* Cb = nullptr; C* tw = nullptr; T* tmp = nullptr; T* Dm = nullptr;
   if (ROUTE == CHEB_ROUTE_TRANSFORM) {
-    Cb = (C*)p;            p += align16(2 * sizeof(T) * (size_t)(kTileL / 2) * P);
+    Cb = (C*)p;            p += align16(2 * sizeof(T) * (size_t)(TL / 2) * P);
     tw = (C*)p;
     for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = ax.tw[t];
   } else {
-    tmp = (T*)p;           p += align16(sizeof(T) * kTileL * ldx);
+    tmp = (T*)p;           p += align16(sizeof(T) * TL * ldx);
     Dm = (T*)p;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) Dm[t] = ax.D[t];
   }
 
   TileMap map;
-  map.axis = axis; map.nx = g.n[0]; map.ny = g.n[1]; map.nz = g.n[2];
+  map.axis = axis; map.nx = g.n[0]; map.ny = g.n[1]; map.nz = g.n[2]; map.TL = TL;
   if (axis == 0) {
-    map.line0 = blockIdx.x * kTileL; map.i0 = 0; map.outer = 0;
+    map.line0 = blockIdx.x * TL; map.i0 = 0; map.outer = 0;
   } else {
-    const int nbx = (g.n[0] + kTileL - 1) / kTileL;
+    const int nbx = (g.n[0] + TL - 1) / TL;
     map.line0 = 0;
-    map.i0 = (blockIdx.x % nbx) * kTileL;
+    map.i0 = (blockIdx.x % nbx) * TL;
     map.outer = blockIdx.x / nbx;
   }
-  const int tile_elems = kTileL * n;
+  const int tile_elems = TL * n;
 
   // load the input tile (u, or lambda for the adjoint)
   for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
@@ -243,8 +244,8 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
 
   const bool adj = (kind == kAdjFirst || kind == kAdjAcc);
   if (kind == kDeriv || kind == kDerivT) {
-    if (kind == kDeriv) tile_deriv<T, ROUTE, P, CM, false>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    else tile_deriv<T, ROUTE, P, CM, true>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    if (kind == kDeriv) tile_deriv<T, ROUTE, P, CM, false, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    else tile_deriv<T, ROUTE, P, CM, true, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
       int l, pt; map.split(e, n, l, pt);
       size_t gi; int i, j, k;
@@ -254,9 +255,11 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
   }
 
   if (!adj) {
-    // ---- A u: D_a u, keep line-end derivatives for Neumann rows
-    tile_deriv<T, ROUTE, P, CM, false>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    if (threadIdx.x < kTileL) {
+    // ---- A u (or the Jacobian action): D_a u, keep line-end derivatives for
+    // Neumann rows; after the product q = K D_a u (+ C u) keep its line-end
+    // values for flux rows (-s q at the owner face)
+    tile_deriv<T, ROUTE, P, CM, false, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    if (threadIdx.x < TL) {
       ends[threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
       ends[threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
     }
@@ -264,10 +267,19 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
       int l, pt; map.split(e, n, l, pt);
       size_t gi; int i, j, k;
-      if (map.at(l, pt, gi, i, j, k)) X[l * ldx + pt] *= K[gi];
+      if (map.at(l, pt, gi, i, j, k)) {
+        T q = X[l * ldx + pt] * K[gi];
+        if (Cj) q += Cj[gi] * u[gi];
+        X[l * ldx + pt] = q;
+      }
     }
-    tile_deriv<T, ROUTE, P, CM, false>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    const bool first = (kind == kApplyFirst);
+    __syncthreads();
+    if (threadIdx.x < TL) {
+      ends[2 * TL + threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
+      ends[2 * TL + threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
+    }
+    tile_deriv<T, ROUTE, P, CM, false, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    const bool first = (kind == kApplyFirst || kind == kJacFirst);
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
       int l, pt; map.split(e, n, l, pt);
       size_t gi; int i, j, k;
@@ -281,25 +293,31 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
         if (first) out[gi] = u[gi];
       } else if ((o >> 1) == axis) {
         // hi face (side 1) is line point 0, lo face (side 0) is point N
-        out[gi] = (o & 1) ? ends[l * 2 + 0] : -ends[l * 2 + 1];
+        if (g.bc[o] == CHEB_FLUX)
+          out[gi] = (o & 1) ? -ends[2 * TL + l * 2 + 0] : ends[2 * TL + l * 2 + 1];
+        else
+          out[gi] = (o & 1) ? ends[l * 2 + 0] : -ends[l * 2 + 1];
       } else if (first) {
-        out[gi] = (T)0;  // Neumann row of a later axis: written by that pass
+        out[gi] = (T)0;  // Neumann / flux row of a later axis: written by that pass
       }
     }
   } else {
     // ---- A^T lam for this axis: D_a^T (S_a lam - K * D_a^T (P_int lam))
-    // S_a lam: +-lam at line ends owned by a Neumann face of this axis.
-    if (threadIdx.x < kTileL) {
+    // S_a lam: +-lam at line ends owned by a Neumann face of this axis,
+    // -+K lam at ends owned by a flux face.
+    if (threadIdx.x < TL) {
       const int l = threadIdx.x;
       size_t gi; int i, j, k;
       T s0 = (T)0, sN = (T)0;
       if (map.at(l, 0, gi, i, j, k)) {
         const int o = owner_face(g, i, j, k);
         if (o == 2 * axis + 1 && g.bc[o] == CHEB_NEUMANN) s0 = X[l * ldx + 0];
+        if (o == 2 * axis + 1 && g.bc[o] == CHEB_FLUX) s0 = -K[gi] * X[l * ldx + 0];
       }
       if (map.at(l, N, gi, i, j, k)) {
         const int o = owner_face(g, i, j, k);
         if (o == 2 * axis && g.bc[o] == CHEB_NEUMANN) sN = -X[l * ldx + N];
+        if (o == 2 * axis && g.bc[o] == CHEB_FLUX) sN = K[gi] * X[l * ldx + N];
       }
       ends[l * 2 + 0] = s0;
       ends[l * 2 + 1] = sN;
@@ -310,7 +328,7 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
       size_t gi; int i, j, k;
       if (map.at(l, pt, gi, i, j, k) && owner_face(g, i, j, k) >= 0) X[l * ldx + pt] = (T)0;
     }
-    tile_deriv<T, ROUTE, P, CM, true>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    tile_deriv<T, ROUTE, P, CM, true, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
       int l, pt; map.split(e, n, l, pt);
       size_t gi; int i, j, k;
@@ -322,7 +340,7 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
       }
       X[l * ldx + pt] = v;
     }
-    tile_deriv<T, ROUTE, P, CM, true>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
+    tile_deriv<T, ROUTE, P, CM, true, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
     const bool first = (kind == kAdjFirst);
     for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
       int l, pt; map.split(e, n, l, pt);
@@ -357,40 +375,41 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int NW>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NW) : "memory"); }
 
-template <typename T, int P>
+template <typename T, int P, int TL>
 __host__ __device__ constexpr size_t tf_smem_bytes() {
-  return align16(sizeof(T) * kTileL * (P / 2 + 1)) * 2 + align16(sizeof(T) * kTileL * 4) +
-         align16(2 * sizeof(T) * (size_t)(kTileL / 2) * FftBuf<P>::len) + align16(2 * sizeof(T) * (size_t)P);
+  return align16(sizeof(T) * TL * (P / 2 + 1)) * 2 + align16(sizeof(T) * TL * 4) +
+         align16(2 * sizeof(T) * (size_t)(TL / 2) * FftBuf<P>::len) + align16(2 * sizeof(T) * (size_t)P);
 }
 
-template <typename T, int P, int CM>
-__global__ void __launch_bounds__(kThreads, 2)
+template <typename T, int P, int CM, int TL>
+__global__ void __launch_bounds__(TL * 16, 2)
 tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
-               const T* __restrict__ u, T* __restrict__ out) {
+               const T* __restrict__ u, T* __restrict__ out, const T* __restrict__ Cj) {
   typedef typename C2<T>::t C;
   constexpr int N = P / 2, n = N + 1, ldx = n;  // n is odd
-  constexpr int TE = kTileL * n;
+  constexpr int NT = TL * 16;                     // threads: two lines per warp
+  constexpr int TE = TL * n;
   constexpr int BL = FftBuf<P>::len;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* p = smem_raw;
-  T* X = (T*)p;    p += align16(sizeof(T) * kTileL * ldx);
-  T* KO = (T*)p;   p += align16(sizeof(T) * kTileL * ldx);
-  T* ends = (T*)p; p += align16(sizeof(T) * kTileL * 4);
-  C* Cb = (C*)p;   p += align16(2 * sizeof(T) * (size_t)(kTileL / 2) * BL);
+  T* X = (T*)p;    p += align16(sizeof(T) * TL * ldx);
+  T* KO = (T*)p;   p += align16(sizeof(T) * TL * ldx);
+  T* ends = (T*)p; p += align16(sizeof(T) * TL * 4);
+  C* Cb = (C*)p;   p += align16(2 * sizeof(T) * (size_t)(TL / 2) * BL);
   C* tw = (C*)p;
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const bool adj = (kind == kAdjFirst || kind == kAdjAcc);
-  const bool is_acc = (kind == kApplyAcc || kind == kAdjAcc);
-  const bool first = (kind == kApplyFirst || kind == kAdjFirst);
+  const bool is_acc = (kind == kApplyAcc || kind == kAdjAcc || kind == kJacAcc);
+  const bool first = (kind == kApplyFirst || kind == kAdjFirst || kind == kJacFirst);
   const bool needK = !(kind == kDeriv || kind == kDerivT);
   // tile geometry
   int line0 = 0, i0 = 0, outer = 0;
   size_t base = 0, pstride = 1;
   if (axis == 0) {
-    line0 = blockIdx.x * kTileL;
+    line0 = blockIdx.x * TL;
   } else {
-    const int nbx = (nx + kTileL - 1) / kTileL;
-    i0 = (blockIdx.x % nbx) * kTileL;
+    const int nbx = (nx + TL - 1) / TL;
+    i0 = (blockIdx.x % nbx) * TL;
     outer = blockIdx.x / nbx;
     if (axis == 1) { base = (size_t)outer * ny * nx + i0; pstride = nx; }
     else { base = (size_t)outer * nx + i0; pstride = (size_t)nx * ny; }
@@ -403,8 +422,8 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
       gi = (size_t)line0 * n + e;
       return line0 + l < nlines;
     }
-    l = e & (kTileL - 1);
-    pt = e >> 4;
+    l = e % TL;
+    pt = e / TL;
     gi = base + (size_t)pt * pstride + l;
     return i0 + l < nx;
   };
@@ -413,6 +432,10 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
     else if (axis == 1) { i = i0 + l; j = pt; k = outer; }
     else { i = i0 + l; j = outer; k = pt; }
   };
+  auto gindex = [&](int l, int pt) -> size_t {  // global index of tile element (l, pt)
+    if (axis == 0) return (size_t)(line0 + l) * n + pt;
+    return base + (size_t)pt * pstride + l;
+  };
   auto on_bnd = [&](int i, int j, int k) -> bool {
     bool b = (i == 0 || i == nx - 1);
     if (g.dim > 1) b = b || j == 0 || j == ny - 1;
@@ -420,15 +443,15 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
     return b;
   };
   // ---- stage twiddles and launch the tile copies
-  for (int t = threadIdx.x; t < P; t += kThreads) tw[t] = ax.tw[t];
-  for (int e = threadIdx.x; e < TE; e += kThreads) {
+  for (int t = threadIdx.x; t < P; t += NT) tw[t] = ax.tw[t];
+  for (int e = threadIdx.x; e < TE; e += NT) {
     int l, pt; size_t gi;
     if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&X[l * ldx + pt], u + gi);
     else X[l * ldx + pt] = (T)0;
   }
   cp_commit();
   if (needK) {
-    for (int e = threadIdx.x; e < TE; e += kThreads) {
+    for (int e = threadIdx.x; e < TE; e += NT) {
       int l, pt; size_t gi;
       if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&KO[l * ldx + pt], K + gi);
       else KO[l * ldx + pt] = (T)0;
@@ -444,7 +467,7 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
     if (kind == kDeriv) warp_deriv_tf<T, P, CM, false>(X, ldx, buf, tw, N, ax.scale, w, lane);
     else warp_deriv_tf<T, P, CM, true>(X, ldx, buf, tw, N, ax.scale, w, lane);
     __syncthreads();
-    for (int e = threadIdx.x; e < TE; e += kThreads) {
+    for (int e = threadIdx.x; e < TE; e += NT) {
       int l, pt; size_t gi;
       if (elem(e, l, pt, gi)) out[gi] = X[l * ldx + pt];
     }
@@ -454,19 +477,35 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
   if (!adj) {
     warp_deriv_tf<T, P, CM, false>(X, ldx, buf, tw, N, ax.scale, w, lane);
     __syncthreads();
-    if (threadIdx.x < kTileL) {
+    if (threadIdx.x < TL) {
       ends[threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
       ends[threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
     }
     cp_wait<0>();
     __syncthreads();
-    for (int e = threadIdx.x; e < TE; e += kThreads) {
-      const int l = e / n, pt = e - (e / n) * n;
-      X[l * ldx + pt] *= KO[l * ldx + pt];
+    if (Cj) {
+      // Jacobian action: q = K D_a du + C_a du (coalesced reads of C_a and du)
+      for (int e = threadIdx.x; e < TE; e += NT) {
+        int l, pt; size_t gi;
+        const bool in = elem(e, l, pt, gi);
+        T q = X[l * ldx + pt] * KO[l * ldx + pt];
+        if (in) q += Cj[gi] * u[gi];
+        X[l * ldx + pt] = q;
+      }
+    } else {
+      for (int e = threadIdx.x; e < TE; e += NT) {
+        const int l = e / n, pt = e - (e / n) * n;
+        X[l * ldx + pt] *= KO[l * ldx + pt];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < TL) {  // line ends of K D_a u for flux rows
+      ends[2 * TL + threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
+      ends[2 * TL + threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
     }
     __syncthreads();
     if (is_acc) {  // prefetch the output being accumulated into the free K tile
-      for (int e = threadIdx.x; e < TE; e += kThreads) {
+      for (int e = threadIdx.x; e < TE; e += NT) {
         int l, pt; size_t gi;
         if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&KO[l * ldx + pt], out + gi);
       }
@@ -475,7 +514,7 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
     warp_deriv_tf<T, P, CM, false>(X, ldx, buf, tw, N, ax.scale, w, lane);
     cp_wait<0>();
     __syncthreads();
-    for (int e = threadIdx.x; e < TE; e += kThreads) {
+    for (int e = threadIdx.x; e < TE; e += NT) {
       int l, pt; size_t gi;
       if (!elem(e, l, pt, gi)) continue;
       int i, j, k;
@@ -490,16 +529,19 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
         if (first) out[gi] = u[gi];
       } else if ((o >> 1) == axis) {
         // hi face (side 1) is line point 0, lo face (side 0) is point N
-        out[gi] = (o & 1) ? ends[l * 2 + 0] : -ends[l * 2 + 1];
+        if (g.bc[o] == CHEB_FLUX)
+          out[gi] = (o & 1) ? -ends[2 * TL + l * 2 + 0] : ends[2 * TL + l * 2 + 1];
+        else
+          out[gi] = (o & 1) ? ends[l * 2 + 0] : -ends[l * 2 + 1];
       } else if (first) {
-        out[gi] = (T)0;  // Neumann row of a later axis: written by that pass
+        out[gi] = (T)0;  // Neumann / flux row of a later axis: written by that pass
       }
     }
     return;
   }
 
   // ---- A^T lam for this axis: D_a^T (S_a lam - K * D_a^T (P_int lam))
-  if (threadIdx.x < kTileL) {
+  if (threadIdx.x < TL) {
     const int l = threadIdx.x;
     T s0 = (T)0, sN = (T)0;
     int e0l, e0p; size_t gi;
@@ -508,15 +550,17 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
       node(l, 0, i, j, k);
       const int o = owner_face(g, i, j, k);
       if (o == 2 * axis + 1 && g.bc[o] == CHEB_NEUMANN) s0 = X[l * ldx + 0];
+      if (o == 2 * axis + 1 && g.bc[o] == CHEB_FLUX) s0 = -K[gindex(l, 0)] * X[l * ldx + 0];
       node(l, N, i, j, k);
       const int o2 = owner_face(g, i, j, k);
       if (o2 == 2 * axis && g.bc[o2] == CHEB_NEUMANN) sN = -X[l * ldx + N];
+      if (o2 == 2 * axis && g.bc[o2] == CHEB_FLUX) sN = K[gindex(l, N)] * X[l * ldx + N];
     }
     ends[l * 2 + 0] = s0;
     ends[l * 2 + 1] = sN;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < TE; e += kThreads) {
+  for (int e = threadIdx.x; e < TE; e += NT) {
     int l, pt; size_t gi;
     if (!elem(e, l, pt, gi)) continue;
     int i, j, k;
@@ -527,7 +571,7 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
   warp_deriv_tf<T, P, CM, true>(X, ldx, buf, tw, N, ax.scale, w, lane);
   cp_wait<0>();
   __syncthreads();
-  for (int e = threadIdx.x; e < TE; e += kThreads) {
+  for (int e = threadIdx.x; e < TE; e += NT) {
     const int l = e / n, pt = e - (e / n) * n;
     T v = -KO[l * ldx + pt] * X[l * ldx + pt];
     if (pt == 0) v += ends[l * 2 + 0];
@@ -536,7 +580,7 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
   }
   __syncthreads();
   if (is_acc) {
-    for (int e = threadIdx.x; e < TE; e += kThreads) {
+    for (int e = threadIdx.x; e < TE; e += NT) {
       int l, pt; size_t gi;
       if (elem(e, l, pt, gi)) cp_async<sizeof(T)>(&KO[l * ldx + pt], out + gi);
     }
@@ -545,7 +589,7 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
   warp_deriv_tf<T, P, CM, true>(X, ldx, buf, tw, N, ax.scale, w, lane);
   cp_wait<0>();
   __syncthreads();
-  for (int e = threadIdx.x; e < TE; e += kThreads) {
+  for (int e = threadIdx.x; e < TE; e += NT) {
     int l, pt; size_t gi;
     if (!elem(e, l, pt, gi)) continue;
     T v = X[l * ldx + pt];
@@ -574,39 +618,59 @@ template <> AxisK<float> axis_k<float>(const AxisTables& t) {
   AxisK<float> a; a.n = t.n; a.N = t.N; a.scale = (float)t.scale; a.tw = t.tw32; a.D = t.D32; return a;
 }
 
-template <typename T, int ROUTE, int P, int CM>
+template <typename T, int ROUTE, int P, int CM, int TL>
 static int launch_kernel(const Geom& g, int axis, int kind, const AxisK<T>& ak, const T* K,
-                         const T* u, T* out, cudaStream_t s, int nblocks) {
+                         const T* u, T* out, cudaStream_t s, int nblocks, const T* C) {
   int st;
   if constexpr (ROUTE == CHEB_ROUTE_TRANSFORM) {
-    auto kern = tf_pass_kernel<T, P, CM>;
-    constexpr size_t smem = tf_smem_bytes<T, P>();
+    auto kern = tf_pass_kernel<T, P, CM, TL>;
+    constexpr size_t smem = tf_smem_bytes<T, P, TL>();
     if ((st = ensure_smem_attr((const void*)kern, smem))) return st;
-    kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
+    kern<<<nblocks, TL * 16, smem, s>>>(g, axis, kind, ak, K, u, out, C);
     CHEB_LAUNCH_CHECK("tf_pass_kernel");
   } else {
-    auto kern = line_pass_kernel<T, ROUTE, P, CM>;
-    const size_t smem = pass_smem_bytes<T>(ROUTE, ak.n, P);
+    auto kern = line_pass_kernel<T, ROUTE, P, CM, TL>;
+    const size_t smem = pass_smem_bytes<T>(ROUTE, ak.n, P, TL);
     if ((st = ensure_smem_attr((const void*)kern, smem))) return st;
-    kern<<<nblocks, kThreads, smem, s>>>(g, axis, kind, ak, K, u, out);
+    kern<<<nblocks, TL * 16, smem, s>>>(g, axis, kind, ak, K, u, out, C);
     CHEB_LAUNCH_CHECK("line_pass_kernel");
   }
   return CHEB_OK;
 }
 
-template <typename T>
-int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u, T* out,
-                cudaStream_t s) {
+template <typename T, int TL>
+static int dispatch_pass(const cheb_plan_s* p, int axis, int kind, int route, const T* K, const T* u, T* out,
+                         cudaStream_t s, const T* C) {
   const Geom g = p->geom();
   const AxisTables& t = p->ax[axis];
   const AxisK<T> ak = axis_k<T>(t);
   int nblocks;
-  if (axis == 0) nblocks = (g.n[1] * g.n[2] + kTileL - 1) / kTileL;
+  if (axis == 0) nblocks = (g.n[1] * g.n[2] + TL - 1) / TL;
   else {
-    const int nbx = (g.n[0] + kTileL - 1) / kTileL;
+    const int nbx = (g.n[0] + TL - 1) / TL;
     nblocks = nbx * (axis == 1 ? g.n[2] : g.n[1]);
   }
   if (nblocks == 0) return CHEB_OK;
+  if (route == CHEB_ROUTE_DENSE)
+    return launch_kernel<T, CHEB_ROUTE_DENSE, 0, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+  switch (t.P) {
+    case 8: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 8, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+    case 16: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 16, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+    case 32: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 32, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+    case 64: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 64, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+    case 128: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 128, 2, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+    case 256: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 256, 3, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+    case 512: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 512, 5, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+    default:
+      set_error("transform route needs 2N a power of two in [8, 512]");
+      return CHEB_ERR_UNSUPPORTED;
+  }
+}
+
+template <typename T>
+int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u, T* out,
+                cudaStream_t s, const T* C) {
+  const AxisTables& t = p->ax[axis];
   int route = sizeof(T) == 4 ? t.route32 : t.route;
   if (route == CHEB_ROUTE_TENSOR) {
     if constexpr (sizeof(T) == 4) {
@@ -615,24 +679,15 @@ int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u
     }
     route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
   }
-  if (route == CHEB_ROUTE_DENSE)
-    return launch_kernel<T, CHEB_ROUTE_DENSE, 0, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
-  switch (t.P) {
-    case 8: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 8, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
-    case 16: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 16, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
-    case 32: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 32, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
-    case 64: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 64, 1>(g, axis, kind, ak, K, u, out, s, nblocks);
-    case 128: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 128, 2>(g, axis, kind, ak, K, u, out, s, nblocks);
-    case 256: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 256, 3>(g, axis, kind, ak, K, u, out, s, nblocks);
-    case 512: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 512, 5>(g, axis, kind, ak, K, u, out, s, nblocks);
-    default:
-      set_error("transform route needs 2N a power of two in [8, 512]");
-      return CHEB_ERR_UNSUPPORTED;
-  }
+  const int tile = sizeof(T) == 4 ? t.tile32 : t.tile;
+  if (tile == 8) return dispatch_pass<T, 8>(p, axis, kind, route, K, u, out, s, C);
+  return dispatch_pass<T, 16>(p, axis, kind, route, K, u, out, s, C);
 }
 
-template int launch_pass<double>(const cheb_plan_s*, int, int, const double*, const double*, double*, cudaStream_t);
-template int launch_pass<float>(const cheb_plan_s*, int, int, const float*, const float*, float*, cudaStream_t);
+template int launch_pass<double>(const cheb_plan_s*, int, int, const double*, const double*, double*, cudaStream_t,
+                                 const double*);
+template int launch_pass<float>(const cheb_plan_s*, int, int, const float*, const float*, float*, cudaStream_t,
+                                const float*);
 
 template <typename T>
 int launch_apply(const cheb_plan_s* p, const T* K, const T* u, T* out, cudaStream_t s) {
@@ -644,6 +699,19 @@ int launch_apply(const cheb_plan_s* p, const T* K, const T* u, T* out, cudaStrea
 }
 template int launch_apply<double>(const cheb_plan_s*, const double*, const double*, double*, cudaStream_t);
 template int launch_apply<float>(const cheb_plan_s*, const float*, const float*, float*, cudaStream_t);
+
+template <typename T>
+int launch_jacobian(const cheb_plan_s* p, const T* K, const T* const C[3], const T* du, T* out, cudaStream_t s) {
+  for (int a = 0; a < p->dim; ++a) {
+    int st = launch_pass<T>(p, a, a == 0 ? kJacFirst : kJacAcc, K, du, out, s, C[a]);
+    if (st != CHEB_OK) return st;
+  }
+  return CHEB_OK;
+}
+template int launch_jacobian<double>(const cheb_plan_s*, const double*, const double* const*, const double*, double*,
+                                     cudaStream_t);
+template int launch_jacobian<float>(const cheb_plan_s*, const float*, const float* const*, const float*, float*,
+                                    cudaStream_t);
 
 template <typename T>
 int launch_adjoint_apply(const cheb_plan_s* p, const T* K, const T* lam, T* out, cudaStream_t s) {

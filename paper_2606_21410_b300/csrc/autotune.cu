@@ -1,9 +1,10 @@
 // Route autotuner: for every active axis and both precisions, time the
 // operator line pass on the plan's own grid with every route the axis size
-// allows - the FFT transform route, the dense differentiation-matrix route
-// and, for FP32, the tensor-core route - and keep the fastest.  Decisions are cached in a plain text
-// file, one line per (GPU name, axis size, precision), so later plans of the
-// same size skip the timing.
+// allows - the FFT transform route and the dense differentiation-matrix route,
+// each with line tiles of 8 and of 16 lines per CTA, and for FP32 the
+// tensor-core route - and keep the fastest (route, tile).  Decisions are
+// cached in a plain text file, one line per (GPU name, axis size, precision),
+// so later plans of the same size skip the timing.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -20,8 +21,8 @@ std::mutex g_tune_mu;
 
 struct TuneRec {
   std::string gpu;
-  int n = 0, bits = 0, route = 0;
-  double ms_tf = 0, ms_dense = 0, ms_tensor = 0;  // 0: not timed
+  int n = 0, bits = 0, route = 0, tile = 16;
+  double ms_tf = 0, ms_dense = 0, ms_tensor = 0;  // best time of each route (0: not timed)
 };
 
 std::vector<TuneRec> load_cache(const char* path) {
@@ -33,9 +34,9 @@ std::vector<TuneRec> load_cache(const char* path) {
   while (std::fgets(line, sizeof(line), f)) {
     char gpu[256];
     TuneRec r;
-    // format: "<gpu name with underscores> <n> <bits> <route> <ms_tf> <ms_dense> [<ms_tensor>]"
-    if (std::sscanf(line, "%255s %d %d %d %lf %lf %lf", gpu, &r.n, &r.bits, &r.route, &r.ms_tf, &r.ms_dense,
-                    &r.ms_tensor) >= 6) {
+    // format: "<gpu name with underscores> <n> <bits> <route> <tile> <ms_tf> <ms_dense> <ms_tensor>"
+    if (std::sscanf(line, "%255s %d %d %d %d %lf %lf %lf", gpu, &r.n, &r.bits, &r.route, &r.tile, &r.ms_tf,
+                    &r.ms_dense, &r.ms_tensor) == 8) {
       r.gpu = gpu;
       v.push_back(r);
     }
@@ -48,8 +49,8 @@ void append_cache(const char* path, const TuneRec& r) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %.6f %.6f %.6f\n", r.gpu.c_str(), r.n, r.bits, r.route, r.ms_tf, r.ms_dense,
-               r.ms_tensor);
+  std::fprintf(f, "%s %d %d %d %d %.6f %.6f %.6f\n", r.gpu.c_str(), r.n, r.bits, r.route, r.tile, r.ms_tf,
+               r.ms_dense, r.ms_tensor);
   std::fclose(f);
 }
 
@@ -84,14 +85,17 @@ int time_pass(cheb_plan_s* p, int axis, T* K, T* u, T* out, float* ms) {
   return st;
 }
 
-// routes the axis allows in this precision
+// (route, tile) pairs the axis allows in this precision
+struct Cand { int route, tile; };
 template <typename T>
-std::vector<int> candidates(const cheb_plan_s* p, int a) {
-  std::vector<int> c;
+std::vector<Cand> candidates(const cheb_plan_s* p, int a) {
+  std::vector<Cand> c;
   const AxisTables& t = p->ax[a];
-  if (t.transform_ok) c.push_back(CHEB_ROUTE_TRANSFORM);
-  if (t.dense_ok) c.push_back(CHEB_ROUTE_DENSE);
-  if (sizeof(T) == 4 && tensor_route_ok(p, a)) c.push_back(CHEB_ROUTE_TENSOR);
+  for (int tile : {16, 8}) {
+    if (t.transform_ok) c.push_back({CHEB_ROUTE_TRANSFORM, tile});
+    if (t.dense_ok) c.push_back({CHEB_ROUTE_DENSE, tile});
+  }
+  if (sizeof(T) == 4 && tensor_route_ok(p, a)) c.push_back({CHEB_ROUTE_TENSOR, 16});
   return c;
 }
 
@@ -122,7 +126,8 @@ int tune_precision(cheb_plan_s* p, const char* cache, const std::string& gpu, in
   for (int a = 0; a < p->dim && !st; ++a) {
     AxisTables& t = p->ax[a];
     int& route = (sizeof(T) == 4) ? t.route32 : t.route;
-    const std::vector<int> cand = candidates<T>(p, a);
+    int& tile = (sizeof(T) == 4) ? t.tile32 : t.tile;
+    const std::vector<Cand> cand = candidates<T>(p, a);
     if (cand.size() < 2) {
       routes_out[a] = route;
       continue;
@@ -132,22 +137,26 @@ int tune_precision(cheb_plan_s* p, const char* cache, const std::string& gpu, in
       if (r.gpu == gpu && r.n == t.n && r.bits == bits) hit = &r;
     if (hit) {
       route = hit->route;
+      tile = hit->tile;
     } else {
       TuneRec r;
       float best = 0;
-      int best_route = cand[0];
-      for (int c : cand) {
+      Cand best_c = cand[0];
+      bool first = true;
+      for (const Cand& c : cand) {
         float ms = 0;
-        route = c;
+        route = c.route;
+        tile = c.tile;
         if ((st = time_pass<T>(p, a, K, u, out, &ms))) break;
-        if (c == CHEB_ROUTE_TRANSFORM) r.ms_tf = ms;
-        else if (c == CHEB_ROUTE_DENSE) r.ms_dense = ms;
-        else r.ms_tensor = ms;
-        if (c == cand[0] || ms < best) { best = ms; best_route = c; }
+        double& slot = c.route == CHEB_ROUTE_TRANSFORM ? r.ms_tf : c.route == CHEB_ROUTE_DENSE ? r.ms_dense
+                                                                                                : r.ms_tensor;
+        if (slot == 0 || ms < slot) slot = ms;
+        if (first || ms < best) { best = ms; best_c = c; first = false; }
       }
       if (st) break;
-      route = best_route;
-      r.gpu = gpu; r.n = t.n; r.bits = bits; r.route = route;
+      route = best_c.route;
+      tile = best_c.tile;
+      r.gpu = gpu; r.n = t.n; r.bits = bits; r.route = route; r.tile = tile;
       append_cache(cache, r);
       cached.push_back(r);
     }

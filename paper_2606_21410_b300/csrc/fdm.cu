@@ -797,6 +797,44 @@ static int faces_and_blines(const cheb_plan_s* p, const Fdm& f, const FdmK<T>& k
 }
 
 
+template <typename T> static T* ybuf(Fdm& f);
+template <> double* ybuf<double>(Fdm& f) { return f.Y64; }
+template <> float* ybuf<float>(Fdm& f) { return f.Y32; }
+
+template <typename T>
+static int ensure_ybuf(const cheb_plan_s* p, Fdm& f) {
+  if (ybuf<T>(f)) return CHEB_OK;
+  T* yb = nullptr;
+  CHEB_CUDA(cudaMalloc(&yb, sizeof(T) * p->size()));
+  if constexpr (sizeof(T) == 8) f.Y64 = (double*)yb;
+  else f.Y32 = (float*)yb;
+  return CHEB_OK;
+}
+
+// out = in with the values at flux-owned boundary nodes multiplied by fac
+// (in and out may alias).  A flux row -kref s (d_a u) = r_p of the
+// constant-coefficient operator is the Neumann row s (d_a u) = -r_p / kref.
+template <typename T>
+__global__ void fdm_flux_scale_kernel(Geom g, T fac, const T* in, T* out) {
+  const size_t tot = (size_t)g.n[0] * g.n[1] * g.n[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int kk = (int)(c / ((size_t)g.n[0] * g.n[1]));
+    const int o = owner_face(g, i, j, kk);
+    const T v = in[c];
+    out[c] = (o >= 0 && g.bc[o] == CHEB_FLUX) ? fac * v : v;
+  }
+}
+
+template <typename T>
+int fdm_fill_boundary(const cheb_plan_s* p, Fdm& f, const T* r, T* x, cudaStream_t s) {
+  const FdmK<T> k = make_k<T>(f, p->dim);
+  return faces_and_blines<T>(p, f, k, full_src<T>(p, x), 0, p->dim, r, x, s);
+}
+template int fdm_fill_boundary<double>(const cheb_plan_s*, Fdm&, const double*, double*, cudaStream_t);
+template int fdm_fill_boundary<float>(const cheb_plan_s*, Fdm&, const float*, float*, cudaStream_t);
+
 template <typename T>
 int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaStream_t s) {
   const Geom g = p->geom();
@@ -804,6 +842,13 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
   T** U = ubuf<T>(f);
   int st;
   if ((st = ensure_compact<T>(f, U, s))) return st;
+  if (has_flux(p)) {
+    // M^{-1} with flux rows = (Neumann-row inverse) after scaling the flux data
+    if ((st = ensure_ybuf<T>(p, f))) return st;
+    fdm_flux_scale_kernel<T><<<grid_for(p->size()), 256, 0, s>>>(g, (T)(-1.0 / kref), r, ybuf<T>(f));
+    CHEB_LAUNCH_CHECK("fdm_flux_scale_kernel");
+    r = ybuf<T>(f);
+  }
   fdm_lift_kernel<T><<<dim3((f.m[0] + 127) / 128, f.m[1], (f.m[2] + kLiftK - 1) / kLiftK), 128, 0, s>>>(
       g, k, (T)kref, r, U[0]);
   CHEB_LAUNCH_CHECK("fdm_lift_kernel");
@@ -853,10 +898,6 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
 template int fdm_apply<double>(const cheb_plan_s*, Fdm&, double, const double*, double*, cudaStream_t);
 template int fdm_apply<float>(const cheb_plan_s*, Fdm&, double, const float*, float*, cudaStream_t);
 
-template <typename T> static T* ybuf(Fdm& f);
-template <> double* ybuf<double>(Fdm& f) { return f.Y64; }
-template <> float* ybuf<float>(Fdm& f) { return f.Y32; }
-
 template <typename T>
 int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cudaStream_t s) {
   const Geom g = p->geom();
@@ -868,11 +909,9 @@ int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cud
     int st0 = ensure_compact<T>(f, U, s);
     if (st0) return st0;
   }
-  if (!ybuf<T>(f)) {
-    T* yb = nullptr;
-    CHEB_CUDA(cudaMalloc(&yb, sizeof(T) * nfull));
-    if constexpr (sizeof(T) == 8) f.Y64 = (double*)yb;
-    else f.Y32 = (float*)yb;
+  {
+    int st0 = ensure_ybuf<T>(p, f);
+    if (st0) return st0;
   }
   T* Y = ybuf<T>(f);
   CHEB_CUDA(cudaMemcpyAsync(Y, y, sizeof(T) * nfull, cudaMemcpyDeviceToDevice, s));
@@ -920,6 +959,11 @@ int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cud
     const size_t lines = tot / f.m[a];
     fdm_faces_t_kernel<T><<<grid_for(lines), 256, 0, s>>>(g, k, a, (T)kref, U[cur], Y, z);
     CHEB_LAUNCH_CHECK("fdm_faces_t_kernel");
+  }
+  if (has_flux(p)) {
+    // (M_N^{-1} S)^T with S the flux-row scaling = S M_N^{-T}
+    fdm_flux_scale_kernel<T><<<grid_for(nfull), 256, 0, s>>>(g, (T)(-1.0 / kref), z, z);
+    CHEB_LAUNCH_CHECK("fdm_flux_scale_kernel");
   }
   return CHEB_OK;
 }

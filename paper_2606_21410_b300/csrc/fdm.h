@@ -49,6 +49,12 @@ int fdm_clear(const Fdm& f, cudaStream_t s);
 // x = M^{-1} r with M the constant-kref collocation operator (same boundary rows).
 template <typename T>
 int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaStream_t s);
+// Boundary values of x from its interior and the boundary data r by the
+// per-line elimination of the boundary rows (Sec. 2.3.1: x_r = G x_k + H g):
+// faces from their lines' interiors, then edges and corners.  Neumann-type
+// rows take r as n.grad x data (flux data must be divided by -K first).
+template <typename T>
+int fdm_fill_boundary(const cheb_plan_s* p, Fdm& f, const T* r, T* x, cudaStream_t s);
 // z = M^{-T} y (for the adjoint solve).
 template <typename T>
 int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cudaStream_t s);

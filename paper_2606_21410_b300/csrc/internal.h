@@ -25,6 +25,8 @@ struct AxisTables {
   double scale = 1.0;  // 2 / (hi - lo)
   int route = CHEB_ROUTE_TRANSFORM;    // FP64 passes
   int route32 = CHEB_ROUTE_TRANSFORM;  // FP32 passes
+  int tile = 16;                       // lines per CTA of the FP64 line passes (8 or 16)
+  int tile32 = 16;                     // same for the FP32 line passes
   bool transform_ok = false;
   bool dense_ok = false;
   double2* tw64 = nullptr;
@@ -110,16 +112,31 @@ enum PassKind {
   kDerivT = 3,      // du = D_a^T u
   kAdjFirst = 4,    // A^T lam, first axis
   kAdjAcc = 5,      // A^T lam, later axes
+  kJacFirst = 6,    // Newton Jacobian action J du, first axis (apply with K D_a du + c_a du)
+  kJacAcc = 7,      // J du, later axes
 };
+
+// true when any active face carries flux data (-K n . grad u = g)
+inline bool has_flux(const cheb_plan_s* p);
 
 template <typename T>
 int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u, T* out,
-                cudaStream_t s);
+                cudaStream_t s, const T* C = nullptr);
+
+inline bool has_flux(const cheb_plan_s* p) {
+  for (int f = 0; f < 2 * p->dim; ++f)
+    if (p->bc[f] == CHEB_FLUX) return true;
+  return false;
+}
 
 // Krylov helpers (krylov.cu)
 template <typename T>
 int launch_apply(const cheb_plan_s* p, const T* K, const T* u, T* out, cudaStream_t s);
 template <typename T>
 int launch_adjoint_apply(const cheb_plan_s* p, const T* K, const T* lam, T* out, cudaStream_t s);
+// J du = A(K) du - sum_a D_a (C_a du) on interior rows, flux rows
+// -s (K D_a du + C_a du) (the linearisation of Sec. 3.4); C[a] per axis.
+template <typename T>
+int launch_jacobian(const cheb_plan_s* p, const T* K, const T* const C[3], const T* du, T* out, cudaStream_t s);
 
 }  // namespace cheb

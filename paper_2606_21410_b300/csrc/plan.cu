@@ -233,8 +233,8 @@ int cheb_plan_create(cheb_plan* out, int dim, const int n[3], const double lo[3]
     } else if (n[a] != 1) { set_error("unused axes need n = 1"); return CHEB_ERR_ARG; }
   }
   for (int f = 0; f < 6; ++f)
-    if (bc_type[f] != CHEB_DIRICHLET && bc_type[f] != CHEB_NEUMANN) {
-      set_error("bc_type must be CHEB_DIRICHLET or CHEB_NEUMANN"); return CHEB_ERR_ARG;
+    if (bc_type[f] != CHEB_DIRICHLET && bc_type[f] != CHEB_NEUMANN && bc_type[f] != CHEB_FLUX) {
+      set_error("bc_type must be CHEB_DIRICHLET, CHEB_NEUMANN or CHEB_FLUX"); return CHEB_ERR_ARG;
     }
   cheb_plan_s* p = new cheb_plan_s();
   p->dim = dim;
@@ -299,13 +299,30 @@ int cheb_plan_set_route32(cheb_plan p, int axis, int route) {
     set_error("dense route needs n <= 129"); return CHEB_ERR_UNSUPPORTED;
   }
   if (route == CHEB_ROUTE_TENSOR && !tensor_route_ok(p, axis)) {
-    set_error("tensor route needs a 2-D or 3-D grid, 33 <= n <= 257 and at least 128 lines");
+    set_error("tensor route needs a 2-D or 3-D grid, 33 <= n <= 257, at least 128 lines and no flux face");
     return CHEB_ERR_UNSUPPORTED;
   }
   if (route != CHEB_ROUTE_TRANSFORM && route != CHEB_ROUTE_DENSE && route != CHEB_ROUTE_TENSOR) {
     set_error("unknown route"); return CHEB_ERR_ARG;
   }
   t.route32 = route;
+  return CHEB_OK;
+}
+
+int cheb_plan_set_tile(cheb_plan p, int axis, int prec, int lines) {
+  if (!p || axis < 0 || axis >= p->dim) { set_error("bad plan or axis"); return CHEB_ERR_ARG; }
+  if (lines != 8 && lines != 16) { set_error("line tiles of 8 or 16 lines"); return CHEB_ERR_ARG; }
+  if (prec == CHEB_FP64) p->ax[axis].tile = lines;
+  else if (prec == CHEB_FP32) p->ax[axis].tile32 = lines;
+  else { set_error("prec must be CHEB_FP64 or CHEB_FP32"); return CHEB_ERR_ARG; }
+  return CHEB_OK;
+}
+
+int cheb_plan_get_tile(cheb_plan p, int axis, int prec, int* lines) {
+  if (!p || !lines || axis < 0 || axis >= p->dim) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  if (prec == CHEB_FP64) *lines = p->ax[axis].tile;
+  else if (prec == CHEB_FP32) *lines = p->ax[axis].tile32;
+  else { set_error("prec must be CHEB_FP64 or CHEB_FP32"); return CHEB_ERR_ARG; }
   return CHEB_OK;
 }
 

@@ -15,10 +15,12 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <thread>
 #include <vector>
 
+#include "device.cuh"
 #include "fdm.h"
 #include "umma.h"
 #include "krylov.h"
@@ -66,6 +68,7 @@ struct Workspace {
   int* dorder = nullptr;      // augmentation slot order (device) and pinned mirror
   int* horder = nullptr;
   cudaStream_t gstream = nullptr;  // private stream for graph capture
+  double* lvl[3] = {nullptr, nullptr, nullptr};  // recomputed coarse level: K, b, u (hierarchy from fine data)
   double* picK = nullptr;                         // Picard conductivity
   double* picU = nullptr;                         // Picard previous iterate
   Fdm fdm;
@@ -92,6 +95,7 @@ void free_workspace(cheb_plan_s* p) {
   for (int i = 0; i < 3; ++i) { cudaFree(w->pro[i]); cudaFree(w->adj[i]); }
   cudaFree(w->picK);
   cudaFree(w->picU);
+  for (int i = 0; i < 3; ++i) cudaFree(w->lvl[i]);
   cudaFree(w->dhess);
   cudaFreeHost(w->hhess);
   cudaFree(w->dorder);
@@ -157,6 +161,18 @@ struct LgOpts {
   int precond = CHEB_PRECOND_FDM;
   double kref = 1.0;
   double tol_abs = 0.0;  // stop when ||c - B x|| <= tol_abs
+  const void* jac[3] = {nullptr, nullptr, nullptr};  // Newton: operator J (C_a fields, type T)
+  bool elim = false;              // elimination formulation: B v = P_int A(E_0 v) (FP64)
+  const void* elim_zero = nullptr;  // a zero field (homogeneous boundary data)
+};
+
+__global__ void mask_interior_kernel(Geom g, const double* __restrict__ x, double* __restrict__ y);
+
+// Augmentation vectors carried from one LGMRES call to the next on the same
+// operator (the FP32 inner solves of one refinement loop): their count and
+// the next slot of the circular Z / BZ store.
+struct LgCarry {
+  int naug = 0, next_slot = 0;
 };
 
 struct LgStats {
@@ -176,9 +192,38 @@ template <typename T>
 static int op_B(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, const T* v, T* out, T* tmp,
                 cudaStream_t s) {
   int st;
+  if constexpr (sizeof(T) == 8) {
+    if (o.elim) {
+      // B v = [M_int^{-1}] P_int A(E_0 v): boundary values of v from its
+      // interior by the elimination with zero data, the operator, interior rows
+      const size_t n = p->size();
+      const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+      prof_begin(kProfOther, s);
+      CHEB_CUDA(cudaMemcpyAsync(tmp, v, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+      if ((st = fdm_fill_boundary<T>(p, w.fdm, (const T*)o.elim_zero, tmp, s))) return st;
+      prof_end(kProfOther, s);
+      prof_begin(Cat<T>::apply, s);
+      if ((st = launch_apply<T>(p, K, tmp, out, s))) return st;
+      prof_end(Cat<T>::apply, s);
+      mask_interior_kernel<<<blocks, 256, 0, s>>>(p->geom(), out, out);
+      CHEB_LAUNCH_CHECK("mask_interior_kernel");
+      if (o.precond != CHEB_PRECOND_FDM) return CHEB_OK;
+      prof_begin(Cat<T>::prec, s);
+      if ((st = fdm_apply<T>(p, w.fdm, o.kref, out, tmp, s))) return st;
+      prof_end(Cat<T>::prec, s);
+      mask_interior_kernel<<<blocks, 256, 0, s>>>(p->geom(), tmp, out);
+      CHEB_LAUNCH_CHECK("mask_interior_kernel");
+      return CHEB_OK;
+    }
+  }
   prof_begin(Cat<T>::apply, s);
   T* dst = o.precond == CHEB_PRECOND_FDM ? tmp : out;
-  st = o.transpose ? launch_adjoint_apply<T>(p, K, v, dst, s) : launch_apply<T>(p, K, v, dst, s);
+  if (o.jac[0]) {
+    const T* C[3] = {(const T*)o.jac[0], (const T*)o.jac[1], (const T*)o.jac[2]};
+    st = launch_jacobian<T>(p, K, C, v, dst, s);
+  } else {
+    st = o.transpose ? launch_adjoint_apply<T>(p, K, v, dst, s) : launch_apply<T>(p, K, v, dst, s);
+  }
   prof_end(Cat<T>::apply, s);
   if (st || o.precond != CHEB_PRECOND_FDM) return st;
   prof_begin(Cat<T>::prec, s);
@@ -377,7 +422,7 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
 // converged, CHEB_ERR_NOT_CONVERGED at maxiter, or an error.
 template <typename T>
 static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, const T* c, T* x,
-                  bool x_is_zero, LgStats& stt, cudaStream_t s) {
+                  bool x_is_zero, LgStats& stt, cudaStream_t s, LgCarry* carry = nullptr) {
   const size_t n = w.n;
   const int m = o.m, kk = o.k;
   const int nbasis = m + kk + 1;
@@ -388,6 +433,19 @@ static int lgmres(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, con
   auto Zp = [&](int i) { return B.Z + (size_t)i * B.ld; };
   auto BZp = [&](int i) { return B.BZ + (size_t)i * B.ld; };
   int naug = 0, next_slot = 0;
+  if (carry && kk > 0) {
+    naug = std::min(carry->naug, kk);
+    next_slot = carry->next_slot % kk;
+  }
+  // record the augmentation state on every return
+  struct SaveCarry {
+    LgCarry* c;
+    int* naug;
+    int* next;
+    ~SaveCarry() {
+      if (c) { c->naug = *naug; c->next_slot = *next; }
+    }
+  } save_carry{carry, &naug, &next_slot};
   std::vector<double> H((size_t)(nbasis + 1) * nbasis), Hr((size_t)(nbasis + 1) * nbasis);
   std::vector<double> cs(nbasis), sn(nbasis), g(nbasis + 1), y(nbasis);
   double* dv = w.dscal;
@@ -600,6 +658,9 @@ static void default_opts(cheb_solve_opts& o) {
   o.precond = CHEB_PRECOND_FDM;
   o.kref = 0.0;
   o.use_graph = 0;
+  o.recycle = 0;
+  o.formulation = CHEB_FORM_REPLACE;
+  o.coarse_rtol = 0.0;
 }
 
 static double norm2_dev(Workspace& w, const double* x, cudaStream_t s, int* st) {
@@ -623,6 +684,88 @@ template <typename T>
 static int precond(cheb_plan_s* p, Workspace& w, const LgOpts& lo, const T* r, T* z, cudaStream_t s) {
   if (lo.precond != CHEB_PRECOND_FDM) return k_scale<T>(z, r, 1.0, w.n, s);
   return lo.transpose ? fdm_apply_t<T>(p, w.fdm, lo.kref, r, z, s) : fdm_apply<T>(p, w.fdm, lo.kref, r, z, s);
+}
+
+// out = in, with the values at flux-owned boundary nodes divided by -K_p: a
+// flux row -K_p s (d_a u)_p = g_p is the Neumann row s (d_a u)_p = -g_p / K_p
+__global__ void flux_data_kernel(Geom g, const double* __restrict__ K, const double* __restrict__ in,
+                                 double* __restrict__ out) {
+  const size_t tot = (size_t)g.n[0] * g.n[1] * g.n[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((size_t)g.n[0] * g.n[1]));
+    const int o = owner_face(g, i, j, k);
+    out[c] = (o >= 0 && g.bc[o] == CHEB_FLUX) ? -in[c] / K[c] : in[c];
+  }
+}
+
+// The paper's formulation (Sec. 2.3.1): the boundary unknowns are eliminated
+// (x_r = G x_k + H g per boundary row) and LGMRES runs on the interior
+// equations (A_kk + A_kr G) x_k = f_k - A_kr H g, matrix-free: B v =
+// P_int A(E_0 v) with E_0 the elimination with zero data, right-hand side
+// P_int (b - A E_g(0)), and the solution u = E_g(v).  FP64.
+static int solve_eliminated(cheb_plan_s* p, Workspace& w, const double* K, const double* b, double* u,
+                            const cheb_solve_opts& o, LgOpts& lo, cheb_solve_info& info, double t0) {
+  cudaStream_t s = p->stream;
+  const size_t n = w.n;
+  int st;
+  if ((st = fdm_setup(p, w.fdm))) return st;
+  if ((st = ensure_bufs<double>(w, lo.m + lo.k + 1, std::max(1, lo.k)))) return st;
+  if (!w.adj[0])
+    for (int i = 0; i < 3; ++i) CHEB_CUDA(cudaMalloc(&w.adj[i], sizeof(double) * n));
+  if (!w.r64) CHEB_CUDA(cudaMalloc(&w.r64, sizeof(double) * n));
+  KrylovBufs<double>& B = w.k64;
+  const Geom g = p->geom();
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+  double* rg = w.adj[0];    // boundary data in Neumann form
+  double* zero = w.adj[1];  // homogeneous data
+  double* v = w.adj[2];     // interior unknowns (full-grid vector)
+  flux_data_kernel<<<blocks, 256, 0, s>>>(g, K, b, rg);
+  CHEB_LAUNCH_CHECK("flux_data_kernel");
+  CHEB_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * n, s));
+  // E_g(0) in B.x, then r64 = P_int (b - A E_g(0))
+  CHEB_CUDA(cudaMemsetAsync(B.x, 0, sizeof(double) * n, s));
+  if ((st = fdm_fill_boundary<double>(p, w.fdm, rg, B.x, s))) return st;
+  if ((st = launch_apply<double>(p, K, B.x, w.r64, s))) return st;
+  if ((st = k_residual<double>(w.r64, b, n, s))) return st;
+  mask_interior_kernel<<<blocks, 256, 0, s>>>(g, w.r64, w.r64);
+  CHEB_LAUNCH_CHECK("mask_interior_kernel");
+  lo.elim = true;
+  lo.elim_zero = zero;
+  // right-hand side c = [M_int^{-1}] P_int (b - A E_g(0))
+  if (lo.precond == CHEB_PRECOND_FDM) {
+    if ((st = fdm_apply<double>(p, w.fdm, lo.kref, w.r64, B.tmp, s))) return st;
+    mask_interior_kernel<<<blocks, 256, 0, s>>>(g, B.tmp, B.c);
+  } else {
+    mask_interior_kernel<<<blocks, 256, 0, s>>>(g, w.r64, B.c);
+  }
+  CHEB_LAUNCH_CHECK("mask_interior_kernel");
+  const double nb = norm2_dev(w, B.c, s, &st);
+  if (st) return st;
+  mask_interior_kernel<<<blocks, 256, 0, s>>>(g, u, v);  // initial guess: the interior of u
+  CHEB_LAUNCH_CHECK("mask_interior_kernel");
+  int rc = CHEB_OK;
+  LgStats stt;
+  if (nb > 0.0) {
+    lo.tol_abs = std::max(o.rtol * nb, o.atol);
+    lo.maxiter = o.maxiter;
+    rc = lgmres<double>(p, w, lo, K, B.c, v, false, stt, s);
+    if (rc < 0) return rc;
+  }
+  // u = E_g(v)
+  CHEB_CUDA(cudaMemcpyAsync(u, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if ((st = fdm_fill_boundary<double>(p, w.fdm, rg, u, s))) return st;
+  CHEB_CUDA(cudaStreamSynchronize(s));
+  info.iterations = stt.iterations;
+  info.cycles = stt.cycles;
+  info.applies_fp64 = stt.applies;
+  info.host_syncs = stt.syncs;
+  info.discarded_steps = stt.overshoot;
+  info.rel_residual = nb > 0.0 ? stt.resid / nb : 0.0;
+  info.seconds = now_s() - t0;
+  info.status = rc;
+  return rc;
 }
 
 static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* u,
@@ -657,6 +800,13 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     }
   }
   info.kref = lo.kref;
+  if (o.formulation == CHEB_FORM_ELIMINATE) {
+    if (o.mode != CHEB_SOLVE_FP64 || transpose) {
+      set_error("the elimination formulation is FP64 forward solves only");
+      return CHEB_ERR_UNSUPPORTED;
+    }
+    return solve_eliminated(p, w, K, b, u, o, lo, info, t0);
+  }
   // ||M^{-1} b||
   double nb;
   if (o.mode == CHEB_SOLVE_FP64) {
@@ -707,6 +857,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   }
   int rc = CHEB_ERR_NOT_CONVERGED;
   double eta = 1.0;
+  LgCarry carry;  // augmentation vectors reused by the next refinement's inner solve
   for (int it = 0; it <= o.max_refinements; ++it) {
     // r64 = b - A u (FP64)
     prof_begin(kProfApply64, s);
@@ -740,7 +891,7 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     li.tol_abs = o.inner_rtol * cn;
     li.maxiter = std::min(o.inner_maxiter, o.maxiter - info.iterations);
     LgStats stt;
-    int r2 = lgmres<float>(p, w, li, B.K, B.c, B.x, true, stt, s);
+    int r2 = lgmres<float>(p, w, li, B.K, B.c, B.x, true, stt, s, o.recycle ? &carry : nullptr);
     if (r2 < 0) return r2;
     info.iterations += stt.iterations;
     info.cycles += stt.cycles;
@@ -783,6 +934,21 @@ __global__ void fma_kernel(const double* __restrict__ a, const double* __restric
     y[c] += a[c] * b[c];
 }
 
+// flux rows -K_p s (D_a u)_p depend on K_p: dJdK_p += s lam_p (D_a u)_p on the
+// rows owned by a flux face of axis a
+__global__ void flux_grad_kernel(Geom g, int axis, const double* __restrict__ lam, const double* __restrict__ du,
+                                 double* __restrict__ dJdK) {
+  const size_t tot = (size_t)g.n[0] * g.n[1] * g.n[2];
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % g.n[0]);
+    const int j = (int)((c / g.n[0]) % g.n[1]);
+    const int k = (int)(c / ((size_t)g.n[0] * g.n[1]));
+    const int o = owner_face(g, i, j, k);
+    if (o >= 0 && (o >> 1) == axis && g.bc[o] == CHEB_FLUX)
+      dJdK[c] += ((o & 1) ? 1.0 : -1.0) * lam[c] * du[c];
+  }
+}
+
 static int grad_K_accumulate(cheb_plan_s* p, const double* u, const double* lam, double* dJdK) {
   int st;
   if ((st = ensure_ws(p))) return st;
@@ -799,6 +965,10 @@ static int grad_K_accumulate(cheb_plan_s* p, const double* u, const double* lam,
     if ((st = launch_pass<double>(p, a, kDeriv, nullptr, u, w.adj[2], s))) return st;
     fma_kernel<<<blocks, 256, 0, s>>>(w.adj[1], w.adj[2], dJdK, n);
     CHEB_LAUNCH_CHECK("fma_kernel");
+    if (has_flux(p)) {
+      flux_grad_kernel<<<blocks, 256, 0, s>>>(p->geom(), a, lam, w.adj[2], dJdK);
+      CHEB_LAUNCH_CHECK("flux_grad_kernel");
+    }
   }
   return CHEB_OK;
 }
@@ -892,11 +1062,218 @@ static int picard_impl(cheb_plan_s* p, const double* K0, const double* b, double
   return rc;
 }
 
+// Newton coefficients of k(u) = K0 / (1 + alpha u): K = k(u) and, from the
+// derivatives d_a u held in C[a], C[a] = k'(u) d_a u = -alpha K / (1 + alpha u) d_a u.
+__global__ void newton_coeff_kernel(const double* __restrict__ K0, const double* __restrict__ u, double alpha,
+                                    int dim, double* __restrict__ K, double* __restrict__ C0,
+                                    double* __restrict__ C1, double* __restrict__ C2, size_t n) {
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+    const double d = 1.0 + alpha * u[c];
+    const double k = K0[c] / d;
+    const double dk = -alpha * k / d;
+    K[c] = k;
+    C0[c] *= dk;
+    if (dim > 1) C1[c] *= dk;
+    if (dim > 2) C2[c] *= dk;
+  }
+}
+
+struct NewtonBufs {
+  double* K = nullptr;
+  double* C[3] = {nullptr, nullptr, nullptr};
+  double* r = nullptr;     // -R(u) = b - A(k(u)) u
+  double* du = nullptr;    // FP64 Newton step
+  float* K32 = nullptr;
+  float* C32[3] = {nullptr, nullptr, nullptr};
+};
+
+static int newton_impl(cheb_plan_s* p, const double* K0, double alpha, const double* b, double* u, double tol,
+                       int maxit, const cheb_solve_opts& o, cheb_solve_info& info, int* iters, double* delta) {
+  const double t0 = now_s();
+  cudaStream_t s = p->stream;
+  int st;
+  bool has_dir = false;
+  for (int f = 0; f < 2 * p->dim; ++f) has_dir |= p->bc[f] == CHEB_DIRICHLET;
+  if (!has_dir) { set_error("no Dirichlet face: the linearised system is singular"); return CHEB_ERR_SINGULAR_BC; }
+  if (o.restart < 1 || o.augment < 0 || o.restart + o.augment + 1 > kMaxVecs) {
+    set_error("need restart >= 1, augment >= 0, restart + augment < 40"); return CHEB_ERR_ARG;
+  }
+  if ((st = ensure_ws(p))) return st;
+  Workspace& w = *p->ws;
+  const size_t n = w.n;
+  const bool mixed = o.mode == CHEB_SOLVE_MIXED;
+  // scratch: K, C_a, residual and step in FP64; FP32 copies for mixed mode
+  NewtonBufs nb;
+  auto release = [&]() {
+    cudaFree(nb.K); cudaFree(nb.r); cudaFree(nb.du); cudaFree(nb.K32);
+    for (int a = 0; a < 3; ++a) { cudaFree(nb.C[a]); cudaFree(nb.C32[a]); }
+  };
+  struct Guard { std::function<void()> f; ~Guard() { f(); } } guard{release};
+  CHEB_CUDA(cudaMalloc(&nb.K, sizeof(double) * n));
+  CHEB_CUDA(cudaMalloc(&nb.r, sizeof(double) * n));
+  CHEB_CUDA(cudaMalloc(&nb.du, sizeof(double) * n));
+  for (int a = 0; a < 3; ++a) CHEB_CUDA(cudaMalloc(&nb.C[a], sizeof(double) * n));
+  if (mixed) {
+    CHEB_CUDA(cudaMalloc(&nb.K32, sizeof(float) * n));
+    for (int a = 0; a < 3; ++a) CHEB_CUDA(cudaMalloc(&nb.C32[a], sizeof(float) * n));
+  }
+  if (o.precond == CHEB_PRECOND_FDM) {
+    if ((st = fdm_setup(p, w.fdm))) return st;
+    if ((st = fdm_clear(w.fdm, s))) return st;
+  }
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
+  int rc = CHEB_ERR_NOT_CONVERGED;
+  double d = 1.0;
+  int m = 0;
+  for (m = 1; m <= maxit; ++m) {
+    // K = k(u), C_a = k'(u) d_a u
+    for (int a = 0; a < p->dim; ++a)
+      if ((st = launch_pass<double>(p, a, kDeriv, nullptr, u, nb.C[a], s))) return st;
+    newton_coeff_kernel<<<blocks, 256, 0, s>>>(K0, u, alpha, p->dim, nb.K, nb.C[0], nb.C[1], nb.C[2], n);
+    CHEB_LAUNCH_CHECK("newton_coeff_kernel");
+    // -R(u) = b - A(K) u (FP64, boundary rows included)
+    prof_begin(kProfApply64, s);
+    if ((st = launch_apply<double>(p, nb.K, u, nb.r, s))) return st;
+    prof_end(kProfApply64, s);
+    info.applies_fp64++;
+    if ((st = k_residual<double>(nb.r, b, n, s))) return st;
+    const double sr = norm2_dev(w, nb.r, s, &st);
+    if (st) return st;
+    if (!std::isfinite(sr)) { set_error("non-finite Newton residual"); return CHEB_ERR_NONFINITE; }
+    if (sr == 0.0) { d = 0.0; rc = CHEB_OK; break; }
+    LgOpts lo;
+    lo.m = o.restart;
+    lo.k = o.augment;
+    lo.reorth = o.reorth != 0;
+    lo.precond = o.precond;
+    if (o.precond == CHEB_PRECOND_FDM) {
+      if (o.kref > 0) lo.kref = o.kref;
+      else {
+        if ((st = k_sum_log(w.rs, nb.K, n, w.dscal, s))) return st;
+        if ((st = sync_read(w, 1, s))) return st;
+        lo.kref = std::exp(w.hscal[0] / (double)n);
+      }
+    }
+    info.kref = lo.kref;
+    // converged already when the preconditioned nonlinear residual meets the
+    // solve tolerance: ||M^{-1} R(u)|| <= rtol ||M^{-1} b|| (e.g. a prolonged
+    // guess from a coarser level that resolved the solution)
+    {
+      if ((st = ensure_bufs<double>(w, lo.m + lo.k + 1, std::max(1, lo.k)))) return st;
+      KrylovBufs<double>& B = w.k64;
+      if ((st = precond<double>(p, w, lo, nb.r, B.c, s))) return st;
+      const double rn = norm2_dev(w, B.c, s, &st);
+      if (st) return st;
+      if ((st = precond<double>(p, w, lo, b, B.tmp, s))) return st;
+      const double bn = norm2_dev(w, B.tmp, s, &st);
+      if (st) return st;
+      info.rel_residual = bn > 0 ? rn / bn : rn;
+      if (!std::isfinite(rn)) { set_error("non-finite Newton residual"); return CHEB_ERR_NONFINITE; }
+      if (rn <= o.rtol * bn || rn <= o.atol) { d = 0.0; rc = CHEB_OK; break; }
+    }
+    LgStats stt;
+    double step_norm = 0.0;
+    if (!mixed) {
+      if ((st = ensure_bufs<double>(w, lo.m + lo.k + 1, std::max(1, lo.k)))) return st;
+      KrylovBufs<double>& B = w.k64;
+      for (int a = 0; a < 3; ++a) lo.jac[a] = nb.C[a < p->dim ? a : 0];
+      if ((st = precond<double>(p, w, lo, nb.r, B.c, s))) return st;
+      const double cn = norm2_dev(w, B.c, s, &st);
+      if (st) return st;
+      lo.tol_abs = o.inner_rtol * cn;
+      lo.maxiter = std::min(o.inner_maxiter, std::max(1, o.maxiter - info.iterations));
+      int r2 = lgmres<double>(p, w, lo, nb.K, B.c, nb.du, true, stt, s);
+      if (r2 < 0) return r2;
+      step_norm = norm2_dev(w, nb.du, s, &st);
+      if (st) return st;
+      if ((st = k_axpy64<double>(u, nb.du, 1.0, n, s))) return st;
+      info.applies_fp64 += stt.applies;
+    } else {
+      if ((st = ensure_bufs<float>(w, lo.m + lo.k + 1, std::max(1, lo.k)))) return st;
+      KrylovBufs<float>& B = w.k32;
+      if ((st = k_cast_scale<float, double>(nb.K32, nb.K, 1.0, n, s))) return st;
+      for (int a = 0; a < p->dim; ++a)
+        if ((st = k_cast_scale<float, double>(nb.C32[a], nb.C[a], 1.0, n, s))) return st;
+      for (int a = 0; a < 3; ++a) lo.jac[a] = nb.C32[a < p->dim ? a : 0];
+      if ((st = k_cast_scale<float, double>(B.tmp, nb.r, 1.0 / sr, n, s))) return st;
+      if ((st = precond<float>(p, w, lo, B.tmp, B.c, s))) return st;
+      const double cn = norm2_t<float>(w, B.c, s, &st);
+      if (st) return st;
+      lo.tol_abs = o.inner_rtol * cn;
+      lo.maxiter = std::min(o.inner_maxiter, std::max(1, o.maxiter - info.iterations));
+      int r2 = lgmres<float>(p, w, lo, nb.K32, B.c, B.x, true, stt, s);
+      if (r2 < 0) return r2;
+      step_norm = sr * norm2_t<float>(w, B.x, s, &st);
+      if (st) return st;
+      if ((st = k_axpy64<float>(u, B.x, sr, n, s))) return st;
+      info.applies_fp32 += stt.applies;
+      info.refinements++;
+    }
+    info.iterations += stt.iterations;
+    info.cycles += stt.cycles;
+    info.host_syncs += stt.syncs;
+    info.discarded_steps += stt.overshoot;
+    info.rel_residual_inner = stt.resid;
+    const double un = norm2_dev(w, u, s, &st);
+    if (st) return st;
+    d = un > 0 ? step_norm / un : step_norm;
+    if (!std::isfinite(d)) { set_error("non-finite Newton step"); return CHEB_ERR_NONFINITE; }
+    if (o.verbose) fprintf(stderr, "[cheb] newton %d: |du|/|u| = %.3e (%d its)\n", m, d, stt.iterations);
+    if (d <= tol) { rc = CHEB_OK; break; }
+  }
+  CHEB_CUDA(cudaStreamSynchronize(s));
+  info.seconds = now_s() - t0;
+  info.status = rc;
+  if (iters) *iters = std::min(m, maxit);
+  if (delta) *delta = d;
+  return rc;
+}
+
 }  // namespace cheb
 
 using namespace cheb;
 
 extern "C" {
+
+static int tensor_core_status(cheb_plan p, int rc);
+
+int cheb_jacobian_apply(cheb_plan p, int prec, const void* K, const void* const C[3], const void* du, void* Jdu) {
+  if (!p || !K || !C || !du || !Jdu) { set_error("null argument"); return CHEB_ERR_ARG; }
+  for (int a = 0; a < p->dim; ++a)
+    if (!C[a]) { set_error("null coefficient field of an active axis"); return CHEB_ERR_ARG; }
+  if (Jdu == du || Jdu == K) { set_error("output must not alias K or du"); return CHEB_ERR_ARG; }
+  if (prec == CHEB_FP64) {
+    const double* c[3] = {(const double*)C[0], (const double*)(p->dim > 1 ? C[1] : C[0]),
+                          (const double*)(p->dim > 2 ? C[2] : C[0])};
+    return launch_jacobian<double>(p, (const double*)K, c, (const double*)du, (double*)Jdu, p->stream);
+  }
+  if (prec == CHEB_FP32) {
+    const float* c[3] = {(const float*)C[0], (const float*)(p->dim > 1 ? C[1] : C[0]),
+                         (const float*)(p->dim > 2 ? C[2] : C[0])};
+    return launch_jacobian<float>(p, (const float*)K, c, (const float*)du, (float*)Jdu, p->stream);
+  }
+  set_error("prec must be CHEB_FP64 or CHEB_FP32");
+  return CHEB_ERR_ARG;
+}
+
+int cheb_newton_solve(cheb_plan p, const double* K0, double alpha, const double* b, double* u, double tol,
+                      int maxit, const cheb_solve_opts* opts, cheb_solve_info* info, int* newton_iters,
+                      double* newton_delta) {
+  if (!p || !K0 || !b || !u || maxit < 1 || !(tol > 0) || !std::isfinite(alpha)) {
+    set_error("bad argument (need maxit >= 1, tol > 0, finite alpha)");
+    return CHEB_ERR_ARG;
+  }
+  cheb_solve_opts o;
+  if (opts) o = *opts;
+  else default_opts(o);
+  if (o.mode != CHEB_SOLVE_FP64 && o.mode != CHEB_SOLVE_MIXED) { set_error("bad mode"); return CHEB_ERR_ARG; }
+  cheb_solve_info tmp;
+  std::memset(&tmp, 0, sizeof(tmp));
+  int rc = newton_impl(p, K0, alpha, b, u, tol, maxit, o, tmp, newton_iters, newton_delta);
+  if (rc >= 0 && (rc = tensor_core_status(p, rc)) < 0) tmp.status = rc;
+  if (info) *info = tmp;
+  return rc;
+}
 
 void cheb_solve_opts_default(cheb_solve_opts* o) {
   if (o) default_opts(*o);
@@ -938,8 +1315,13 @@ int cheb_prolong(cheb_plan coarse, cheb_plan fine, int prec, const void* uc, voi
   if ((st = ensure_ws(fine))) return st;
   Workspace& w = *fine->ws;
   if (!w.pro[0]) {
-    CHEB_CUDA(cudaMalloc(&w.pro[0], sizeof(double) * (w.n / 2 + 1)));
-    CHEB_CUDA(cudaMalloc(&w.pro[1], sizeof(double) * (w.n / 2 + 1)));
+    // intermediates of the axis passes: after x (nx_f, ny_c, nz_c), after y
+    // (nx_f, ny_f, nz_c); the larger one sizes both scratch arrays
+    const size_t n1 = (size_t)fine->n[0] * coarse->n[1] * coarse->n[2];
+    const size_t n2 = (size_t)fine->n[0] * fine->n[1] * coarse->n[2];
+    const size_t cap = std::max<size_t>(1, std::max(n1, n2));
+    CHEB_CUDA(cudaMalloc(&w.pro[0], sizeof(double) * cap));
+    CHEB_CUDA(cudaMalloc(&w.pro[1], sizeof(double) * cap));
   }
   if (prec == CHEB_FP64) {
     prof_begin(kProfProlong, fine->stream);
@@ -986,7 +1368,11 @@ int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const
       CHEB_CUDA(cudaMemcpyAsync(w.pro[2], u[l], sizeof(double) * w.n, cudaMemcpyDeviceToDevice, p->stream));
     }
     cheb_solve_info info;
-    rc = cheb_solve(p, K[l], b[l], u[l], opts, &info);
+    cheb_solve_opts ol;
+    if (opts) ol = *opts;
+    else default_opts(ol);
+    if (l + 1 < levels && ol.coarse_rtol > 0) ol.rtol = ol.coarse_rtol;
+    rc = cheb_solve(p, K[l], b[l], u[l], &ol, &info);
     if (infos) infos[l] = info;
     if (rc < 0) return rc;
     if (e_ref) {
@@ -995,6 +1381,62 @@ int cheb_solve_hierarchy(int levels, const cheb_plan* plans, const double* const
     }
   }
   return rc;
+}
+
+}  // extern "C"
+
+// coarse[k][j][i] = fine[r k][r j][r i] (restriction by injection: CGL nodes
+// nest, coarse node j is fine node r j for N_fine = r N_coarse)
+__global__ void inject_kernel(const double* __restrict__ fine, int fnx, int fny, int r, int cnx, int cny, int cnz,
+                              int dim, double* __restrict__ coarse) {
+  const size_t tot = (size_t)cnx * cny * cnz;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < tot; c += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(c % cnx);
+    const int j = (int)((c / cnx) % cny);
+    const int k = (int)(c / ((size_t)cnx * cny));
+    const size_t fi = (size_t)i * r;
+    const size_t fj = dim > 1 ? (size_t)j * r : 0;
+    const size_t fk = dim > 2 ? (size_t)k * r : 0;
+    coarse[c] = fine[(fk * fny + fj) * fnx + fi];
+  }
+}
+
+extern "C" {
+
+int cheb_solve_hierarchy_fine(int levels, const cheb_plan* plans, const double* K, const double* b, double* u,
+                              const cheb_solve_opts* opts, cheb_solve_info* infos, double* e_ref) {
+  if (levels < 1 || !plans || !K || !b || !u) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  cheb_plan pf = plans[levels - 1];
+  for (int l = 0; l + 1 < levels; ++l) {
+    int st = check_prolong_pair(plans[l], plans[l + 1]);
+    if (st) return st;
+  }
+  int st;
+  std::vector<const double*> Kl(levels), bl(levels);
+  std::vector<double*> ul(levels);
+  for (int l = 0; l < levels; ++l) {
+    cheb_plan p = plans[l];
+    if (l == levels - 1) { Kl[l] = K; bl[l] = b; ul[l] = u; continue; }
+    if ((st = ensure_ws(p))) return st;
+    Workspace& w = *p->ws;
+    for (int i = 0; i < 3; ++i)
+      if (!w.lvl[i]) CHEB_CUDA(cudaMalloc(&w.lvl[i], sizeof(double) * w.n));
+    const int r = (pf->n[0] - 1) / (p->n[0] - 1);
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((w.n + 255) / 256, 148 * 8));
+    inject_kernel<<<blocks, 256, 0, pf->stream>>>(K, pf->n[0], pf->n[1], r, p->n[0], p->n[1], p->n[2], p->dim,
+                                                  w.lvl[0]);
+    CHEB_LAUNCH_CHECK("inject_kernel");
+    inject_kernel<<<blocks, 256, 0, pf->stream>>>(b, pf->n[0], pf->n[1], r, p->n[0], p->n[1], p->n[2], p->dim,
+                                                  w.lvl[1]);
+    CHEB_LAUNCH_CHECK("inject_kernel");
+    Kl[l] = w.lvl[0];
+    bl[l] = w.lvl[1];
+    ul[l] = w.lvl[2];
+  }
+  // the coarsest level starts from zero; every plan orders its work after the injections
+  CHEB_CUDA(cudaMemsetAsync(ul[0], 0, sizeof(double) * plans[0]->size(), pf->stream));
+  CHEB_CUDA(cudaStreamSynchronize(pf->stream));
+  return cheb_solve_hierarchy(levels, plans, Kl.data(), bl.data(), ul.data(), opts, infos, e_ref);
 }
 
 int cheb_precond_apply_t(cheb_plan p, int prec, double kref, const void* y, void* z) {
@@ -1108,6 +1550,16 @@ int cheb_picard_batched(int count, const cheb_plan* plans, const double* const* 
                         double tol, int maxit, const cheb_solve_opts* opts, cheb_solve_info* infos,
                         int* picard_iters) {
   return batched(count, plans, K0, b, u, opts, infos, beta, omega, tol, maxit, picard_iters, true);
+}
+
+int cheb_selftest_bounded_wait(long long wait_cycles) {
+  int st = umma_wait_selftest(wait_cycles, nullptr);
+  if (st) return st;
+  const int e = umma_take_error();
+  if (e == 0) { set_error("bounded-wait self-test: the wait did not give up"); return CHEB_OK; }
+  set_error(e < 0 ? "could not read the tensor-core error word"
+                  : "tensor-core contraction: a bounded pipeline wait gave up (self-test)");
+  return CHEB_ERR_CUDA;
 }
 
 int cheb_flux_average(cheb_plan p, int axis, const double* K, const double* u, double* out) {

@@ -74,12 +74,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Waits for the phase of `parity` to complete.  Gives up (false) when the
-// CTA's abort flag is raised or after kWaitCycles, raising the flag itself.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// CTA's abort flag is raised or after `limit` cycles (kWaitCycles in the
+// kernels), raising the flag and the device error word itself.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                          long long limit = kWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicOr(&g_umma_err, 1);
       return false;
@@ -87,6 +89,7 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
   }
   return true;
 }
+
 // Same, ignoring the abort flag (teardown drains).
 __device__ bool mbar_drain(uint32_t bar, uint32_t parity) {
   const long long t0 = clock64();
@@ -111,6 +114,41 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Self-test of the bounded waits and the abort path: the CTA allocates
+// tensor memory as the contraction kernels do, thread 0 waits (with a short
+// limit) on a freshly initialised mbarrier that nothing ever arrives on, the
+// wait gives up and raises the abort flag and the device error word, and the
+// CTA frees its tensor memory and returns.  No copy or MMA is ever issued, so
+// nothing is in flight when the CTA ends.
+__global__ void __launch_bounds__(64, 1) wait_selftest_kernel(long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(32)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0u, &abort_flag, limit);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(&tmem_slot);
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
+  }
 }
 
 // Shared-memory matrix descriptor of a K-major operand whose rows are
@@ -1196,7 +1234,7 @@ struct TensorApply {
 };
 
 bool tensor_route_ok(const cheb_plan_s* p, int axis) {
-  if (p->dim < 2 || axis < 0 || axis >= p->dim) return false;
+  if (p->dim < 2 || axis < 0 || axis >= p->dim || has_flux(p)) return false;
   const int n = p->n[axis];
   return n >= 33 && n <= 257 && p->size() / (size_t)n >= (size_t)kBM;
 }
@@ -1312,6 +1350,14 @@ int tensor_apply_pass(const cheb_plan_s* pc, int axis, bool first, const float* 
     st = axis == 0 ? launch_dense<true>(mh, ml, lg, A, nA, s) : launch_dense<false>(mh, ml, lg, A, nA, s);
     if (st) return st;
   }
+  return CHEB_OK;
+}
+
+int umma_wait_selftest(long long wait_cycles, cudaStream_t s) {
+  if (wait_cycles < 1 || wait_cycles > kWaitCycles) { set_error("wait_cycles out of range"); return CHEB_ERR_ARG; }
+  wait_selftest_kernel<<<1, 64, 0, s>>>(wait_cycles);
+  CHEB_LAUNCH_CHECK("wait_selftest_kernel");
+  CHEB_CUDA(cudaStreamSynchronize(s));
   return CHEB_OK;
 }
 

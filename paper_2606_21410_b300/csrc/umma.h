@@ -61,5 +61,8 @@ void tensor_apply_free(TensorApply* t);
 // Reads and clears the device-side error word the kernel sets when one of
 // its bounded waits gives up (returns 0 when no wait gave up).
 int umma_take_error();
+// Runs the bounded-wait self-test kernel (a wait that nothing completes,
+// limit wait_cycles) on stream s and synchronises it.
+int umma_wait_selftest(long long wait_cycles, cudaStream_t s);
 
 }  // namespace cheb

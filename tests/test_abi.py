@@ -57,7 +57,7 @@ def test_plan_create_rejects_bad_arguments_without_cuda():
     assert lib.cheb_plan_create(C.byref(h), 3, (C.c_int * 3)(9, 2, 9), lo, hi, bc, None) == -1
     assert lib.cheb_plan_create(C.byref(h), 2, (C.c_int * 3)(9, 9, 9), lo, hi, bc, None) == -1
     assert lib.cheb_plan_create(C.byref(h), 3, n, lo, (C.c_double * 3)(1, -1, 1), bc, None) == -1
-    assert lib.cheb_plan_create(C.byref(h), 3, n, lo, hi, (C.c_int * 6)(0, 0, 2, 0, 0, 0), None) == -1
+    assert lib.cheb_plan_create(C.byref(h), 3, n, lo, hi, (C.c_int * 6)(0, 0, 3, 0, 0, 0), None) == -1
     assert b"bc_type" in lib.cheb_last_error()
     assert lib.cheb_apply(None, 0, None, None, None) == -1
     assert lib.cheb_plan_destroy(None) == 0

@@ -148,3 +148,95 @@ def test_autograd_mean_flux_gradient():
     fd = (objective(torch.tensor(10.0 + h, dtype=torch.float64, device="cuda")).item()
           - objective(torch.tensor(10.0 - h, dtype=torch.float64, device="cuda")).item()) / (2 * h)
     assert abs(k.grad.item() - fd) <= 1e-6 * abs(fd), (k.grad.item(), fd)
+
+
+def _two_phase(p_or_g, contrast, nodes):
+    bc = [0, 0, 1, 1, 1, 1]
+    X, Y, Z = W.mesh(*nodes)
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, contrast)
+    faces = W.face_values(bc, nodes[0], nodes[1], nodes[2],
+                          lambda X, Y, Z: (X, (np.ones_like(X), 0 * X, 0 * X), 0 * X))
+    return K, faces
+
+
+def test_hierarchy_from_fine_data_equals_sampled_levels():
+    """cheb_solve_hierarchy_fine recomputes the coarse K and b by injection
+    (CGL grids nest); it must give the hierarchy of separately sampled
+    levels: same fine solution, same e_ref."""
+    import paper_2606_21410_b300 as P
+    bc = [0, 0, 1, 1, 1, 1]
+    plans, Ks, bs = [], [], []
+    for n in (9, 17, 33):
+        p = P.Plan((n,) * 3, bc=bc)
+        K, faces = _two_phase(p, 100.0, [p.nodes(0), p.nodes(1), p.nodes(2)])
+        plans.append(p)
+        Ks.append(_dev(K))
+        bs.append(p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"), [_dev(f) for f in faces]))
+    us, _, eref = P.solve_hierarchy(plans, Ks, bs, mode=1, rtol=1e-12)
+    plans2 = [P.Plan((n,) * 3, bc=bc) for n in (9, 17, 33)]
+    uf, _, eref2 = P.solve_hierarchy_fine(plans2, Ks[-1], bs[-1], mode=1, rtol=1e-12)
+    assert _rel(uf.cpu().numpy(), us[-1].cpu().numpy()) < 1e-12
+    for a, b_ in zip(eref, eref2):
+        assert abs(a - b_) <= 1e-9 * max(a, 1e-300)
+
+
+def _mean_flux(p, K, u, wface):
+    """J = mean of K d_x u over the x = +1 face (x index 0), Clenshaw-Curtis
+    weights on the face nodes; -J is the outward heat flux."""
+    from paper_2606_21410_b300 import autograd as AG
+    return (wface * (K * AG.deriv(p, u, 0))[:, :, 0]).sum()
+
+
+def test_hierarchical_gradient_129_by_central_differences():
+    """The 129^3 two-phase configuration (contrast 10) solved by the
+    hierarchy 33^3 -> 65^3 -> 129^3 from the fine data; J = mean flux on
+    x = +1.  dJ/dk_incl by autograd (fine-level adjoint solve) against central
+    differences of hierarchical solves, relative error <= 1e-6."""
+    import paper_2606_21410_b300 as P
+    from paper_2606_21410_b300 import autograd as AG
+    bc = [0, 0, 1, 1, 1, 1]
+    plans = [P.Plan((n,) * 3, bc=bc) for n in (33, 65, 129)]
+    pf = plans[-1]
+    chi, faces = _two_phase(pf, 1.0 + 1.0, [pf.nodes(0), pf.nodes(1), pf.nodes(2)])
+    inc = _dev(chi - 1.0)                   # indicator of the inclusions
+    b = pf.rhs(torch.zeros(pf.shape, dtype=torch.float64, device="cuda"), [_dev(f) for f in faces])
+    w = O.cc_weights(128)
+    wface = _dev(np.outer(w, w) / 4.0)
+
+    def J(kinc):
+        K = 1.0 + (kinc - 1.0) * inc
+        u = AG.solve_hierarchy(plans, K, b, mode=1, rtol=1e-12)
+        return _mean_flux(pf, K, u, wface)
+
+    k = torch.tensor(10.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    Jv = J(k)
+    Jv.backward()
+    h = 1e-3
+    with torch.no_grad():
+        fd = (J(torch.tensor(10.0 + h, dtype=torch.float64, device="cuda")).item()
+              - J(torch.tensor(10.0 - h, dtype=torch.float64, device="cuda")).item()) / (2 * h)
+    assert abs(k.grad.item() - fd) <= 1e-6 * abs(fd), (k.grad.item(), fd)
+
+
+def test_adjoint_and_gradient_33_against_oracle_transposed_gmres():
+    """The C3 geometry at 33^3 (contrast 10), J = <c, u>: lambda from the GPU
+    adjoint solve against the oracle's transposed-preconditioned GMRES, and
+    dJ/dK against the oracle's gradient formula with the oracle's own u and
+    lambda."""
+    bc = [0, 0, 1, 1, 1, 1]
+    n = (33, 33, 33)
+    g = O.Grid(n, bc=bc)
+    Ko, faces_o = _two_phase(g, 10.0, [g.nodes(0), g.nodes(1), g.nodes(2)])
+    bo = O.rhs(np.zeros(g.shape), faces_o, g)
+    c = W.random_field(g.shape, 231)
+    uo, _ = O.solve_preconditioned(Ko, bo, g, rtol=1e-13)
+    lo, io = O.adjoint_solve_preconditioned(Ko, c, g, rtol=1e-13)
+    gK_o = O.grad_K(uo, lo, g)
+    p = _plan(n, bc=bc)
+    Kp, faces_p = _two_phase(p, 10.0, [p.nodes(0), p.nodes(1), p.nodes(2)])
+    b = p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"), [_dev(f) for f in faces_p])
+    u, _ = p.solve(_dev(Kp), b, mode=0, rtol=1e-13)
+    dK = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
+    lam, dK, info = p.adjoint_solve(_dev(Kp), _dev(c), u=u, dJdK=dK, mode=0, rtol=1e-13)
+    assert _rel(lam.cpu().numpy(), lo) < 1e-9, (info, io["iterations"])
+    assert _rel(dK.cpu().numpy(), gK_o) < 1e-8

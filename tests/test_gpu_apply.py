@@ -235,9 +235,10 @@ def test_apply_full_size_sampled(nn):
 
 
 def test_autotuner_picks_a_route_and_caches(tmp_path):
-    """The autotuner times every route an axis allows (FP32 includes the
-    tensor-core route), records the decision, reuses it from the cache file,
-    and the tuned plan still matches the oracle."""
+    """The autotuner times every route an axis allows, each with line tiles
+    of 8 and 16 lines (FP32 also the tensor-core route), records the (route,
+    tile) decision, reuses it from the cache file, and the tuned plan still
+    matches the oracle."""
     import paper_2606_21410_b300 as P
     cache = str(tmp_path / "routes.txt")
     n = (65, 33, 12)
@@ -247,12 +248,37 @@ def test_autotuner_picks_a_route_and_caches(tmp_path):
     assert all(x in ("transform", "dense") for x in r["fp64"])
     assert all(x in ("transform", "dense", "tensor") for x in r["fp32"])
     lines = open(cache).read().splitlines()
-    assert len(lines) == 4                                       # 65 and 33, two precisions
+    assert len(lines) == 6        # 65, 33 and 12 (dense with 8- or 16-line tiles), two precisions
+    assert all(r[k][a] in (8, 16) for k in ("tile64", "tile32") for a in range(3))
     r2 = P.Plan(n).autotune(cache)
-    assert r2 == r and len(open(cache).read().splitlines()) == 4
+    assert r2 == r and len(open(cache).read().splitlines()) == 6
     g = O.Grid(n)
     u = W.random_field(g.shape, 71)
     K = W.random_positive_field(g.shape, 72)
     got = p.apply(_dev(K), _dev(u)).cpu().numpy()
     ref = O.apply(u, K, g)
     assert _rel(got, ref) < TOL[torch.float64], _rel(got, ref)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n", [(17, 9, 33), (12, 7, 10), (65, 33, 9)])
+def test_line_tiles_of_8_and_16_agree_bitwise(n, dtype):
+    """The line tile (8 or 16 lines per CTA) only changes which CTA computes a
+    line, not the arithmetic of any line: the operator apply, its adjoint and
+    the Jacobian action are bit-identical for both tiles, on the transform
+    route (power-of-two N) and the dense route (other N), ragged tiles included."""
+    import paper_2606_21410_b300 as P
+    bc = [0, 1, 2, 1, 0, 2]
+    p = _plan(n, bc=bc)
+    u = _dev(W.random_field(p.shape, 701), dtype)
+    K = _dev(W.random_positive_field(p.shape, 702), dtype)
+    C = [_dev(W.random_field(p.shape, 703 + a), dtype) for a in range(3)]
+    prec = P.FP64 if dtype == torch.float64 else P.FP32
+    res = {}
+    for lines in (16, 8):
+        for a in range(3):
+            p.set_tile(a, prec, lines)
+            assert p.tile(a, prec) == lines
+        res[lines] = [p.apply(K, u).cpu(), p.adjoint_apply(K, u).cpu(), p.jacobian_apply(K, C, u).cpu()]
+    for x16, x8 in zip(res[16], res[8]):
+        assert torch.equal(x16, x8)

@@ -86,3 +86,27 @@ def test_picard_batch_of_uneven_lognormal_instances():
         us, _, its1, _ = p.picard_solve(K0[i], b[i], beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1,
                                         rtol=1e-12)
         assert _rel(u[i].cpu().numpy(), us.cpu().numpy()) < 1e-9
+
+
+def test_picard_batch_each_instance_matches_oracle():
+    """A batch of small uneven instances (both line routes, lognormal K0,
+    K = K0 (1 + 0.5 |grad u|^2)) solved concurrently by cheb_picard_batched:
+    every instance against the oracle's relaxed Picard iteration."""
+    import paper_2606_21410_b300 as P
+    sizes = [(9, 9, 9), (11, 11, 11), (13, 9, 11), (9, 13, 7)]
+    items = [_instance(n, 300 + i) for i, n in enumerate(sizes)]
+    plans = [it[0] for it in items]
+    K0 = [_dev(it[1]) for it in items]
+    b = [it[2] for it in items]
+    u, infos, its = P.picard_batched(plans, K0, b, beta=0.5, tol=1e-12, maxit=100, omega=0.5, mode=1,
+                                     rtol=1e-13)
+    for i, n in enumerate(sizes):
+        assert infos[i]["status"] == 0, (n, infos[i], its[i])
+        g = O.Grid(n, bc=BC4)
+        X, Y, Z = g.mesh()
+        K0o = W.lognormal_conductivity(X, Y, Z, seed=300 + i)
+        faces = W.face_values(BC4, g.nodes(0), g.nodes(1), g.nodes(2),
+                              lambda X, Y, Z: (X, (np.ones_like(X), 0 * X, 0 * X), 0 * X))
+        bo = O.rhs(np.zeros(g.shape), faces, g)
+        uo, io = O.picard_solve(K0o, bo, g, tol=1e-13, maxit=100, omega=0.5)
+        assert _rel(u[i].cpu().numpy(), uo) < 1e-9, (n, its[i], io["iterations"])

@@ -105,3 +105,27 @@ def test_hierarchy_spheres_matches_oracle():
         # e_ref differences of solutions that agree to 1e-10 relative
         assert abs(eref[lvl] - eref_o[lvl]) <= 1e-8 * eref_o[lvl], (lvl, eref[lvl], eref_o[lvl])
     assert eref[2] < 0.5
+
+
+def test_repeated_fp64_hierarchies_on_the_same_plans():
+    """Regression: the prolongation's intermediate arrays (after the x and y
+    passes) must fit their scratch; an undersized scratch wrote past its end
+    and broke later FP64 solves on the fine plan.  Two FP64 hierarchies at
+    different tolerances on the same plans, then a solve on the fine plan,
+    all converge and agree with a fresh plan."""
+    import paper_2606_21410_b300 as P
+    bc = [0, 0, 1, 1, 1, 1]
+    plans = [P.Plan((n,) * 3, bc=bc) for n in (33, 65, 129)]
+    pf = plans[-1]
+    X, Y, Z = pf.mesh()
+    K = _dev(W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 10.0))
+    faces = W.face_values(bc, pf.nodes(0), pf.nodes(1), pf.nodes(2),
+                          lambda X, Y, Z: (X, (np.ones_like(X), 0 * X, 0 * X), 0 * X))
+    b = pf.rhs(_dev(np.zeros(pf.shape)), [_dev(f) for f in faces])
+    for rtol in (1e-12, 1e-11):
+        u, infos, _ = P.solve_hierarchy_fine(plans, K, b, mode=0, rtol=rtol)
+        assert all(i["status"] == 0 for i in infos), infos
+    u2, info = pf.solve(K, b, mode=0, rtol=1e-12)
+    assert info["status"] == 0 and info["iterations"] < 200, info
+    u3, _ = P.Plan((129,) * 3, bc=bc).solve(K, b, mode=0, rtol=1e-12)
+    assert _rel(u2.cpu().numpy(), u3.cpu().numpy()) < 1e-10

@@ -272,3 +272,47 @@ def test_graph_captured_cycles_match_stepwise(mode):
     lam0, _, _ = p.adjoint_solve(K, b, mode=mode, rtol=1e-12)
     lam1, _, _ = p.adjoint_solve(K, b, mode=mode, rtol=1e-12, use_graph=1)
     assert _rel(lam1.cpu().numpy(), lam0.cpu().numpy()) < 1e-11
+
+
+@pytest.mark.parametrize("bc", [[0, 0, 1, 1, 1, 1], [0, 0, 0, 0, 0, 0], [0, 2, 1, 2, 0, 1]])
+@pytest.mark.parametrize("precond", [0, 2])
+def test_elimination_formulation_matches_oracle(bc, precond):
+    """The paper's formulation (Sec. 2.3.1): boundary unknowns eliminated,
+    LGMRES on the reduced interior system; same discrete solution as the
+    row-replaced system and as the oracle's dense elimination."""
+    import paper_2606_21410_b300 as P
+    n = (9, 13, 11)
+    g = O.Grid(n, bc=bc)
+    p = _plan(n, bc=bc)
+    X, Y, Z = g.mesh()
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0, 0.2, 0.4, 0.2), 1.0, 10.0)
+    f = W.random_field(g.shape, 91)
+    shapes = [(11, 13), (11, 13), (11, 9), (11, 9), (13, 9), (13, 9)]
+    faces = [W.random_field(s_, 92 + i) for i, s_ in enumerate(shapes)]
+    ref = O.eliminate_solve(K, f, faces, g)
+    b = p.rhs(_dev(f), [_dev(x) for x in faces])
+    u, info = p.solve(_dev(K), b, mode=0, precond=precond, formulation=P.FORM_ELIMINATE,
+                      rtol=1e-13 if precond == 0 else 1e-12, maxiter=20000, restart=36)
+    assert _rel(u.cpu().numpy(), ref) < (1e-9 if precond == 0 else 1e-10), info
+
+
+def test_elimination_needs_fewer_unpreconditioned_iterations():
+    """Krylov conditioning of the two formulations (Sec. 2.3.1 against row
+    replacement): unpreconditioned LGMRES on the reduced interior system
+    converges in fewer iterations than on the row-replaced system (the
+    reduced matrix is 10-25x better conditioned at N = 4..10), to the same
+    solution."""
+    import paper_2606_21410_b300 as P
+    bc = [0, 0, 1, 1, 1, 1]
+    n = (13, 13, 13)
+    p = _plan(n, bc=bc)
+    X, Y, Z = p.mesh()
+    K = _dev(W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0, 0.2, 0.4, 0.2), 1.0, 10.0))
+    b = _dev(W.random_field(p.shape, 97))
+    kw = dict(mode=0, precond=0, rtol=1e-10, maxiter=20000, restart=36, check_status=False)
+    u_r, i_r = p.solve(K, b, formulation=P.FORM_REPLACE, **kw)
+    u_e, i_e = p.solve(K, b, formulation=P.FORM_ELIMINATE, **kw)
+    assert i_e["status"] == 0, i_e
+    assert i_e["iterations"] < i_r["iterations"], (i_e["iterations"], i_r["iterations"])
+    if i_r["status"] == 0:
+        assert _rel(u_e.cpu().numpy(), u_r.cpu().numpy()) < 1e-6

@@ -202,3 +202,24 @@ def test_tensor_route_mixed_solve_matches_fp64():
     um, im = pm.solve(_dev(K), _dev(b), mode=1, rtol=1e-12)
     assert im["status"] == 0 and im["applies_fp32"] > 0
     assert _rel(um.cpu().numpy(), u64.cpu().numpy()) < 1e-9
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """Failure detection without a fault: a tensor-core CTA waits on a barrier
+    that nothing completes, with a short limit (2^20 SM clocks, about half a
+    millisecond); the wait gives up, the library reports CHEB_ERR_CUDA with
+    the give-up message, the CTA has freed its tensor memory, and the next
+    tensor-core preconditioner call runs and matches the oracle."""
+    import paper_2606_21410_b300 as P
+    lib = P.lib
+    st = lib.cheb_selftest_bounded_wait(1 << 20)
+    assert st == -2
+    assert b"bounded pipeline wait gave up" in lib.cheb_last_error()
+    # the error word was read and cleared: a second self-test reports again
+    assert lib.cheb_selftest_bounded_wait(1 << 20) == -2
+    n, bc = (35, 34, 41), [0, 1, 1, 0, 0, 1]
+    g = O.Grid(n, bc=bc)
+    r = W.random_field(g.shape, 25)
+    ref = FDMPreconditioner(g, 1.1)(r)
+    got = _plan(n, bc).precond_apply(_dev(r, torch.float32), 1.1).double().cpu().numpy()
+    assert _rel(got, ref) < 1e-4

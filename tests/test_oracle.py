@@ -548,6 +548,20 @@ def test_jacobian_action_is_the_derivative_of_the_residual():
     assert np.abs(J - fd).max() < 1e-7 * np.abs(J).max()
 
 
+def test_linearized_apply_is_the_jacobian_at_the_law():
+    """The generic linearised operator evaluated at K = k(T), C_a = k'(T) d_a T
+    is the Jacobian action (itself pinned by central differences above)."""
+    bc = [2, 0, 1, 2, 0, 2]
+    g = O.Grid((5, 6, 7), bc=bc)
+    K0 = W.random_positive_field(g.shape, 75)
+    T = 0.2 * W.random_field(g.shape, 76)
+    dT = W.random_field(g.shape, 77)
+    k, dk = O.reciprocal_law(K0, T, 0.5)
+    C = [dk * O.grad(T, g, a) for a in range(3)]
+    assert np.allclose(O.linearized_apply(dT, k, C, g), O.jacobian_apply(dT, T, K0, 0.5, g), rtol=1e-14,
+                       atol=1e-12)
+
+
 def _golden_table1():
     rows = []
     path = os.path.join(os.path.dirname(__file__), "golden", "table1_nonlinear_heat.txt")
@@ -580,3 +594,18 @@ def test_newton_matches_paper_table1():
         else:
             assert abs(err - err_paper) <= float(tol) * err_paper, (N, err, err_paper)
         prev = (Tn, g)
+
+
+@pytest.mark.parametrize("bc", [[0, 0, 0, 0, 0, 0], [0, 0, 1, 1, 1, 1], [0, 2, 1, 2, 0, 1]])
+def test_elimination_improves_conditioning(bc):
+    """The paper's elimination of the boundary unknowns (Sec. 2.3.1) leaves a
+    reduced interior operator much better conditioned than the row-replaced
+    matrix (boundary rows O(1), interior rows O(N^4)): measured 10-25x at
+    N = 4..10 on the two-phase medium; the pin asks for a factor 5."""
+    for N in (4, 8):
+        g = O.Grid((N + 1,) * 3, bc=bc)
+        X, Y, Z = g.mesh()
+        K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0, 0.2, 0.4, 0.2), 1.0, 10.0)
+        c_rep = np.linalg.cond(O.assemble(K, g))
+        c_eli = np.linalg.cond(O.eliminated_system(K, g))
+        assert c_eli * 5 < c_rep, (N, c_rep, c_eli)
