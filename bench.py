@@ -57,8 +57,12 @@ def parse():
                          "lognormal Picard instances solved concurrently (a secondary line); newton: the "
                          "paper's Table 1 nonlinear problem by hierarchical Newton (a secondary line)")
     ap.add_argument("--use-graph", type=int, default=0)
-    ap.add_argument("--coarse-rtol", type=float, default=0.0,
-                    help="relative tolerance of the hierarchy's coarse levels (0: the same 1e-12)")
+    ap.add_argument("--coarse-rtol", type=float, default=1e-4,
+                    help="relative tolerance of the hierarchy's coarse levels, whose solutions only "
+                         "start the next level (0: the finest level's 1e-12)")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="after the warm-up, run one step between cudaProfilerStart/Stop and exit "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--recycle", type=int, default=0,
                     help="carry LGMRES augmentation vectors across refinement steps (1) or not (0)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-instance batch keys")
@@ -440,7 +444,7 @@ def batch_workload(args):
 
 def workload_config(levels, contrast):
     return {"workload": f"two-phase spheres, hierarchical {'->'.join(f'{n}^3' for n in levels)}, "
-                        f"K_incl/K_matrix={contrast:g}, mixed FP32/FP64, rtol 1e-12",
+                        f"K_incl/K_matrix={contrast:g}, mixed FP32/FP64, finest level to rtol 1e-12",
             "levels": levels, "precond": "FDM (constant-K fast diagonalization)",
             "lgmres": "restart 30, augment 3", "l2": "inputs larger than L2 (257^3 FP64 = 136 MB)"}
 
@@ -484,6 +488,12 @@ def main():
     for _ in range(max(3, args.warmup)):
         us, infos, eref = step()
     torch.cuda.synchronize()
+    if args.ncu_step:
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
 
     def barrier():
         if world > 1:
@@ -709,7 +719,7 @@ def main():
             "warmup": max(3, args.warmup), "ms_per_step": per_step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": dict(workload_config(levels, args.contrast),
-                           coarse_rtol=args.coarse_rtol or 1e-12, recycle=args.recycle,
+                           coarse_levels_rtol=args.coarse_rtol or 1e-12, recycle=args.recycle,
                            inner_rtol=args.inner_rtol),
             "solves_per_s": world * args.steps / elapsed,
             "iterations_per_level": [i["iterations"] for i in infos],
