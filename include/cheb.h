@@ -63,7 +63,8 @@ enum cheb_solve_mode { CHEB_SOLVE_FP64 = 0, CHEB_SOLVE_MIXED = 1 };
  * tensor cores (split-TF32 tcgen05 contractions, FP32-level accuracy);
  * needs a 2-D or 3-D grid, 33 <= n <= 257 on the axis and at least 128
  * lines; the other FP32 line operations of that axis (derivative, adjoint)
- * then use the transform route where it exists, else the dense one. */
+ * then use the power-of-two transform route where it exists, else the
+ * dense one, else the chirp transform. */
 enum cheb_route { CHEB_ROUTE_AUTO = -1, CHEB_ROUTE_TRANSFORM = 0, CHEB_ROUTE_DENSE = 1, CHEB_ROUTE_TENSOR = 2 };
 
 enum cheb_status {
@@ -80,8 +81,12 @@ enum cheb_status {
 /* Create a plan for one grid.
  *   dim      1, 2 or 3 (the first dim axes are active)
  *   n        points per axis, n[a] >= 3 for a < dim, n[a] = 1 otherwise
- *            (route TRANSFORM needs n - 1 a power of two, 4 <= n - 1 <= 256;
- *             route DENSE needs n <= 129; every axis needs one of them)
+ *            (route TRANSFORM needs 2 <= n - 1 <= 256: a power of two n - 1 >= 4
+ *             runs one FFT of length 2(n - 1) per line pair, any other n - 1 the
+ *             chirp form (Bluestein's convolution, FFT length the power of two
+ *             >= 4(n - 1) - 1); route DENSE needs n <= 129.  Without a forced
+ *             route an axis takes the power-of-two transform, else dense, else
+ *             the chirp transform)
  *   lo, hi   interval of each axis (hi > lo); entries of unused axes ignored
  *   bc_type  six CHEB_DIRICHLET / CHEB_NEUMANN / CHEB_FLUX values, faces
  *            x-,x+,y-,y+,z-,z+ (flux faces exclude CHEB_ROUTE_TENSOR)
@@ -326,7 +331,8 @@ int cheb_adjoint_solve(cheb_plan plan, const double* K, const double* u, const d
 /* Modal prolongation (Sec. 2.3.3, Alg. 4): per axis, coarse nodal values
  * -> Chebyshev coefficients (DCT-I), zero-padded to the fine degree, ->
  * fine nodal values (inverse DCT-I).  The fine plan must have N_f = 2 N on
- * every active axis (powers of two, N_f <= 256) and the same box.  u_c:
+ * every active axis (3 <= N, N_f <= 256; CHEB_ERR_UNSUPPORTED otherwise)
+ * and the same box; N not a power of two runs the chirp form.  u_c:
  * coarse device field, u_f: fine device field, both of type prec.  Uses two
  * scratch arrays owned by the fine plan (allocated at the first call). */
 int cheb_prolong(cheb_plan coarse, cheb_plan fine, int prec, const void* u_c, void* u_f);

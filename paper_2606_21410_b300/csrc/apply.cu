@@ -19,344 +19,10 @@
 // Dense route: f' = D f with D staged in shared memory.
 #include <cstdio>
 
-#include "device.cuh"
+#include "line_pass.cuh"
 #include "umma.h"
 
 namespace cheb {
-
-template <typename T>
-struct AxisK {
-  int n, N;
-  T scale;
-  const typename C2<T>::t* tw;  // P twiddles (transform route)
-  const T* D;                   // n x n row-major (dense route)
-};
-
-__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-// Shared-memory layout of a line pass: X (tile), ends (2 x TL x 2),
-// then the route's buffers.
-template <typename T>
-static size_t pass_smem_bytes(int route, int n, int P, int TL) {
-  const int ldx = n | 1;
-  size_t b = align16(sizeof(T) * TL * ldx) + align16(sizeof(T) * TL * 4);
-  if (route == CHEB_ROUTE_TRANSFORM) {
-    b += align16(2 * sizeof(T) * (size_t)(TL / 2) * P) + align16(2 * sizeof(T) * (size_t)P);
-  } else {
-    b += align16(sizeof(T) * TL * ldx) + align16(sizeof(T) * (size_t)n * n);
-  }
-  return b;
-}
-
-// Tile <-> global mapping of element (lane l, point pt).
-struct TileMap {
-  int axis, nx, ny, nz, TL;
-  int line0;      // axis 0: first line of the tile
-  int i0, outer;  // axes 1, 2: first x index, fixed k (axis 1) or j (axis 2)
-  __device__ __forceinline__ bool at(int l, int pt, size_t& gidx, int& i, int& j, int& k) const {
-    if (axis == 0) {
-      const int line = line0 + l;
-      if (line >= ny * nz) return false;
-      i = pt; j = line % ny; k = line / ny;
-      gidx = (size_t)line * nx + pt;
-    } else {
-      i = i0 + l;
-      if (i >= nx) return false;
-      if (axis == 1) { j = pt; k = outer; }
-      else { j = outer; k = pt; }
-      gidx = ((size_t)k * ny + j) * nx + i;
-    }
-    return true;
-  }
-  // element e of the tile in a coalesced enumeration order
-  __device__ __forceinline__ void split(int e, int n, int& l, int& pt) const {
-    if (axis == 0) { l = e / n; pt = e - l * n; }
-    else { pt = e / TL; l = e - pt * TL; }
-  }
-};
-
-// ---------------------------------------------------------------------------
-// per-warp transform derivative of lines 2w, 2w+1 (in place in X)
-// ---------------------------------------------------------------------------
-template <typename T, int P, int CM, bool TRANSPOSE>
-__device__ __forceinline__ void warp_deriv_tf(T* X, int ldx, typename C2<T>::t* buf,
-                                              const typename C2<T>::t* tw, int N, T scale,
-                                              int w, int lane) {
-  typedef typename C2<T>::t C;
-  T* xa = X + (2 * w) * ldx;
-  T* xb = X + (2 * w + 1) * ldx;
-  const T invN = (T)1 / (T)N;
-  // weight m_j of the DCT-I matrix columns: 1 at the ends, 2 inside
-  auto pack = [&](bool divide_m) {
-    for (int j = lane; j < P; j += 32) {
-      const int jj = j <= N ? j : P - j;
-      C v;
-      v.x = xa[jj];
-      v.y = xb[jj];
-      if (divide_m && jj != 0 && jj != N) { v.x *= (T)0.5; v.y *= (T)0.5; }
-      buf[fpad(j)] = v;
-    }
-    __syncwarp();
-  };
-  auto weight = [&](int k) -> T {  // w_k = k c_k scale / N
-    T wk = (T)k * scale * invN;
-    return k == N ? (T)0.5 * wk : wk;
-  };
-  if (!TRANSPOSE) {
-    pack(false);
-    warp_fft<T, P>(buf, tw, lane);
-    for (int k = lane; k <= N; k += 32) {
-      const T wk = weight(k);
-      const C F = buf[fpad(k)];
-      xa[k] = wk * F.x;
-      xb[k] = wk * F.y;
-    }
-    __syncwarp();
-    warp_parity_scan<T, CM, true>(xa, N, lane);
-    warp_parity_scan<T, CM, true>(xb, N, lane);
-    pack(false);
-    warp_fft<T, P>(buf, tw, lane);
-    for (int k = lane; k <= N; k += 32) {
-      const C F = buf[fpad(k)];
-      xa[k] = F.x;
-      xb[k] = F.y;
-    }
-    __syncwarp();
-  } else {
-    // D^T = diag(m) M diag(1/m) W S^T diag(m) M diag(1/m), M = DCT-I matrix,
-    // S^T the exclusive parity prefix scan.
-    pack(true);
-    warp_fft<T, P>(buf, tw, lane);
-    for (int k = lane; k <= N; k += 32) {
-      const T mk = (k == 0 || k == N) ? (T)1 : (T)2;
-      const C F = buf[fpad(k)];
-      xa[k] = mk * F.x;
-      xb[k] = mk * F.y;
-    }
-    __syncwarp();
-    warp_parity_scan<T, CM, false>(xa, N, lane);
-    warp_parity_scan<T, CM, false>(xb, N, lane);
-    for (int k = lane; k <= N; k += 32) {
-      const T wk = weight(k);
-      xa[k] *= wk;
-      xb[k] *= wk;
-    }
-    __syncwarp();
-    pack(true);
-    warp_fft<T, P>(buf, tw, lane);
-    for (int k = lane; k <= N; k += 32) {
-      const T mk = (k == 0 || k == N) ? (T)1 : (T)2;
-      const C F = buf[fpad(k)];
-      xa[k] = mk * F.x;
-      xb[k] = mk * F.y;
-    }
-    __syncwarp();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// block-wide dense derivative X <- D X (or D^T X), tile lines as rows
-// ---------------------------------------------------------------------------
-template <typename T, bool TRANSPOSE, int TL>
-__device__ __forceinline__ void block_deriv_dense(T* X, T* tmp, int ldx, const T* Dm, int n) {
-  constexpr int G = 4;                  // lines per work item
-  const int items = n * (TL / G);
-  for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int i = it % n;
-    const int l0 = (it / n) * G;
-    T acc[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) acc[g] = (T)0;
-    for (int m = 0; m < n; ++m) {
-      const T d = TRANSPOSE ? Dm[m * n + i] : Dm[i * n + m];
-#pragma unroll
-      for (int g = 0; g < G; ++g) acc[g] += d * X[(l0 + g) * ldx + m];
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) tmp[(l0 + g) * ldx + i] = acc[g];
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < TL * ldx; e += blockDim.x) X[e] = tmp[e];
-  __syncthreads();
-}
-
-template <typename T, int ROUTE, int P, int CM, bool TRANSPOSE, int TL>
-__device__ __forceinline__ void tile_deriv(T* X, T* tmp, int ldx, typename C2<T>::t* Cb,
-                                           const typename C2<T>::t* tw, const T* Dm, int n,
-                                           T scale) {
-  if constexpr (ROUTE == CHEB_ROUTE_TRANSFORM) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    warp_deriv_tf<T, P, CM, TRANSPOSE>(X, ldx, Cb + (size_t)w * P, tw, n - 1, scale, w, lane);
-    __syncthreads();
-  } else {
-    __syncthreads();
-    block_deriv_dense<T, TRANSPOSE, TL>(X, tmp, ldx, Dm, n);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// the line-pass kernel
-// ---------------------------------------------------------------------------
-template <typename T, int ROUTE, int P, int CM, int TL>
-__global__ void __launch_bounds__(TL * 16)
-line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
-                 const T* __restrict__ u, T* __restrict__ out, const T* __restrict__ Cj) {
-  typedef typename C2<T>::t C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = ax.n, N = ax.N;
-  const int ldx = n | 1;
-  unsigned char* p = smem_raw;
-  T* X = (T*)p;            p += align16(sizeof(T) * TL * ldx);
-  T* ends = (T*)p;         p += align16(sizeof(T) * TL * 4);
-  C* Cb = nullptr; C* tw = nullptr; T* tmp = nullptr; T* Dm = nullptr;
-  if (ROUTE == CHEB_ROUTE_TRANSFORM) {
-    Cb = (C*)p;            p += align16(2 * sizeof(T) * (size_t)(TL / 2) * P);
-    tw = (C*)p;
-    for (int t = threadIdx.x; t < P; t += blockDim.x) tw[t] = ax.tw[t];
-  } else {
-    tmp = (T*)p;           p += align16(sizeof(T) * TL * ldx);
-    Dm = (T*)p;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Dm[t] = ax.D[t];
-  }
-
-  TileMap map;
-  map.axis = axis; map.nx = g.n[0]; map.ny = g.n[1]; map.nz = g.n[2]; map.TL = TL;
-  if (axis == 0) {
-    map.line0 = blockIdx.x * TL; map.i0 = 0; map.outer = 0;
-  } else {
-    const int nbx = (g.n[0] + TL - 1) / TL;
-    map.line0 = 0;
-    map.i0 = (blockIdx.x % nbx) * TL;
-    map.outer = blockIdx.x / nbx;
-  }
-  const int tile_elems = TL * n;
-
-  // load the input tile (u, or lambda for the adjoint)
-  for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-    int l, pt; map.split(e, n, l, pt);
-    size_t gi; int i, j, k;
-    T v = (T)0;
-    if (map.at(l, pt, gi, i, j, k)) v = u[gi];
-    X[l * ldx + pt] = v;
-  }
-  __syncthreads();
-
-  const bool adj = (kind == kAdjFirst || kind == kAdjAcc);
-  if (kind == kDeriv || kind == kDerivT) {
-    if (kind == kDeriv) tile_deriv<T, ROUTE, P, CM, false, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    else tile_deriv<T, ROUTE, P, CM, true, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-      int l, pt; map.split(e, n, l, pt);
-      size_t gi; int i, j, k;
-      if (map.at(l, pt, gi, i, j, k)) out[gi] = X[l * ldx + pt];
-    }
-    return;
-  }
-
-  if (!adj) {
-    // ---- A u (or the Jacobian action): D_a u, keep line-end derivatives for
-    // Neumann rows; after the product q = K D_a u (+ C u) keep its line-end
-    // values for flux rows (-s q at the owner face)
-    tile_deriv<T, ROUTE, P, CM, false, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    if (threadIdx.x < TL) {
-      ends[threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
-      ends[threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-      int l, pt; map.split(e, n, l, pt);
-      size_t gi; int i, j, k;
-      if (map.at(l, pt, gi, i, j, k)) {
-        T q = X[l * ldx + pt] * K[gi];
-        if (Cj) q += Cj[gi] * u[gi];
-        X[l * ldx + pt] = q;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < TL) {
-      ends[2 * TL + threadIdx.x * 2 + 0] = X[threadIdx.x * ldx + 0];
-      ends[2 * TL + threadIdx.x * 2 + 1] = X[threadIdx.x * ldx + N];
-    }
-    tile_deriv<T, ROUTE, P, CM, false, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    const bool first = (kind == kApplyFirst || kind == kJacFirst);
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-      int l, pt; map.split(e, n, l, pt);
-      size_t gi; int i, j, k;
-      if (!map.at(l, pt, gi, i, j, k)) continue;
-      const int o = owner_face(g, i, j, k);
-      if (o < 0) {
-        const T v = -X[l * ldx + pt];
-        if (first) out[gi] = v;
-        else out[gi] += v;
-      } else if (g.bc[o] == CHEB_DIRICHLET) {
-        if (first) out[gi] = u[gi];
-      } else if ((o >> 1) == axis) {
-        // hi face (side 1) is line point 0, lo face (side 0) is point N
-        if (g.bc[o] == CHEB_FLUX)
-          out[gi] = (o & 1) ? -ends[2 * TL + l * 2 + 0] : ends[2 * TL + l * 2 + 1];
-        else
-          out[gi] = (o & 1) ? ends[l * 2 + 0] : -ends[l * 2 + 1];
-      } else if (first) {
-        out[gi] = (T)0;  // Neumann / flux row of a later axis: written by that pass
-      }
-    }
-  } else {
-    // ---- A^T lam for this axis: D_a^T (S_a lam - K * D_a^T (P_int lam))
-    // S_a lam: +-lam at line ends owned by a Neumann face of this axis,
-    // -+K lam at ends owned by a flux face.
-    if (threadIdx.x < TL) {
-      const int l = threadIdx.x;
-      size_t gi; int i, j, k;
-      T s0 = (T)0, sN = (T)0;
-      if (map.at(l, 0, gi, i, j, k)) {
-        const int o = owner_face(g, i, j, k);
-        if (o == 2 * axis + 1 && g.bc[o] == CHEB_NEUMANN) s0 = X[l * ldx + 0];
-        if (o == 2 * axis + 1 && g.bc[o] == CHEB_FLUX) s0 = -K[gi] * X[l * ldx + 0];
-      }
-      if (map.at(l, N, gi, i, j, k)) {
-        const int o = owner_face(g, i, j, k);
-        if (o == 2 * axis && g.bc[o] == CHEB_NEUMANN) sN = -X[l * ldx + N];
-        if (o == 2 * axis && g.bc[o] == CHEB_FLUX) sN = K[gi] * X[l * ldx + N];
-      }
-      ends[l * 2 + 0] = s0;
-      ends[l * 2 + 1] = sN;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-      int l, pt; map.split(e, n, l, pt);
-      size_t gi; int i, j, k;
-      if (map.at(l, pt, gi, i, j, k) && owner_face(g, i, j, k) >= 0) X[l * ldx + pt] = (T)0;
-    }
-    tile_deriv<T, ROUTE, P, CM, true, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-      int l, pt; map.split(e, n, l, pt);
-      size_t gi; int i, j, k;
-      T v = (T)0;
-      if (map.at(l, pt, gi, i, j, k)) {
-        v = -K[gi] * X[l * ldx + pt];
-        if (pt == 0) v += ends[l * 2 + 0];
-        if (pt == N) v += ends[l * 2 + 1];
-      }
-      X[l * ldx + pt] = v;
-    }
-    tile_deriv<T, ROUTE, P, CM, true, TL>(X, tmp, ldx, Cb, tw, Dm, n, ax.scale);
-    const bool first = (kind == kAdjFirst);
-    for (int e = threadIdx.x; e < tile_elems; e += blockDim.x) {
-      int l, pt; map.split(e, n, l, pt);
-      size_t gi; int i, j, k;
-      if (!map.at(l, pt, gi, i, j, k)) continue;
-      T v = X[l * ldx + pt];
-      if (first) {
-        const int o = owner_face(g, i, j, k);
-        if (o >= 0 && g.bc[o] == CHEB_DIRICHLET) v += u[gi];
-        out[gi] = v;
-      } else {
-        out[gi] += v;
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // transform-route pass with compile-time N: tiles staged by cp.async (u, then
@@ -612,10 +278,15 @@ tf_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
 // ---------------------------------------------------------------------------
 template <typename T> static AxisK<T> axis_k(const AxisTables& t);
 template <> AxisK<double> axis_k<double>(const AxisTables& t) {
-  AxisK<double> a; a.n = t.n; a.N = t.N; a.scale = t.scale; a.tw = t.tw64; a.D = t.D64; return a;
+  AxisK<double> a;
+  a.n = t.n; a.N = t.N; a.scale = t.scale; a.tw = t.tw64; a.chirp = t.chirp64; a.bhat = t.bhat64; a.D = t.D64;
+  return a;
 }
 template <> AxisK<float> axis_k<float>(const AxisTables& t) {
-  AxisK<float> a; a.n = t.n; a.N = t.N; a.scale = (float)t.scale; a.tw = t.tw32; a.D = t.D32; return a;
+  AxisK<float> a;
+  a.n = t.n; a.N = t.N; a.scale = (float)t.scale; a.tw = t.tw32; a.chirp = t.chirp32; a.bhat = t.bhat32;
+  a.D = t.D32;
+  return a;
 }
 
 template <typename T, int ROUTE, int P, int CM, int TL>
@@ -653,6 +324,7 @@ static int dispatch_pass(const cheb_plan_s* p, int axis, int kind, int route, co
   if (nblocks == 0) return CHEB_OK;
   if (route == CHEB_ROUTE_DENSE)
     return launch_kernel<T, CHEB_ROUTE_DENSE, 0, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
+  if (t.chirp) return launch_chirp_pass<T>(g, axis, kind, ak, t.P, K, u, out, s, C);
   switch (t.P) {
     case 8: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 8, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
     case 16: return launch_kernel<T, CHEB_ROUTE_TRANSFORM, 16, 1, TL>(g, axis, kind, ak, K, u, out, s, nblocks, C);
@@ -677,7 +349,7 @@ int launch_pass(const cheb_plan_s* p, int axis, int kind, const T* K, const T* u
       if (kind == kApplyFirst || kind == kApplyAcc)
         return tensor_apply_pass(p, axis, kind == kApplyFirst, K, u, out, s);
     }
-    route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+    route = line_route(t);
   }
   const int tile = sizeof(T) == 4 ? t.tile32 : t.tile;
   if (tile == 8) return dispatch_pass<T, 8>(p, axis, kind, route, K, u, out, s, C);

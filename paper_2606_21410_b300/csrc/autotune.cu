@@ -92,7 +92,8 @@ std::vector<Cand> candidates(const cheb_plan_s* p, int a) {
   std::vector<Cand> c;
   const AxisTables& t = p->ax[a];
   for (int tile : {16, 8}) {
-    if (t.transform_ok) c.push_back({CHEB_ROUTE_TRANSFORM, tile});
+    // the chirp form of the transform route always runs 8-line tiles
+    if (t.transform_ok && (!t.chirp || tile == 8)) c.push_back({CHEB_ROUTE_TRANSFORM, tile});
     if (t.dense_ok) c.push_back({CHEB_ROUTE_DENSE, tile});
   }
   if (sizeof(T) == 4 && tensor_route_ok(p, a)) c.push_back({CHEB_ROUTE_TENSOR, 16});

@@ -174,6 +174,51 @@ __device__ __forceinline__ void warp_fft(typename C2<T>::t* buf, const typename 
 }
 
 // ---------------------------------------------------------------------------
+// DFT of any length M by Bluestein's chirp-z identity (L. I. Bluestein, "A
+// linear filtering approach to the computation of the discrete Fourier
+// transform", 1970).  With c_j = exp(-i pi j^2 / M), jk = (j^2 + k^2 -
+// (k - j)^2) / 2 gives
+//   X_k = sum_{j<M} x_j exp(-2 pi i jk / M) = c_k sum_{j<M} (x_j c_j) conj(c_{k-j}),
+// a circular convolution of length L (a power of two, L >= 2M - 1, so the
+// wrapped kernel b_m = conj(c_|m|), |m| < M, does not alias).  It is
+// evaluated with two length-L warp FFTs: FFT(conj(A * B)) = L conj(IFFT(A * B)).
+// bhat = FFT_L(b) / L is a plan table; chirp holds c_j for j < M.
+// On entry buf[fpad(j)] holds x_j for j < M (later entries are ignored); on
+// exit buf[fpad(k)] holds X_k for k < M.
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__device__ __noinline__ void warp_dft_chirp(typename C2<T>::t* buf, const typename C2<T>::t* tw,
+                                               const typename C2<T>::t* chirp,
+                                               const typename C2<T>::t* bhat, int M, int lane) {
+  typedef typename C2<T>::t C;
+  for (int j = lane; j < L; j += 32) {
+    C v;
+    if (j < M) {
+      v = cmul(buf[fpad(j)], chirp[j]);
+    } else {
+      v.x = (T)0;
+      v.y = (T)0;
+    }
+    buf[fpad(j)] = v;
+  }
+  __syncwarp();
+  warp_fft<T, L>(buf, tw, lane);
+  for (int k = lane; k < L; k += 32) {
+    C v = cmul(buf[fpad(k)], bhat[k]);
+    v.y = -v.y;
+    buf[fpad(k)] = v;
+  }
+  __syncwarp();
+  warp_fft<T, L>(buf, tw, lane);
+  for (int k = lane; k < M; k += 32) {
+    C v = buf[fpad(k)];
+    v.y = -v.y;
+    buf[fpad(k)] = cmul(chirp[k], v);
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
 // Parity-interleaved scans on one line x[0..N] held in shared memory, by one
 // warp.  SUFFIX: x_k <- sum_{j > k, j - k odd} x_j for k < N, x_N <- 0
 // (the backward derivative recurrence in closed form).  PREFIX (its

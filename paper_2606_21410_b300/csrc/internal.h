@@ -21,7 +21,8 @@ constexpr int kTransformMaxN = 256;
 struct AxisTables {
   int n = 1;           // points
   int N = 0;           // n - 1
-  int P = 0;           // FFT length 2N (transform route), 0 otherwise
+  int P = 0;           // warp FFT length of the transform route: 2N, or for the chirp
+                       // form the power of two >= 4N - 1 (at least 8)
   double scale = 1.0;  // 2 / (hi - lo)
   int route = CHEB_ROUTE_TRANSFORM;    // FP64 passes
   int route32 = CHEB_ROUTE_TRANSFORM;  // FP32 passes
@@ -29,12 +30,25 @@ struct AxisTables {
   int tile32 = 16;                     // same for the FP32 line passes
   bool transform_ok = false;
   bool dense_ok = false;
-  double2* tw64 = nullptr;
+  bool chirp = false;  // transform route by Bluestein's convolution (N not a power of two, or N < 4)
+  double2* tw64 = nullptr;  // stage twiddles of the length-P warp FFT
   float2* tw32 = nullptr;
+  double2* chirp64 = nullptr;  // chirp route: c_j = exp(-i pi j^2 / 2N), j < 2N
+  float2* chirp32 = nullptr;
+  double2* bhat64 = nullptr;   // chirp route: FFT_P of the wrapped conj(c) kernel, / P
+  float2* bhat32 = nullptr;
   double* D64 = nullptr;   // row-major D (n x n)
   float* D32 = nullptr;
   double* cc64 = nullptr;  // Clenshaw-Curtis weights of the axis (n, physical length)
 };
+
+// Line route of an axis when the requested one does not apply (tensor route
+// for pass kinds it does not cover): the power-of-two transform, else dense
+// where the size allows it, else the chirp transform.
+inline int line_route(const AxisTables& t) {
+  if (t.transform_ok && !t.chirp) return CHEB_ROUTE_TRANSFORM;
+  return t.dense_ok ? CHEB_ROUTE_DENSE : CHEB_ROUTE_TRANSFORM;
+}
 
 // Geometry passed by value to kernels.
 struct Geom {

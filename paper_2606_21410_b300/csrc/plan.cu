@@ -1,5 +1,6 @@
 // Plan creation and the plain entry points: nodes, routes, derivative line
 // passes, operator apply (forward and transposed), right-hand side.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -113,6 +114,50 @@ void prof_end(int cat, cudaStream_t s) {
 }
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Tables of the chirp-form DFT of length M = 2N with convolution length L
+// (Bluestein): c_j = exp(-i pi j^2 / M), j < M, with j^2 reduced mod 2M
+// before the angle is formed; bhat = FFT_L(b) / L, b_m = conj(c_m) at
+// m and L - m for 0 <= m < M, zero elsewhere.  Evaluated in long double, the
+// transform by direct summation over the 2M - 1 non-zero b_m with the
+// exponent m k reduced mod L.
+static void chirp_tables(int N, int L, std::vector<double2>& c, std::vector<double2>& bhat) {
+  const int M = 2 * N;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> cr(M), ci(M);
+  for (int j = 0; j < M; ++j) {
+    const long long r = ((long long)j * j) % (2LL * M);
+    const long double ang = -pi * (long double)r / (long double)M;
+    cr[j] = cosl(ang);
+    ci[j] = sinl(ang);
+  }
+  std::vector<long double> wr(L), wi(L);  // exp(-2 pi i q / L)
+  for (int q = 0; q < L; ++q) {
+    const long double ang = -2.0L * pi * (long double)q / (long double)L;
+    wr[q] = cosl(ang);
+    wi[q] = sinl(ang);
+  }
+  c.resize(M);
+  for (int j = 0; j < M; ++j) c[j] = make_double2((double)cr[j], (double)ci[j]);
+  bhat.resize(L);
+  for (int k = 0; k < L; ++k) {
+    long double ar = 0, ai = 0;
+    for (int m = -(M - 1); m <= M - 1; ++m) {
+      const int am = m < 0 ? -m : m;
+      const int idx = (m + L) % L;                         // position of b_m
+      const long double br = cr[am], bi = -ci[am];         // conj(c_|m|)
+      const int q = (int)(((long long)idx * k) % L);
+      ar += br * wr[q] - bi * wi[q];
+      ai += br * wi[q] + bi * wr[q];
+    }
+    bhat[k] = make_double2((double)(ar / L), (double)(ai / L));
+  }
+}
 
 // Reference CGL coordinate x_j = cos(pi j / N), evaluated as
 // sin(pi (N - 2j) / (2N)) (same value; exactly antisymmetric).
@@ -123,12 +168,13 @@ static int build_axis(cheb_plan_s* p, int a) {
   t.n = p->n[a];
   t.N = t.n - 1;
   t.scale = 2.0 / (p->hi[a] - p->lo[a]);
-  t.transform_ok = is_pow2(t.N) && t.N >= 4 && t.N <= kTransformMaxN;
+  t.transform_ok = t.N >= 2 && t.N <= kTransformMaxN;
+  t.chirp = !(is_pow2(t.N) && t.N >= 4);
   t.dense_ok = t.n <= kDenseMaxN;
-  t.route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  t.route = line_route(t);
   t.route32 = t.route;
   if (t.transform_ok) {
-    t.P = 2 * t.N;
+    t.P = t.chirp ? std::max(8, next_pow2(4 * t.N - 1)) : 2 * t.N;
     // per-stage twiddles of the warp FFT (radix 8, then 4 or 2):
     // stage with span Ns and radix R stores exp(-2 pi i r k / (Ns R)) at
     // (Ns - 1) + (r - 1) Ns + k, r = 1..R-1, k < Ns
@@ -150,6 +196,21 @@ static int build_axis(cheb_plan_s* p, int a) {
     CHEB_CUDA(cudaMalloc(&t.tw32, sizeof(float2) * t.P));
     CHEB_CUDA(cudaMemcpy(t.tw64, tw64.data(), sizeof(double2) * t.P, cudaMemcpyHostToDevice));
     CHEB_CUDA(cudaMemcpy(t.tw32, tw32.data(), sizeof(float2) * t.P, cudaMemcpyHostToDevice));
+    if (t.chirp) {
+      std::vector<double2> c64, b64;
+      chirp_tables(t.N, t.P, c64, b64);
+      std::vector<float2> c32(c64.size()), b32(b64.size());
+      for (size_t i = 0; i < c64.size(); ++i) c32[i] = make_float2((float)c64[i].x, (float)c64[i].y);
+      for (size_t i = 0; i < b64.size(); ++i) b32[i] = make_float2((float)b64[i].x, (float)b64[i].y);
+      CHEB_CUDA(cudaMalloc(&t.chirp64, sizeof(double2) * c64.size()));
+      CHEB_CUDA(cudaMalloc(&t.chirp32, sizeof(float2) * c32.size()));
+      CHEB_CUDA(cudaMalloc(&t.bhat64, sizeof(double2) * b64.size()));
+      CHEB_CUDA(cudaMalloc(&t.bhat32, sizeof(float2) * b32.size()));
+      CHEB_CUDA(cudaMemcpy(t.chirp64, c64.data(), sizeof(double2) * c64.size(), cudaMemcpyHostToDevice));
+      CHEB_CUDA(cudaMemcpy(t.chirp32, c32.data(), sizeof(float2) * c32.size(), cudaMemcpyHostToDevice));
+      CHEB_CUDA(cudaMemcpy(t.bhat64, b64.data(), sizeof(double2) * b64.size(), cudaMemcpyHostToDevice));
+      CHEB_CUDA(cudaMemcpy(t.bhat32, b32.data(), sizeof(float2) * b32.size(), cudaMemcpyHostToDevice));
+    }
   }
   if (t.dense_ok) {
     std::vector<double> D = dense_deriv_matrix(t.N, t.scale);
@@ -174,7 +235,9 @@ static int build_axis(cheb_plan_s* p, int a) {
 
 static void free_axis(AxisTables& t) {
   cudaFree(t.tw64); cudaFree(t.tw32); cudaFree(t.D64); cudaFree(t.D32); cudaFree(t.cc64);
+  cudaFree(t.chirp64); cudaFree(t.chirp32); cudaFree(t.bhat64); cudaFree(t.bhat32);
   t.tw64 = nullptr; t.tw32 = nullptr; t.D64 = nullptr; t.D32 = nullptr; t.cc64 = nullptr;
+  t.chirp64 = nullptr; t.chirp32 = nullptr; t.bhat64 = nullptr; t.bhat32 = nullptr;
 }
 
 }  // namespace cheb
@@ -273,9 +336,9 @@ int cheb_plan_set_stream(cheb_plan p, void* stream) {
 int cheb_plan_set_route(cheb_plan p, int axis, int route) {
   if (!p || axis < 0 || axis >= p->dim) { set_error("bad plan or axis"); return CHEB_ERR_ARG; }
   AxisTables& t = p->ax[axis];
-  if (route == CHEB_ROUTE_AUTO) route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  if (route == CHEB_ROUTE_AUTO) route = line_route(t);
   if (route == CHEB_ROUTE_TRANSFORM && !t.transform_ok) {
-    set_error("transform route needs n - 1 a power of two in [4, 256]"); return CHEB_ERR_UNSUPPORTED;
+    set_error("transform route needs 2 <= n - 1 <= 256"); return CHEB_ERR_UNSUPPORTED;
   }
   if (route == CHEB_ROUTE_DENSE && !t.dense_ok) {
     set_error("dense route needs n <= 129"); return CHEB_ERR_UNSUPPORTED;
@@ -291,9 +354,9 @@ int cheb_plan_set_route(cheb_plan p, int axis, int route) {
 int cheb_plan_set_route32(cheb_plan p, int axis, int route) {
   if (!p || axis < 0 || axis >= p->dim) { set_error("bad plan or axis"); return CHEB_ERR_ARG; }
   AxisTables& t = p->ax[axis];
-  if (route == CHEB_ROUTE_AUTO) route = t.transform_ok ? CHEB_ROUTE_TRANSFORM : CHEB_ROUTE_DENSE;
+  if (route == CHEB_ROUTE_AUTO) route = line_route(t);
   if (route == CHEB_ROUTE_TRANSFORM && !t.transform_ok) {
-    set_error("transform route needs n - 1 a power of two in [4, 256]"); return CHEB_ERR_UNSUPPORTED;
+    set_error("transform route needs 2 <= n - 1 <= 256"); return CHEB_ERR_UNSUPPORTED;
   }
   if (route == CHEB_ROUTE_DENSE && !t.dense_ok) {
     set_error("dense route needs n <= 129"); return CHEB_ERR_UNSUPPORTED;
