@@ -57,6 +57,8 @@ def parse():
                          "lognormal Picard instances solved concurrently (a secondary line); newton: the "
                          "paper's Table 1 nonlinear problem by hierarchical Newton (a secondary line)")
     ap.add_argument("--use-graph", type=int, default=0)
+    ap.add_argument("--batch-mode", type=int, default=1, choices=[1, 2],
+                    help="--workload batch: 1 lockstep, 2 one concurrent solver per instance")
     ap.add_argument("--coarse-rtol", type=float, default=1e-4,
                     help="relative tolerance of the hierarchy's coarse levels, whose solutions only "
                          "start the next level (0: the finest level's 1e-12)")
@@ -350,7 +352,7 @@ def apply_only(args, n):
     print(json.dumps(rec), flush=True)
 
 
-def batch_run(steps=1, warmup=1, use_graph=0):
+def batch_run(steps=1, warmup=1, use_graph=0, batch_mode=1):
     """The batched configuration: 16 instances, sizes U{33..97} (seed 1),
     K = K0 (1 + 0.5 |grad u|^2) with lognormal K0 (sigma 0.5, correlation 0.2),
     Dirichlet u = x on x = +-1 and z = -1, Neumann 0 elsewhere; relaxed Picard
@@ -370,7 +372,8 @@ def batch_run(steps=1, warmup=1, use_graph=0):
         bs.append(p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"),
                         [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in faces]))
         plans.append(p)
-    kw = dict(beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1, rtol=1e-10, use_graph=use_graph)
+    kw = dict(beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1, rtol=1e-10, use_graph=use_graph,
+              batch_mode=batch_mode)
     for _ in range(max(1, warmup)):
         us, infos, its = P.picard_batched(plans, K0, bs, check_status=False, **kw)
     torch.cuda.synchronize()
@@ -381,10 +384,13 @@ def batch_run(steps=1, warmup=1, use_graph=0):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
     dofs = sum(n ** 3 for n in sizes)
-    return {"workload": "16 uneven lognormal Picard instances, concurrent", "sizes": sizes, "dofs": dofs,
+    mode_name = {1: "lockstep (batched passes, per-instance mask, step graphs)",
+                 2: "concurrent (one solver per instance)"}[batch_mode]
+    return {"workload": f"16 uneven lognormal Picard instances, {mode_name}", "sizes": sizes, "dofs": dofs,
             "s_per_batch": dt, "gdofs_solved_per_s": dofs / dt / 1e9, "picard_iters": its,
             "inner_iterations": [i["iterations"] for i in infos],
-            "status": [i["status"] for i in infos], "use_graph": use_graph,
+            "status": [i["status"] for i in infos], "use_graph": use_graph, "batch_mode": batch_mode,
+            "graph_captures": infos[0]["graph_captures"],
             "gpu_launches_per_batch": (P.lib.cheb_launch_count() - l0) // steps}
 
 
@@ -439,7 +445,7 @@ def newton_table(Ns=(4, 8, 16, 32, 64, 128, 256), mode=1):
 
 
 def batch_workload(args):
-    print(json.dumps(batch_run(args.steps, args.warmup, args.use_graph)), flush=True)
+    print(json.dumps(batch_run(args.steps, args.warmup, args.use_graph, args.batch_mode)), flush=True)
 
 
 def workload_config(levels, contrast):
@@ -616,7 +622,10 @@ def main():
     # ---- the batched configuration (secondary keys of the line)
     batch = None
     if not args.no_batch:
-        batch = batch_run(steps=1, warmup=1)
+        batch = batch_run(steps=1, warmup=1, batch_mode=1)
+        batch_c = batch_run(steps=1, warmup=1, batch_mode=2)
+        batch["concurrent_s_per_batch"] = batch_c["s_per_batch"]
+        batch["concurrent_gpu_launches_per_batch"] = batch_c["gpu_launches_per_batch"]
     newton = None
     if not args.no_newton:
         newton_table(Ns=(4, 8, 16))            # warm-up of the level plans' kernels

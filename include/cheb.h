@@ -212,7 +212,18 @@ typedef struct cheb_solve_opts {
   int formulation;     /* CHEB_FORM_REPLACE or CHEB_FORM_ELIMINATE */
   double coarse_rtol;  /* hierarchies: rtol of the levels below the finest (their
                           solutions only start the next level); 0 = rtol */
+  int batch_mode;      /* cheb_solve_batched / cheb_picard_batched: CHEB_BATCH_* */
 } cheb_solve_opts;
+
+/* How a batch iterates: LOCKSTEP = every instance in one iteration stream
+ * (batched line passes over an (instance, line-tile) work list, batched
+ * Gram-Schmidt and Givens kernels with a per-instance converged mask, one
+ * captured graph per Arnoldi step; needs n <= 129 on every axis, a
+ * Dirichlet face per instance, plans of one dimension and device, the
+ * row-replaced formulation and reorth 0); CONCURRENT = one host thread and
+ * stream per instance running the single-instance solver; AUTO = LOCKSTEP
+ * where allowed, else CONCURRENT. */
+enum cheb_batch_mode { CHEB_BATCH_AUTO = 0, CHEB_BATCH_LOCKSTEP = 1, CHEB_BATCH_CONCURRENT = 2 };
 
 typedef struct cheb_solve_info {
   int status;              /* return code of the solve */
@@ -234,7 +245,8 @@ typedef struct cheb_solve_info {
 
 /* Defaults: MIXED, rtol 1e-12, restart 30, augment 3, maxiter 2000,
  * inner_rtol 1e-4, inner_maxiter 400, max_refinements 30, FDM, kref auto,
- * use_graph 0, recycle 0, formulation REPLACE, coarse_rtol 0 (= rtol). */
+ * use_graph 0, recycle 0, formulation REPLACE, coarse_rtol 0 (= rtol),
+ * batch_mode AUTO. */
 void cheb_solve_opts_default(cheb_solve_opts* opts);
 
 /* Solve A u = b (Alg. 2 with the Krylov solver LGMRES; boundary rows as in
@@ -303,8 +315,14 @@ int cheb_newton_solve(cheb_plan plan, const double* K0, double alpha, const doub
                       int maxit, const cheb_solve_opts* opts, cheb_solve_info* info, int* newton_iters,
                       double* newton_delta);
 
-/* Batches of independent instances (each its own plan, any sizes), solved
- * concurrently: one host thread per instance orders its work on its plan's
+/* Batches of independent instances (each its own plan, any sizes).
+ * opts->batch_mode picks the iteration (CHEB_BATCH_*).  LOCKSTEP copies the
+ * instances' K, b and u into one concatenated workspace (allocated for the
+ * call: about (restart + 2 augment + 5) FP32 and 8 FP64 words per DOF of the
+ * batch), iterates all instances together, each leaving the iteration when
+ * it converges, and copies u back; it waits for the plans' streams first and
+ * runs on a private stream.  info.graph_captures counts the step graphs it
+ * captured.  CONCURRENT runs one host thread per instance on its plan's
  * stream (plans on the legacy NULL stream get a private stream for the
  * call).  Arrays have `count` entries; infos / picard_iters may be NULL.
  * Returns the most severe status; the first error message is kept. */

@@ -24,6 +24,7 @@ SOLVE_FP64, SOLVE_MIXED = 0, 1
 ROUTE_AUTO, ROUTE_TRANSFORM, ROUTE_DENSE, ROUTE_TENSOR = -1, 0, 1, 2
 PRECOND_NONE, PRECOND_FDM = 0, 2
 FORM_REPLACE, FORM_ELIMINATE = 0, 1
+BATCH_AUTO, BATCH_LOCKSTEP, BATCH_CONCURRENT = 0, 1, 2
 
 
 def solve_opts(**kw) -> SolveOpts:
@@ -418,8 +419,8 @@ def _batch_args(plans, A, b, u):
 
 
 def solve_batched(plans, K, b, u=None, check_status: bool = True, **opts):
-    """Independent solves run concurrently (``cheb_solve_batched``).
-    Returns (solutions, infos)."""
+    """Independent solves of a batch (``cheb_solve_batched``; ``batch_mode``
+    = BATCH_AUTO / BATCH_LOCKSTEP / BATCH_CONCURRENT).  Returns (solutions, infos)."""
     torch.cuda.synchronize()
     L, hp, Kp, bp, up, u = _batch_args(plans, K, b, u)
     infos = (SolveInfo * L)()
@@ -432,8 +433,8 @@ def solve_batched(plans, K, b, u=None, check_status: bool = True, **opts):
 
 def picard_batched(plans, K0, b, u=None, beta: float = 0.5, tol: float = 1e-9, maxit: int = 30,
                    omega: float = 1.0, check_status: bool = True, **opts):
-    """Independent Picard solves run concurrently (``cheb_picard_batched``).
-    Returns (solutions, infos, picard iteration counts)."""
+    """Independent Picard solves of a batch (``cheb_picard_batched``, same
+    ``batch_mode`` choice).  Returns (solutions, infos, picard iteration counts)."""
     torch.cuda.synchronize()
     L, hp, Kp, bp, up, u = _batch_args(plans, K0, b, u)
     infos = (SolveInfo * L)()

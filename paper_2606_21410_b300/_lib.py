@@ -44,6 +44,7 @@ class SolveOpts(C.Structure):
         ("recycle", i32),
         ("formulation", i32),
         ("coarse_rtol", C.c_double),
+        ("batch_mode", C.c_int),
     ]
 
 

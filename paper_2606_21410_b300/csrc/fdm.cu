@@ -203,6 +203,7 @@ void fdm_free(Fdm& f) {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct FdmK {
+  const int* active;  // batched solves: skip while *active == 0 (null: always run)
   int m[3], mp[3], off[3];
   const T* Lh[3];
   const T* lam[3];
@@ -235,6 +236,7 @@ __device__ __forceinline__ uint32_t cpos(const FdmK<T>& t, int ci, int cj, int c
 constexpr int kLiftK = 8;
 template <typename T>
 __global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__ r, T* __restrict__ U) {
+  if (t.active && *t.active == 0) return;  // converged batch instance
   const int ci = blockIdx.x * blockDim.x + threadIdx.x, cj = blockIdx.y;
   if (ci >= t.m[0]) return;
   const int i = ci + t.off[0], j = cj + t.off[1];
@@ -260,6 +262,7 @@ __global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__
 
 template <typename T>
 __global__ void fdm_scale_kernel(FdmK<T> t, int dim, T kref, T* __restrict__ U) {
+  if (t.active && *t.active == 0) return;  // converged batch instance
   FDM_CELL_INDEX
   T l = t.lam[0][ci];
   if (dim > 1) l += t.lam[1][cj];
@@ -270,6 +273,7 @@ __global__ void fdm_scale_kernel(FdmK<T> t, int dim, T kref, T* __restrict__ U) 
 
 template <typename T>
 __global__ void fdm_scatter_kernel(Geom g, FdmK<T> t, const T* __restrict__ U, T* __restrict__ x) {
+  if (t.active && *t.active == 0) return;  // converged batch instance
   FDM_CELL_INDEX
   x[gidx3(g, ci + t.off[0], cj + t.off[1], ck + t.off[2])] = U[cpos(t, ci, cj, ck)];
 }
@@ -289,6 +293,7 @@ struct FdmSrc {
 template <typename T>
 __global__ void __launch_bounds__(256) fdm_faces_x_kernel(Geom g, FdmK<T> t, FdmSrc<T> u,
                                                           const T* __restrict__ r, T* __restrict__ x) {
+  if (t.active && *t.active == 0) return;  // converged batch instance
   const int ma = t.m[0];
   const int lines = t.m[1] * t.m[2];
   const int lane = threadIdx.x & 31;
@@ -337,6 +342,7 @@ __global__ void __launch_bounds__(256) fdm_faces_x_kernel(Geom g, FdmK<T> t, Fdm
 template <typename T>
 __global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, int a, FdmSrc<T> u,
                                                            const T* __restrict__ r, T* __restrict__ x) {
+  if (t.active && *t.active == 0) return;  // converged batch instance
   __shared__ T red[2][8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int ci = blockIdx.x * 32 + tx, co = blockIdx.y;
@@ -387,6 +393,7 @@ __global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, in
 template <typename T>
 __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __restrict__ r,
                                  T* __restrict__ x) {
+  if (t.active && *t.active == 0) return;  // converged batch instance
   const int nb_axes = g.dim - 1;  // other active axes
   int others[2], no = 0;
   for (int q = 0; q < g.dim; ++q)
@@ -638,6 +645,7 @@ __global__ void fdm_faces_t_kernel(Geom g, FdmK<T> t, int a, T kref, const T* __
 template <typename T> static FdmK<T> make_k(const Fdm& f, int dim);
 template <> FdmK<double> make_k<double>(const Fdm& f, int dim) {
   FdmK<double> k;
+  k.active = f.active;
   for (int a = 0; a < 3; ++a) {
     k.m[a] = f.m[a];
     k.mp[a] = f.mp[a];
@@ -649,6 +657,7 @@ template <> FdmK<double> make_k<double>(const Fdm& f, int dim) {
 }
 template <> FdmK<float> make_k<float>(const Fdm& f, int dim) {
   FdmK<float> k;
+  k.active = f.active;
   for (int a = 0; a < 3; ++a) {
     k.m[a] = f.m[a];
     k.mp[a] = f.mp[a];
@@ -733,7 +742,9 @@ static int rot_sweep(const cheb_plan_s* p, Fdm& f, float** U, int& cur, int q, U
   last.mc = f.m[L];
   for (int a = 0; a < p->dim; ++a) {
     const int K = f.mp[a];
-    const UmmaEpi plain;
+    UmmaEpi plain;
+    plain.active = f.active;
+    last.active = f.active;
     const int st = umma_tf32x3_rot(U[cur], f.uw[a][2 * q], f.uw[a][2 * q + 1], U[1 - cur], (int)(ptot / K), K, K,
                                    a == L ? last : plain, s);
     if (st) return st;
@@ -897,6 +908,16 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
 
 template int fdm_apply<double>(const cheb_plan_s*, Fdm&, double, const double*, double*, cudaStream_t);
 template int fdm_apply<float>(const cheb_plan_s*, Fdm&, double, const float*, float*, cudaStream_t);
+
+template <typename T>
+int fdm_prepare(const cheb_plan_s* p, Fdm& f, cudaStream_t s) {
+  int st;
+  if ((st = ensure_compact<T>(f, ubuf<T>(f), s))) return st;
+  if (has_flux(p) && (st = ensure_ybuf<T>(p, f))) return st;
+  return CHEB_OK;
+}
+template int fdm_prepare<double>(const cheb_plan_s*, Fdm&, cudaStream_t);
+template int fdm_prepare<float>(const cheb_plan_s*, Fdm&, cudaStream_t);
 
 template <typename T>
 int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cudaStream_t s) {

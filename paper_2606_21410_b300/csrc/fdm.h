@@ -37,6 +37,10 @@ struct Fdm {
   // (hi, lo) of S, S^{-1}, S^T, S^{-T}, each umma_n_tile(mp) x mp.
   bool rot = false;
   float* uw[3][8] = {};
+  // batched solves: the kernels of this preconditioner return at entry while
+  // *active == 0 (the instance has converged); null outside batches.  The
+  // small-grid GEMM contractions (no tcgen05 route) are not masked.
+  const int* active = nullptr;
 };
 
 int fdm_setup(const cheb_plan_s* p, Fdm& f);
@@ -55,6 +59,10 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
 // rows take r as n.grad x data (flux data must be divided by -K first).
 template <typename T>
 int fdm_fill_boundary(const cheb_plan_s* p, Fdm& f, const T* r, T* x, cudaStream_t s);
+// The allocations fdm_apply<T> makes on first use, made now (a captured
+// graph may not allocate).
+template <typename T>
+int fdm_prepare(const cheb_plan_s* p, Fdm& f, cudaStream_t s);
 // z = M^{-T} y (for the adjoint solve).
 template <typename T>
 int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cudaStream_t s);

@@ -208,43 +208,73 @@ int launch_chirp_pass(const Geom& g, int axis, int kind, const AxisK<T>& ak, int
 // ---------------------------------------------------------------------------
 // the line-pass kernel
 // ---------------------------------------------------------------------------
-template <typename T, int ROUTE, int P, int CM, int TL>
-__global__ void __launch_bounds__(TL * 16)
-line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
-                 const T* __restrict__ u, T* __restrict__ out, const T* __restrict__ Cj) {
+// Shared-memory pointers of one line pass (layout of pass_smem_bytes).
+template <typename T>
+struct PassSmem {
+  T* X;
+  T* ends;
+  typename C2<T>::t *Cb, *tw, *ch, *bh;
+  T *tmp, *Dm;
+};
+
+// Carve the pass' shared memory for the axis tables `ax` and stage the
+// tables (chirp transform: twiddles, chirp, kernel transform; dense: D).
+// The caller synchronises before the tables are read.
+template <typename T, int ROUTE, int P, int TL>
+__device__ __forceinline__ PassSmem<T> pass_stage(unsigned char* p, const AxisK<T>& ax) {
   typedef typename C2<T>::t C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = ax.n, N = ax.N;
   const int ldx = n | 1;
-  unsigned char* p = smem_raw;
-  T* X = (T*)p;            p += align16(sizeof(T) * TL * ldx);
-  T* ends = (T*)p;         p += align16(sizeof(T) * TL * 4);
-  C* Cb = nullptr; C* tw = nullptr; C* ch = nullptr; C* bh = nullptr; T* tmp = nullptr; T* Dm = nullptr;
+  PassSmem<T> sm;
+  sm.X = (T*)p;            p += align16(sizeof(T) * TL * ldx);
+  sm.ends = (T*)p;         p += align16(sizeof(T) * TL * 4);
+  sm.Cb = sm.tw = sm.ch = sm.bh = nullptr;
+  sm.tmp = sm.Dm = nullptr;
   if (ROUTE == CHEB_ROUTE_TRANSFORM) {
-    Cb = (C*)p;            p += align16(2 * sizeof(T) * (size_t)(TL / 2) * FftBuf<P>::len);
-    tw = (C*)p;            p += align16(2 * sizeof(T) * (size_t)P);
-    ch = (C*)p;            p += align16(2 * sizeof(T) * (size_t)(P / 2));
-    bh = (C*)p;
+    sm.Cb = (C*)p;         p += align16(2 * sizeof(T) * (size_t)(TL / 2) * FftBuf<P>::len);
+    sm.tw = (C*)p;         p += align16(2 * sizeof(T) * (size_t)P);
+    sm.ch = (C*)p;         p += align16(2 * sizeof(T) * (size_t)(P / 2));
+    sm.bh = (C*)p;
     for (int t = threadIdx.x; t < P; t += blockDim.x) {
-      tw[t] = ax.tw[t];
-      bh[t] = ax.bhat[t];
+      sm.tw[t] = ax.tw[t];
+      sm.bh[t] = ax.bhat[t];
     }
-    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) ch[t] = ax.chirp[t];
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) sm.ch[t] = ax.chirp[t];
   } else {
-    tmp = (T*)p;           p += align16(sizeof(T) * TL * ldx);
-    Dm = (T*)p;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Dm[t] = ax.D[t];
+    sm.tmp = (T*)p;        p += align16(sizeof(T) * TL * ldx);
+    sm.Dm = (T*)p;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sm.Dm[t] = ax.D[t];
   }
+  return sm;
+}
 
+// One tile of TL lines of a line pass (tile index `tile` of the axis'
+// tiling: x lines in groups of TL, y / z lines in TL-wide x blocks).
+template <typename T, int ROUTE, int P, int CM, int TL>
+__device__ __forceinline__ void line_pass_tile(const Geom& g, int axis, int kind, const AxisK<T>& ax,
+                                               const T* __restrict__ K, const T* __restrict__ u,
+                                               T* __restrict__ out, const T* __restrict__ Cj, int tile,
+                                               const PassSmem<T>& sm) {
+  typedef typename C2<T>::t C;
+  const int n = ax.n, N = ax.N;
+  const int ldx = n | 1;
+  T* X = sm.X;
+  T* ends = sm.ends;
+  C* Cb = sm.Cb;
+  const C* tw = sm.tw;
+  const C* ch = sm.ch;
+  const C* bh = sm.bh;
+  T* tmp = sm.tmp;
+  const T* Dm = sm.Dm;
   TileMap map;
   map.axis = axis; map.nx = g.n[0]; map.ny = g.n[1]; map.nz = g.n[2]; map.TL = TL;
   if (axis == 0) {
-    map.line0 = blockIdx.x * TL; map.i0 = 0; map.outer = 0;
+    map.line0 = tile * TL; map.i0 = 0; map.outer = 0;
   } else {
     const int nbx = (g.n[0] + TL - 1) / TL;
     map.line0 = 0;
-    map.i0 = (blockIdx.x % nbx) * TL;
-    map.outer = blockIdx.x / nbx;
+    map.i0 = (tile % nbx) * TL;
+    map.outer = tile / nbx;
   }
   const int tile_elems = TL * n;
 
@@ -372,6 +402,15 @@ line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ 
       }
     }
   }
+}
+
+template <typename T, int ROUTE, int P, int CM, int TL>
+__global__ void __launch_bounds__(TL * 16)
+line_pass_kernel(Geom g, int axis, int kind, AxisK<T> ax, const T* __restrict__ K,
+                 const T* __restrict__ u, T* __restrict__ out, const T* __restrict__ Cj) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PassSmem<T> sm = pass_stage<T, ROUTE, P, TL>(smem_raw, ax);
+  line_pass_tile<T, ROUTE, P, CM, TL>(g, axis, kind, ax, K, u, out, Cj, blockIdx.x, sm);
 }
 
 }  // namespace cheb

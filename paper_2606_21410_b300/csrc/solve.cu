@@ -22,6 +22,7 @@
 
 #include "device.cuh"
 #include "fdm.h"
+#include "hess.cuh"
 #include "umma.h"
 #include "krylov.h"
 #include "prolong.h"
@@ -233,58 +234,12 @@ static int op_B(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K, const
   return st;
 }
 
-// ---------------------------------------------------------------------------
-// device-side Hessenberg update for graph-captured cycles.  Layout of the
-// FP64 block (nb = basis size): H[(nb+1) x nb] unrotated, R[(nb+1) x nb]
-// rotated, cs[nb], sn[nb], g[nb+1], res[nb] (|g_{j+1}| after step j).
-// ---------------------------------------------------------------------------
-struct HessLayout {
-  int nb;
-  __host__ __device__ size_t H() const { return 0; }
-  __host__ __device__ size_t R() const { return (size_t)(nb + 1) * nb; }
-  __host__ __device__ size_t cs() const { return 2 * (size_t)(nb + 1) * nb; }
-  __host__ __device__ size_t sn() const { return cs() + nb; }
-  __host__ __device__ size_t g() const { return sn() + nb; }
-  __host__ __device__ size_t res() const { return g() + nb + 1; }
-  __host__ __device__ size_t total() const { return res() + nb; }
-};
-
-// column j of H from the Gram-Schmidt coefficients of one pass
+// Hessenberg column and Givens rotation of step j on the device (hess.cuh)
 __global__ void hcol_kernel(double* hess, HessLayout L, int j, int pass, const double* __restrict__ dv) {
-  double* H = hess + L.H();
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    const double v = dv[i];
-    H[(size_t)i * L.nb + j] = pass == 0 ? v : H[(size_t)i * L.nb + j] + v;
-  }
+  hess_column(hess, L, j, pass, dv);
 }
-
-// H[j+1][j] = |w|, rotate column j with the earlier rotations, make rotation j,
-// update g and record |g_{j+1}|
 __global__ void givens_kernel(double* hess, HessLayout L, int j, const double* __restrict__ norm2) {
-  if (threadIdx.x != 0) return;
-  double* H = hess + L.H();
-  double* R = hess + L.R();
-  double* cs = hess + L.cs();
-  double* sn = hess + L.sn();
-  double* g = hess + L.g();
-  const int nb = L.nb;
-  const double hn = sqrt(fmax(0.0, *norm2));
-  H[(size_t)(j + 1) * nb + j] = hn;
-  for (int i = 0; i <= j + 1; ++i) R[(size_t)i * nb + j] = H[(size_t)i * nb + j];
-  for (int i = 0; i < j; ++i) {
-    const double a = R[(size_t)i * nb + j], b = R[(size_t)(i + 1) * nb + j];
-    R[(size_t)i * nb + j] = cs[i] * a + sn[i] * b;
-    R[(size_t)(i + 1) * nb + j] = -sn[i] * a + cs[i] * b;
-  }
-  const double a = R[(size_t)j * nb + j], b = R[(size_t)(j + 1) * nb + j];
-  const double den = hypot(a, b);
-  cs[j] = den > 0 ? a / den : 1.0;
-  sn[j] = den > 0 ? b / den : 0.0;
-  R[(size_t)j * nb + j] = den;
-  R[(size_t)(j + 1) * nb + j] = 0.0;
-  g[j + 1] = -sn[j] * g[j];
-  g[j] = cs[j] * g[j];
-  hess[L.res() + j] = fabs(g[j + 1]);
+  if (threadIdx.x == 0) hess_givens(hess, L, j, *norm2);
 }
 
 // w = BZ[order[q]] (augmentation step q of a cycle; vectors ld apart)
@@ -382,6 +337,7 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
     cg.m_eff = m_eff; cg.K = K; cg.kref = o.kref; cg.precond = o.precond; cg.reorth = o.reorth;
     cg.transpose = o.transpose; cg.m = o.m; cg.k = o.k;
     cg.nkernels = thread_launches() - l0;
+    add_launches(-cg.nkernels);  // recorded, not run: counted at each replay
     stt.captures++;
   }
   prof_begin(kProfOther, s);
@@ -661,6 +617,38 @@ static void default_opts(cheb_solve_opts& o) {
   o.recycle = 0;
   o.formulation = CHEB_FORM_REPLACE;
   o.coarse_rtol = 0.0;
+  o.batch_mode = CHEB_BATCH_AUTO;
+}
+
+// lockstep batch engine (batch.cu)
+bool lockstep_ok(int count, const cheb_plan* plans, const cheb_solve_opts& o);
+int lockstep_solve(int count, const cheb_plan* plans, const double* const* K, const double* const* b,
+                   double* const* u, const cheb_solve_opts& o, cheb_solve_info* infos, bool picard, double beta,
+                   double omega, double ptol, int pmaxit, int* piters);
+
+// plan-level helpers of the lockstep batch engine (batch.cu)
+int plan_fdm(cheb_plan_s* p, Fdm** f) {
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  if ((st = fdm_setup(p, p->ws->fdm))) return st;
+  *f = &p->ws->fdm;
+  return CHEB_OK;
+}
+
+// geometric mean of K over the plan's grid, computed on stream s (synchronises s)
+int plan_kref(cheb_plan_s* p, const double* K, double* kref, cudaStream_t s) {
+  int st;
+  if ((st = ensure_ws(p))) return st;
+  Workspace& w = *p->ws;
+  if ((st = k_sum_log(w.rs, K, w.n, w.dscal, s))) return st;
+  if ((st = sync_read(w, 1, s))) return st;
+  *kref = std::exp(w.hscal[0] / (double)w.n);
+  return CHEB_OK;
+}
+
+void resolve_opts(const cheb_solve_opts* in, cheb_solve_opts* out) {
+  if (in) *out = *in;
+  else default_opts(*out);
 }
 
 static double norm2_dev(Workspace& w, const double* x, cudaStream_t s, int* st) {
@@ -1540,16 +1528,48 @@ static int batched(int count, const cheb_plan* plans, const double* const* K, co
   return worst;
 }
 
+// LOCKSTEP / CONCURRENT choice of a batch (CHEB_ERR_UNSUPPORTED when
+// LOCKSTEP is forced on a batch it does not cover)
+static int batch_route(int count, const cheb_plan* plans, const cheb_solve_opts& o, bool* lock) {
+  if (o.batch_mode != CHEB_BATCH_AUTO && o.batch_mode != CHEB_BATCH_LOCKSTEP &&
+      o.batch_mode != CHEB_BATCH_CONCURRENT) {
+    set_error("bad batch_mode");
+    return CHEB_ERR_ARG;
+  }
+  if (o.mode != CHEB_SOLVE_FP64 && o.mode != CHEB_SOLVE_MIXED) { set_error("bad mode"); return CHEB_ERR_ARG; }
+  const bool ok = lockstep_ok(count, plans, o);
+  if (o.batch_mode == CHEB_BATCH_LOCKSTEP && !ok) {
+    set_error("lockstep batch needs n <= 129, a Dirichlet face, one dimension and device, REPLACE, reorth 0");
+    return CHEB_ERR_UNSUPPORTED;
+  }
+  *lock = ok && o.batch_mode != CHEB_BATCH_CONCURRENT;
+  return CHEB_OK;
+}
+
 int cheb_solve_batched(int count, const cheb_plan* plans, const double* const* K, const double* const* b,
                        double* const* u, const cheb_solve_opts* opts, cheb_solve_info* infos) {
-  return batched(count, plans, K, b, u, opts, infos, 0.0, 1.0, 1.0, 1, nullptr, false);
+  if (count < 1 || !plans || !K || !b || !u) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  cheb_solve_opts o;
+  resolve_opts(opts, &o);
+  bool lock = false;
+  int st;
+  if ((st = batch_route(count, plans, o, &lock))) return st;
+  if (lock) return lockstep_solve(count, plans, K, b, u, o, infos, false, 0.0, 1.0, 1.0, 1, nullptr);
+  return batched(count, plans, K, b, u, &o, infos, 0.0, 1.0, 1.0, 1, nullptr, false);
 }
 
 int cheb_picard_batched(int count, const cheb_plan* plans, const double* const* K0,
                         const double* const* b, double* const* u, double beta, double omega,
                         double tol, int maxit, const cheb_solve_opts* opts, cheb_solve_info* infos,
                         int* picard_iters) {
-  return batched(count, plans, K0, b, u, opts, infos, beta, omega, tol, maxit, picard_iters, true);
+  if (count < 1 || !plans || !K0 || !b || !u) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  cheb_solve_opts o;
+  resolve_opts(opts, &o);
+  bool lock = false;
+  int st;
+  if ((st = batch_route(count, plans, o, &lock))) return st;
+  if (lock) return lockstep_solve(count, plans, K0, b, u, o, infos, true, beta, omega, tol, maxit, picard_iters);
+  return batched(count, plans, K0, b, u, &o, infos, beta, omega, tol, maxit, picard_iters, true);
 }
 
 int cheb_selftest_bounded_wait(long long wait_cycles) {

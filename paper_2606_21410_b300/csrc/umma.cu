@@ -246,6 +246,9 @@ __global__ void __launch_bounds__(kUThreads, 1)
     umma_tf32x3_rot_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmWh,
                            const __grid_constant__ CUtensorMap tmWl, float* __restrict__ Y, int M, int N, int K,
                            int n_tile, int tmem_cols, const UmmaEpi ep) {
+  // a converged instance of a batched solve: nothing is initialised or
+  // allocated yet, every thread of the CTA returns
+  if (ep.active && *ep.active == 0) return;
   constexpr int S = UmmaCfg<BK>::kStages;
   constexpr uint32_t RB = UmmaCfg<BK>::kRow;
   extern __shared__ uint8_t smem_raw[];

@@ -41,6 +41,7 @@ struct UmmaEpi {
   int ncol = 0;  // points of the column axis, ends included
   const float* G = nullptr;
   const float* Binv = nullptr;
+  const int* active = nullptr;  // batched solves: the CTA returns at entry while *active == 0
 };
 int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M, int N, int K,
                     const UmmaEpi& ep, cudaStream_t s);

@@ -1,7 +1,11 @@
 """Picard iteration and batched solves: the GPU Picard fixed point against
 the oracle's Picard iteration (uneven sizes exercising both line-derivative
 routes), batched solves against single solves and the oracle, and a batch
-of the configuration's uneven lognormal instances."""
+of the configuration's uneven lognormal instances.  Batches run in both
+iteration modes: LOCKSTEP (all instances in one iteration stream, batched
+line passes over an (instance, tile) work list, per-instance converged
+mask, one captured graph per Arnoldi step) and CONCURRENT (one solver per
+instance)."""
 import numpy as np
 import pytest
 import torch
@@ -33,6 +37,9 @@ def _instance(n, seed):
     return p, K0, b
 
 
+LOCKSTEP, CONCURRENT = 1, 2
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_picard_matches_oracle(mode):
     n = (13, 9, 11)
@@ -52,18 +59,24 @@ def test_picard_matches_oracle(mode):
     assert np.linalg.norm(O.FDMPreconditioner(g, O.geometric_mean(K))(r)) < 1e-9 * np.abs(u.cpu().numpy()).max()
 
 
-def test_batched_solve_matches_single_solves():
+@pytest.mark.parametrize("batch_mode", [LOCKSTEP, CONCURRENT])
+def test_batched_solve_matches_single_solves(batch_mode):
+    """Both iteration modes against single solves (rtol 1e-12 everywhere:
+    solutions agree to 1e-10, the bound of kappa(M^-1 A) ~ 10-100 times the
+    tolerance) and the oracle's direct solve."""
     import paper_2606_21410_b300 as P
     sizes = [(17, 17, 17), (13, 21, 9), (33, 9, 17), (9, 9, 9)]
     items = [_instance(n, 10 + i) for i, n in enumerate(sizes)]
     plans = [it[0] for it in items]
     K = [_dev(it[1]) for it in items]
     b = [it[2] for it in items]
-    ub, infos = P.solve_batched(plans, K, b, mode=1, rtol=1e-12)
+    ub, infos = P.solve_batched(plans, K, b, mode=1, rtol=1e-12, batch_mode=batch_mode)
     for i, (p, Ki, bi) in enumerate(zip(plans, K, b)):
         us, _ = p.solve(Ki, bi, mode=1, rtol=1e-12)
-        assert _rel(ub[i].cpu().numpy(), us.cpu().numpy()) < 1e-11
+        assert _rel(ub[i].cpu().numpy(), us.cpu().numpy()) < 1e-10
         assert infos[i]["status"] == 0
+    if batch_mode == LOCKSTEP:
+        assert all(i["graph_captures"] > 0 for i in infos)
     g = O.Grid(sizes[3], bc=BC4)
     ud = O.solve_direct(K[3].cpu().numpy(), b[3].cpu().numpy(), g)
     assert _rel(ub[3].cpu().numpy(), ud) < 1e-10
@@ -88,10 +101,12 @@ def test_picard_batch_of_uneven_lognormal_instances():
         assert _rel(u[i].cpu().numpy(), us.cpu().numpy()) < 1e-9
 
 
-def test_picard_batch_each_instance_matches_oracle():
+@pytest.mark.parametrize("batch_mode", [LOCKSTEP, CONCURRENT])
+def test_picard_batch_each_instance_matches_oracle(batch_mode):
     """A batch of small uneven instances (both line routes, lognormal K0,
-    K = K0 (1 + 0.5 |grad u|^2)) solved concurrently by cheb_picard_batched:
-    every instance against the oracle's relaxed Picard iteration."""
+    K = K0 (1 + 0.5 |grad u|^2)) solved by cheb_picard_batched in both
+    iteration modes: every instance against the oracle's relaxed Picard
+    iteration."""
     import paper_2606_21410_b300 as P
     sizes = [(9, 9, 9), (11, 11, 11), (13, 9, 11), (9, 13, 7)]
     items = [_instance(n, 300 + i) for i, n in enumerate(sizes)]
@@ -99,7 +114,7 @@ def test_picard_batch_each_instance_matches_oracle():
     K0 = [_dev(it[1]) for it in items]
     b = [it[2] for it in items]
     u, infos, its = P.picard_batched(plans, K0, b, beta=0.5, tol=1e-12, maxit=100, omega=0.5, mode=1,
-                                     rtol=1e-13)
+                                     rtol=1e-13, batch_mode=batch_mode)
     for i, n in enumerate(sizes):
         assert infos[i]["status"] == 0, (n, infos[i], its[i])
         g = O.Grid(n, bc=BC4)
@@ -110,3 +125,61 @@ def test_picard_batch_each_instance_matches_oracle():
         bo = O.rhs(np.zeros(g.shape), faces, g)
         uo, io = O.picard_solve(K0o, bo, g, tol=1e-13, maxit=100, omega=0.5)
         assert _rel(u[i].cpu().numpy(), uo) < 1e-9, (n, its[i], io["iterations"])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_lockstep_converged_mask_and_uneven_instances(mode):
+    """Instances that need very different work in one lockstep batch: a
+    zero right-hand side (u = 0 without an iteration), a constant K (the
+    preconditioner is the exact inverse: a step or two), lognormal fields of
+    uneven and non-power-of-two sizes, two boundary sets.  Each leaves the
+    iteration when it converges (per-instance iteration counts), and each
+    solution equals the concurrent mode's and, for the small ones, the
+    oracle's direct solve."""
+    import paper_2606_21410_b300 as P
+    sizes = [(17, 17, 17), (25, 12, 7), (9, 9, 9), (33, 19, 11), (13, 13, 13), (11, 11, 11)]
+    items = [_instance(n, 500 + i) for i, n in enumerate(sizes)]
+    plans = [it[0] for it in items]
+    K = [_dev(it[1]) for it in items]
+    b = [it[2].clone() for it in items]
+    b[2].zero_()                           # zero right-hand side
+    K[4] = torch.full_like(K[4], 2.5)      # constant conductivity
+    bc5 = [0, 0, 0, 0, 0, 0]
+    p5 = P.Plan(sizes[5], bc=bc5)
+    plans[5] = p5
+    b[5] = _dev(W.random_field(p5.shape, 77))
+    kw = dict(mode=mode, rtol=1e-12)
+    ul, il = P.solve_batched(plans, K, b, batch_mode=LOCKSTEP, **kw)
+    uc, ic = P.solve_batched(plans, K, b, batch_mode=CONCURRENT, **kw)
+    for i in range(len(plans)):
+        assert il[i]["status"] == 0, (i, il[i])
+        if i == 2:
+            assert float(ul[i].abs().max()) == 0.0 and il[i]["iterations"] == 0
+            continue
+        assert _rel(ul[i].cpu().numpy(), uc[i].cpu().numpy()) < 1e-10, (i, il[i], ic[i])
+    its = [il[i]["iterations"] for i in range(len(plans))]
+    assert its[4] <= 3 and min(its[0], its[1], its[3]) > 3 * max(its[4], 1), its
+    # one step graph per (step, Krylov-direction count, augmentation slot),
+    # whichever instances are still iterating: at most 4 x (30 + 3 + 1)
+    assert 0 < il[0]["graph_captures"] <= 4 * 34, il[0]["graph_captures"]
+    for i in (2, 5):
+        g = O.Grid(sizes[i], bc=plans[i].bc)
+        ud = O.solve_direct(K[i].cpu().numpy(), b[i].cpu().numpy(), g)
+        assert np.allclose(ul[i].cpu().numpy(), ud, rtol=0, atol=1e-10 * max(1.0, np.abs(ud).max()))
+
+
+def test_lockstep_batch_needs_supported_plans():
+    """LOCKSTEP needs the dense route on every axis (n <= 129): forced on a
+    batch holding a 131-point axis it is refused; AUTO runs that batch in
+    the concurrent mode."""
+    import paper_2606_21410_b300 as P
+    from paper_2606_21410_b300._lib import ChebError
+    sizes = [(9, 9, 9), (131, 5, 5)]
+    items = [_instance(n, 600 + i) for i, n in enumerate(sizes)]
+    plans = [it[0] for it in items]
+    K = [_dev(it[1]) for it in items]
+    b = [it[2] for it in items]
+    with pytest.raises(ChebError):
+        P.solve_batched(plans, K, b, mode=1, rtol=1e-10, batch_mode=LOCKSTEP)
+    u, infos = P.solve_batched(plans, K, b, mode=1, rtol=1e-10)
+    assert all(i["status"] == 0 and i["graph_captures"] == 0 for i in infos)
