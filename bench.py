@@ -626,6 +626,9 @@ def main():
         batch_c = batch_run(steps=1, warmup=1, batch_mode=2)
         batch["concurrent_s_per_batch"] = batch_c["s_per_batch"]
         batch["concurrent_gpu_launches_per_batch"] = batch_c["gpu_launches_per_batch"]
+        # batch_mode AUTO picks lockstep for >= 32 instances or <= 200k points each
+        mean = batch["dofs"] / len(batch["sizes"])
+        batch["auto_mode"] = "lockstep" if len(batch["sizes"]) >= 32 or mean <= 2e5 else "concurrent"
     newton = None
     if not args.no_newton:
         newton_table(Ns=(4, 8, 16))            # warm-up of the level plans' kernels

@@ -222,7 +222,9 @@ typedef struct cheb_solve_opts {
  * Dirichlet face per instance, plans of one dimension and device, the
  * row-replaced formulation and reorth 0); CONCURRENT = one host thread and
  * stream per instance running the single-instance solver; AUTO = LOCKSTEP
- * where allowed, else CONCURRENT. */
+ * where allowed and the batch has at least 32 instances or at most 200,000
+ * points per instance on average (where it measured faster), else
+ * CONCURRENT. */
 enum cheb_batch_mode { CHEB_BATCH_AUTO = 0, CHEB_BATCH_LOCKSTEP = 1, CHEB_BATCH_CONCURRENT = 2 };
 
 typedef struct cheb_solve_info {

@@ -1537,10 +1537,20 @@ static int batch_route(int count, const cheb_plan* plans, const cheb_solve_opts&
     return CHEB_ERR_ARG;
   }
   if (o.mode != CHEB_SOLVE_FP64 && o.mode != CHEB_SOLVE_MIXED) { set_error("bad mode"); return CHEB_ERR_ARG; }
-  const bool ok = lockstep_ok(count, plans, o);
+  bool ok = lockstep_ok(count, plans, o);
   if (o.batch_mode == CHEB_BATCH_LOCKSTEP && !ok) {
     set_error("lockstep batch needs n <= 129, a Dirichlet face, one dimension and device, REPLACE, reorth 0");
     return CHEB_ERR_UNSUPPORTED;
+  }
+  if (o.batch_mode == CHEB_BATCH_AUTO && ok) {
+    // Measured on B300 (Picard batches, 8 steps): lockstep wins where the
+    // instances are many or small (128 x 17^3: 2.8x, 64 x 33^3: 2.0x,
+    // 32 x 49^3: 1.2x), ties at 16 x 65^3 and trails by 15 % on 16 instances
+    // of 33^3 .. 97^3 (mean 363k points), where one solver per instance
+    // already fills the GPU.
+    size_t tot = 0;
+    for (int i = 0; i < count; ++i) tot += plans[i]->size();
+    ok = count >= 32 || tot / (size_t)count <= 200000;
   }
   *lock = ok && o.batch_mode != CHEB_BATCH_CONCURRENT;
   return CHEB_OK;

@@ -183,3 +183,17 @@ def test_lockstep_batch_needs_supported_plans():
         P.solve_batched(plans, K, b, mode=1, rtol=1e-10, batch_mode=LOCKSTEP)
     u, infos = P.solve_batched(plans, K, b, mode=1, rtol=1e-10)
     assert all(i["status"] == 0 and i["graph_captures"] == 0 for i in infos)
+
+
+def test_auto_batch_mode_follows_instance_count_and_size():
+    """AUTO runs lockstep for many small instances (captured step graphs)
+    and one solver per instance for a few large ones (no captures)."""
+    import paper_2606_21410_b300 as P
+    small = [_instance((9, 9, 9), 800 + i) for i in range(40)]
+    u, infos = P.solve_batched([it[0] for it in small], [_dev(it[1]) for it in small], [it[2] for it in small],
+                               mode=1, rtol=1e-10)
+    assert all(i["status"] == 0 for i in infos) and infos[0]["graph_captures"] > 0
+    big = [_instance((65, 65, 65), 900 + i) for i in range(2)]
+    u, infos = P.solve_batched([it[0] for it in big], [_dev(it[1]) for it in big], [it[2] for it in big],
+                               mode=1, rtol=1e-10)
+    assert all(i["status"] == 0 for i in infos) and infos[0]["graph_captures"] == 0
