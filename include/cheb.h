@@ -193,7 +193,9 @@ typedef struct cheb_solve_opts {
   int augment;         /* k: error-approximation vectors carried between cycles;
                           restart + augment + 1 <= 40 */
   int maxiter;         /* cap on Arnoldi steps (all precisions) */
-  double inner_rtol;   /* MIXED: relative tolerance of each FP32 inner solve */
+  double inner_rtol;   /* MIXED: relative tolerance of each FP32 inner solve; a
+                          refinement that needs less takes max(inner_rtol,
+                          rtol / (2 eta)), eta the current outer residual */
   int inner_maxiter;   /* MIXED: cap on Arnoldi steps of one inner solve */
   int max_refinements; /* MIXED: cap on FP64 refinement steps */
   int reorth;          /* 1: Gram-Schmidt twice per Arnoldi step */

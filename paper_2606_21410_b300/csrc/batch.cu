@@ -1048,7 +1048,7 @@ int bsolve(Engine& E, std::vector<int> live, const cheb_solve_opts& o, const dou
       info[i].rel_residual = eta[i];
       if (eta[i] <= o.rtol || sr[i] * cn <= o.atol) { info[i].status = CHEB_OK; continue; }
       if (it == o.max_refinements || info[i].iterations >= o.maxiter) { info[i].status = CHEB_ERR_NOT_CONVERGED; continue; }
-      tol[i] = o.inner_rtol * cn;
+      tol[i] = std::max(o.inner_rtol, 0.5 * o.rtol / eta[i]) * cn;  // as the single solve
       go.push_back(i);
     }
     live = go;

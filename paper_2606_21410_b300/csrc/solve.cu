@@ -876,7 +876,10 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
     if (eta <= o.rtol || sr * cn <= o.atol) { rc = CHEB_OK; break; }
     if (it == o.max_refinements || info.iterations >= o.maxiter) break;
     LgOpts li = lo;
-    li.tol_abs = o.inner_rtol * cn;
+    // the inner solve reduces its residual by inner_rtol, but by no more than
+    // the outer tolerance still asks for (with a factor 2 margin): the last
+    // refinement of a solve usually needs far less than inner_rtol
+    li.tol_abs = std::max(o.inner_rtol, 0.5 * o.rtol / eta) * cn;
     li.maxiter = std::min(o.inner_maxiter, o.maxiter - info.iterations);
     LgStats stt;
     int r2 = lgmres<float>(p, w, li, B.K, B.c, B.x, true, stt, s, o.recycle ? &carry : nullptr);
