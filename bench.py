@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--use-graph", type=int, default=0)
     ap.add_argument("--batch-mode", type=int, default=1, choices=[1, 2],
                     help="--workload batch: 1 lockstep, 2 one concurrent solver per instance")
-    ap.add_argument("--coarse-rtol", type=float, default=1e-4,
+    ap.add_argument("--coarse-rtol", type=float, default=1e-2,
                     help="relative tolerance of the hierarchy's coarse levels, whose solutions only "
                          "start the next level (0: the finest level's 1e-12)")
     ap.add_argument("--ncu-step", action="store_true",
