@@ -572,6 +572,38 @@ def main():
     apply = {"fp32_gdofs": ntot / t32 / 1e9, "fp64_gdofs": ntot / t64 / 1e9,
              "fp32_ms": t32 * 1e3, "fp64_ms": t64 * 1e3}
 
+    # ---- apply at every level with the solve's routes, L2 flushed before each
+    # timed apply (65^3 and 129^3 fields fit in the 126 MB L2)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB
+
+    def time_apply_cold(l, dtype, reps=10):
+        K = Ks[l].to(dtype)
+        u = us[l].to(dtype)
+        out = torch.empty_like(u)
+        plans[l].apply(K, u, out)
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plans[l].apply(K, u, out)
+            b2.record(stream)
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b2) / 1e3
+        return tot / reps
+
+    apply_levels = []
+    for l, n in enumerate(levels):
+        ta32, ta64 = time_apply_cold(l, torch.float32), time_apply_cold(l, torch.float64)
+        apply_levels.append({
+            "n": n, "fp32_routes": [plans[l].route32(a) for a in range(3)],
+            "fp64_routes": [plans[l].route(a) for a in range(3)],
+            "fp32_ms": ta32 * 1e3, "fp64_ms": ta64 * 1e3,
+            "fp32_gdofs": n ** 3 / ta32 / 1e9, "fp64_gdofs": n ** 3 / ta64 / 1e9,
+            "fp32_gbs_3word": 12.0 * n ** 3 / ta32 / 1e9, "fp32_gbs_11word": 44.0 * n ** 3 / ta32 / 1e9,
+            "fp64_gbs_3word": 24.0 * n ** 3 / ta64 / 1e9})
+    del flush
+
     # ---- measured FMA peaks of the CUDA cores, clocks sampled meanwhile
     fma = {}
     with ClockSampler(local) as clk_fma:
@@ -738,7 +770,7 @@ def main():
             "seconds_per_level": [i["seconds"] for i in infos],
             "refinements_per_level": [i["refinements"] for i in infos],
             "rel_residual": infos[-1]["rel_residual"], "e_ref": eref,
-            "apply": apply, "fp64": fp64, "phase_ms_per_step": phase,
+            "apply": apply, "apply_levels": apply_levels, "fp64": fp64, "phase_ms_per_step": phase,
             "routes_per_level": [p.chosen_routes for p in plans],
             "roofline": roof, "prec_roofline": prec_roof, "fp64_apply_roofline": fp64_roof,
             "fma_peaks": fma, "batch": batch, "newton_table1": newton,

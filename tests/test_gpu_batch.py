@@ -148,6 +148,13 @@ def test_lockstep_converged_mask_and_uneven_instances(mode):
     p5 = P.Plan(sizes[5], bc=bc5)
     plans[5] = p5
     b[5] = _dev(W.random_field(p5.shape, 77))
+    # flux faces (their preconditioner rescales the flux data first)
+    bc6 = [0, 2, 2, 2, 0, 2]
+    p6 = P.Plan((15, 10, 12), bc=bc6)
+    sizes.append((15, 10, 12))
+    plans.append(p6)
+    K.append(_dev(W.random_positive_field(p6.shape, 78)))
+    b.append(_dev(W.random_field(p6.shape, 79)))
     kw = dict(mode=mode, rtol=1e-12)
     ul, il = P.solve_batched(plans, K, b, batch_mode=LOCKSTEP, **kw)
     uc, ic = P.solve_batched(plans, K, b, batch_mode=CONCURRENT, **kw)

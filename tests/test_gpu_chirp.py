@@ -228,3 +228,41 @@ def test_chirp_hierarchy_matches_oracle():
         assert _rel(us[i].cpu().numpy(), ud[i]) < 1e-10, (i, infos[i])
     ref_eref = O.e_ref(ud[1], O.prolong(ud[0], grids[0], grids[1]))
     assert abs(eref[1] - ref_eref) <= 1e-8 * ref_eref + 1e-14, (eref, ref_eref)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chirp_adjoint_solve_and_gradient_match_oracle(mode):
+    """Adjoint solve A^T lam = c and dJ/dK on an axis that only the chirp
+    transform covers (n = 131), against the oracle's dense transpose solve
+    (rtol 1e-11 as for the forward solve on this grid)."""
+    n, bc = (131, 5, 4), [0, 1, 2, 0, 1, 0]
+    g = O.Grid(n, bc=bc)
+    p = _plan(n, bc=bc)
+    X, Y, Z = g.mesh()
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0, 0.2, 0.4, 0.2), 1.0, 10.0)
+    b = W.random_field(g.shape, 321)
+    c = W.random_field(g.shape, 322)
+    ud = O.solve_direct(K, b, g)
+    lam_ref = O.adjoint_solve_direct(K, c, g)
+    gK_ref = O.grad_K(ud, lam_ref, g)
+    dK = torch.zeros(p.shape, dtype=torch.float64, device="cuda")
+    lam, dK, info = p.adjoint_solve(_dev(K), _dev(c), u=_dev(ud), dJdK=dK, mode=mode, rtol=1e-11)
+    assert _rel(lam.cpu().numpy(), lam_ref) < 5e-10, info
+    assert _rel(dK.cpu().numpy(), gK_ref) < 5e-9
+
+
+def test_chirp_hierarchy_from_fine_data_matches_oracle():
+    """cheb_solve_hierarchy_fine on chirp sizes (N = (12, 6, 6) -> (24, 12, 12)):
+    coarse K and b injected from the fine data, the fine solution equal to
+    the oracle's direct solve."""
+    import paper_2606_21410_b300 as P
+    lo, hi = (0, 0, 0), (1, 1, 1)
+    ns = [(13, 7, 7), (25, 13, 13)]
+    plans = [_plan(n, lo, hi, force=False) for n in ns]
+    g = O.Grid(ns[-1], lo, hi)
+    X, Y, Z = g.mesh()
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(1, 0.08, 0.2, 0.2, 0.0, 1.0), 1.0, 10.0)
+    b = np.sin(np.pi * X) * Y * (1 - Z) + 1.0
+    u, infos, eref = P.solve_hierarchy_fine(plans, _dev(K), _dev(b), mode=1, rtol=1e-12)
+    assert all(i["status"] == 0 for i in infos), infos
+    assert _rel(u.cpu().numpy(), O.solve_direct(K, b, g)) < 1e-10

@@ -24,7 +24,8 @@ def _fine(nc):
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 1e-6)])
-@pytest.mark.parametrize("nc", [(33, 33, 33), (65, 65, 65), (17, 33, 9), (65, 17), (129,)])
+@pytest.mark.parametrize("nc", [(33, 33, 33), (65, 65, 65), (17, 33, 9), (65, 17), (129,),
+                                (25, 13, 7), (101, 9)])  # the last two: N not powers of two
 def test_noalloc_prolong_matches_cheb_prolong_twice(nc, dtype, tol):
     import paper_2606_21410_b300 as P
     lib = P.lib
