@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--use-graph", type=int, default=0)
     ap.add_argument("--batch-mode", type=int, default=1, choices=[1, 2],
                     help="--workload batch: 1 lockstep, 2 one concurrent solver per instance")
+    ap.add_argument("--picard-steps", type=int, default=60,
+                    help="--workload batch: Picard iteration limit (the batch converges in 30)")
     ap.add_argument("--coarse-rtol", type=float, default=1e-2,
                     help="relative tolerance of the hierarchy's coarse levels, whose solutions only "
                          "start the next level (0: the finest level's 1e-12)")
@@ -352,7 +354,7 @@ def apply_only(args, n):
     print(json.dumps(rec), flush=True)
 
 
-def batch_run(steps=1, warmup=1, use_graph=0, batch_mode=1):
+def batch_run(steps=1, warmup=1, use_graph=0, batch_mode=1, picard_steps=60, ncu_step=False):
     """The batched configuration: 16 instances, sizes U{33..97} (seed 1),
     K = K0 (1 + 0.5 |grad u|^2) with lognormal K0 (sigma 0.5, correlation 0.2),
     Dirichlet u = x on x = +-1 and z = -1, Neumann 0 elsewhere; relaxed Picard
@@ -372,11 +374,17 @@ def batch_run(steps=1, warmup=1, use_graph=0, batch_mode=1):
         bs.append(p.rhs(torch.zeros(p.shape, dtype=torch.float64, device="cuda"),
                         [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in faces]))
         plans.append(p)
-    kw = dict(beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1, rtol=1e-10, use_graph=use_graph,
+    kw = dict(beta=0.5, tol=1e-9, maxit=picard_steps, omega=0.5, mode=1, rtol=1e-10, use_graph=use_graph,
               batch_mode=batch_mode)
     for _ in range(max(1, warmup)):
         us, infos, its = P.picard_batched(plans, K0, bs, check_status=False, **kw)
     torch.cuda.synchronize()
+    if ncu_step:
+        torch.cuda.profiler.start()
+        P.picard_batched(plans, K0, bs, check_status=False, **kw)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return {"profiled": True}
     l0 = P.lib.cheb_launch_count()
     t0 = time.perf_counter()
     for _ in range(steps):
@@ -445,7 +453,8 @@ def newton_table(Ns=(4, 8, 16, 32, 64, 128, 256), mode=1):
 
 
 def batch_workload(args):
-    print(json.dumps(batch_run(args.steps, args.warmup, args.use_graph, args.batch_mode)), flush=True)
+    print(json.dumps(batch_run(args.steps, args.warmup, args.use_graph, args.batch_mode, args.picard_steps,
+                               args.ncu_step)), flush=True)
 
 
 def workload_config(levels, contrast):
