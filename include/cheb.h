@@ -219,8 +219,9 @@ typedef struct cheb_solve_opts {
 
 /* How a batch iterates: LOCKSTEP = every instance in one iteration stream
  * (batched line passes over an (instance, line-tile) work list, batched
- * Gram-Schmidt and Givens kernels with a per-instance converged mask, one
- * captured graph per Arnoldi step; needs n <= 129 on every axis, a
+ * Gram-Schmidt and Givens kernels with a per-instance converged mask, the
+ * preconditioner's lift, face and boundary-line steps batched over the
+ * instances, one captured graph per Arnoldi step; needs n <= 129 on every axis, a
  * Dirichlet face per instance, plans of one dimension and device, the
  * row-replaced formulation and reorth 0); CONCURRENT = one host thread and
  * stream per instance running the single-instance solver; AUTO = LOCKSTEP

@@ -418,6 +418,8 @@ struct Engine {
   double* r64 = nullptr;
   std::vector<double> kref;
   int precond = CHEB_PRECOND_FDM;
+  FdmBatch* fb = nullptr;           // batched lift / face / boundary-line steps (FP32)
+  std::vector<char> in_fb;          // instance i runs its FP32 preconditioner through fb
   std::map<std::string, StepGraph> graphs;
   bool warm = false;
   int captures = 0;
@@ -427,6 +429,8 @@ struct Engine {
     for (auto& kv : graphs)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     graphs.clear();
+    fdm_batch_free(fb);
+    fb = nullptr;
     auto fr = [](auto*& p) { if (p) cudaFree(p); p = nullptr; };
     auto frh = [](auto*& p) { if (p) cudaFreeHost(p); p = nullptr; };
     fr(d_inst); fr(d_lo); fr(d_hi); fr(d_first); fr(part); fr(counter);
@@ -612,20 +616,38 @@ int bapply(Engine& E, const T* K, const T* u, T* out, cudaStream_t s) {
 }
 
 // z = M^{-1} r for the live instances, one graph branch (stream) each
+// z = M^{-1} r for the live instances.  FP32 with the batched steps: one
+// lift launch for all instances, then each instance's two tcgen05 sweeps
+// as a branch, then one face launch and the boundary-line launches for all
+// instances; other instances run their whole preconditioner in their branch.
 template <typename T>
 int bprecond(Engine& E, const std::vector<int>& live, const T* r, T* z, cudaStream_t s) {
   if (E.precond != CHEB_PRECOND_FDM) {
     CHEB_CUDA(cudaMemcpyAsync(z, r, sizeof(T) * (size_t)E.total, cudaMemcpyDeviceToDevice, s));
     return CHEB_OK;
   }
-  CHEB_CUDA(cudaEventRecord(E.fork, s));
   int st = CHEB_OK;
+  bool batched = false;
+  if constexpr (sizeof(T) == 4) {
+    batched = E.fb != nullptr;
+    if (batched && (st = fdm_batch_lift(E.fb, r, s))) return st;
+  }
+  CHEB_CUDA(cudaEventRecord(E.fork, s));
   for (int i : live) {
     CHEB_CUDA(cudaStreamWaitEvent(E.bs[i], E.fork, 0));
-    if ((st = fdm_apply<T>(E.plans[i], *E.fdm[i], E.kref[i], r + E.off[i], z + E.off[i], E.bs[i]))) return st;
+    if constexpr (sizeof(T) == 4) {
+      if (batched && E.in_fb[i]) st = fdm_rot_core(E.plans[i], *E.fdm[i], E.kref[i], r + E.off[i], z + E.off[i], E.bs[i]);
+      else st = fdm_apply<T>(E.plans[i], *E.fdm[i], E.kref[i], r + E.off[i], z + E.off[i], E.bs[i]);
+    } else {
+      st = fdm_apply<T>(E.plans[i], *E.fdm[i], E.kref[i], r + E.off[i], z + E.off[i], E.bs[i]);
+    }
+    if (st) return st;
     CHEB_CUDA(cudaEventRecord(E.join[i], E.bs[i]));
   }
   for (int i : live) CHEB_CUDA(cudaStreamWaitEvent(s, E.join[i], 0));
+  if constexpr (sizeof(T) == 4) {
+    if (batched && (st = fdm_batch_faces(E.fb, r, z, s))) return st;
+  }
   return CHEB_OK;
 }
 
@@ -948,6 +970,30 @@ int bsolve(Engine& E, std::vector<int> live, const cheb_solve_opts& o, const dou
                                      : fdm_prepare<float>(E.plans[i], *E.fdm[i], s);
       if (st) return st;
     }
+  // FP32: the lift, face and boundary-line steps of the instances with the
+  // tcgen05 route run batched (their per-instance kref in the work list)
+  if (E.precond == CHEB_PRECOND_FDM && o.mode == CHEB_SOLVE_MIXED) {
+    if (!E.fb) {
+      std::vector<const cheb_plan_s*> bp;
+      std::vector<Fdm*> bf;
+      std::vector<long long> bo;
+      E.in_fb.assign(E.B, 0);
+      for (int i = 0; i < E.B; ++i)
+        if (fdm_batchable(E.plans[i], *E.fdm[i])) {
+          E.in_fb[i] = 1;
+          bp.push_back(E.plans[i]);
+          bf.push_back(E.fdm[i]);
+          bo.push_back(E.off[i]);
+        }
+      if (!bp.empty() && (st = fdm_batch_create(&E.fb, bp, bf, bo))) return st;
+    }
+    if (E.fb) {
+      std::vector<double> kb;
+      for (int i = 0; i < E.B; ++i)
+        if (E.in_fb[i]) kb.push_back(E.kref[i]);
+      if ((st = fdm_batch_kref(E.fb, kb))) return st;
+    }
+  }
   const long long n = E.total;
   BStats stt;
   stt.init(E.B);

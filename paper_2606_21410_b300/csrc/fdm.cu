@@ -13,6 +13,7 @@
 //    solved on its owner axis' line (1x1 or 2x2) once the line interior is
 //    known, edges before corners.
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <cstdlib>
 #include <vector>
@@ -234,10 +235,12 @@ __device__ __forceinline__ uint32_t cpos(const FdmK<T>& t, int ci, int cj, int c
 // consecutive z entries of one (x, y) column (independent loads in flight;
 // the z-end values of the column are read once).
 constexpr int kLiftK = 8;
+// (block coordinates explicit: the kernel below and the batched lift share it)
 template <typename T>
-__global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__ r, T* __restrict__ U) {
+__device__ __forceinline__ void fdm_lift_body(const Geom& g, const FdmK<T>& t, T kref, const T* __restrict__ r,
+                                              T* __restrict__ U, int bx, int by, int bz) {
   if (t.active && *t.active == 0) return;  // converged batch instance
-  const int ci = blockIdx.x * blockDim.x + threadIdx.x, cj = blockIdx.y;
+  const int ci = bx * blockDim.x + threadIdx.x, cj = by;
   if (ci >= t.m[0]) return;
   const int i = ci + t.off[0], j = cj + t.off[1];
   const int s1 = g.n[0], s2 = g.n[0] * g.n[1];
@@ -248,7 +251,7 @@ __global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__
     rz0 = r[j * s1 + i];
     rzN = r[(g.n[2] - 1) * s2 + j * s1 + i];
   }
-  const int ck0 = blockIdx.z * kLiftK, ck1 = min(ck0 + kLiftK, t.m[2]);
+  const int ck0 = bz * kLiftK, ck1 = min(ck0 + kLiftK, t.m[2]);
 #pragma unroll 4
   for (int ck = ck0; ck < ck1; ++ck) {
     const int k = ck + t.off[2];
@@ -258,6 +261,11 @@ __global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__
     if (g.dim > 2) v += kref * (t.Lh[2][2 * ck] * rz0 + t.Lh[2][2 * ck + 1] * rzN);
     U[cpos(t, ci, cj, ck)] = v;
   }
+}
+
+template <typename T>
+__global__ void fdm_lift_kernel(Geom g, FdmK<T> t, T kref, const T* __restrict__ r, T* __restrict__ U) {
+  fdm_lift_body(g, t, kref, r, U, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 template <typename T>
@@ -291,8 +299,9 @@ struct FdmSrc {
 // entries of G (m <= 255 < 8 * 32) in registers for all its lines, loads its
 // eight line values at once and the warp combines with shuffles.
 template <typename T>
-__global__ void __launch_bounds__(256) fdm_faces_x_kernel(Geom g, FdmK<T> t, FdmSrc<T> u,
-                                                          const T* __restrict__ r, T* __restrict__ x) {
+__device__ __forceinline__ void fdm_faces_x_body(const Geom& g, const FdmK<T>& t, const FdmSrc<T>& u,
+                                                 const T* __restrict__ r, T* __restrict__ x, int blk,
+                                                 int nblk) {
   if (t.active && *t.active == 0) return;  // converged batch instance
   const int ma = t.m[0];
   const int lines = t.m[1] * t.m[2];
@@ -305,8 +314,8 @@ __global__ void __launch_bounds__(256) fdm_faces_x_kernel(Geom g, FdmK<T> t, Fdm
     gN[q] = l < ma ? t.G[0][ma + l] : T(0);
   }
   const T* Bi = t.Binv[0];
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int L = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; L < lines; L += nw) {
+  const int nw = (nblk * blockDim.x) >> 5;
+  for (int L = (blk * blockDim.x + threadIdx.x) >> 5; L < lines; L += nw) {
     const int cj = L % t.m[1], ck = L / t.m[1];
     const T* line = u.p + u.off + cj * u.s1 + ck * u.s2;
     T v[8];
@@ -336,16 +345,23 @@ __global__ void __launch_bounds__(256) fdm_faces_x_kernel(Geom g, FdmK<T> t, Fdm
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) fdm_faces_x_kernel(Geom g, FdmK<T> t, FdmSrc<T> u,
+                                                          const T* __restrict__ r, T* __restrict__ x) {
+  fdm_faces_x_body(g, t, u, r, x, blockIdx.x, gridDim.x);
+}
+
 // Same for the y (a = 1) or z (a = 2) lines: a 32 x 8 block takes 32
 // x-adjacent lines (coalesced reads), its 8 rows split the line and reduce
 // through shared memory.  Grid: (ceil(m_x / 32), m_other).
 template <typename T>
-__global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, int a, FdmSrc<T> u,
-                                                           const T* __restrict__ r, T* __restrict__ x) {
+__device__ __forceinline__ void fdm_faces_yz_body(const Geom& g, const FdmK<T>& t, int a, const FdmSrc<T>& u,
+                                                  const T* __restrict__ r, T* __restrict__ x, int bx,
+                                                  int by) {
   if (t.active && *t.active == 0) return;  // converged batch instance
   __shared__ T red[2][8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int ci = blockIdx.x * 32 + tx, co = blockIdx.y;
+  const int ci = bx * 32 + tx, co = by;
   const int ma = t.m[a];
   const long long sl = a == 1 ? u.s1 : u.s2, so = a == 1 ? u.s2 : u.s1;
   const T* G0 = t.G[a];
@@ -382,6 +398,12 @@ __global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, in
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, int a, FdmSrc<T> u,
+                                                           const T* __restrict__ r, T* __restrict__ x) {
+  fdm_faces_yz_body(g, t, a, u, r, x, blockIdx.x, blockIdx.y);
+}
+
 // Boundary-row solve on a-lines that lie in one face (kind 1: the third
 // index interior) or in two faces (kind 2), one warp per line.  End nodes
 // owned by a Neumann face of axis a are solved from their rows
@@ -391,8 +413,8 @@ __global__ void __launch_bounds__(256) fdm_faces_yz_kernel(Geom g, FdmK<T> t, in
 // end the lower axis wins among Neumann faces), so the axes run in
 // increasing order, one launch each.
 template <typename T>
-__global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __restrict__ r,
-                                 T* __restrict__ x) {
+__device__ __forceinline__ void fdm_bline_body(const Geom& g, const FdmK<T>& t, int a, int kind,
+                                               const T* __restrict__ r, T* __restrict__ x, int blk, int nblk) {
   if (t.active && *t.active == 0) return;  // converged batch instance
   const int nb_axes = g.dim - 1;  // other active axes
   int others[2], no = 0;
@@ -416,7 +438,7 @@ __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __
   const T* D0 = t.Drow[a];
   const T* DN = t.Drow[a] + n;
   const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int L = blockIdx.x * wpb + (threadIdx.x >> 5); L < total; L += gridDim.x * wpb) {
+  for (int L = blk * wpb + (threadIdx.x >> 5); L < total; L += nblk * wpb) {
     int idx[3] = {0, 0, 0};
     if (kind == 1) {
       int rest = L, q = 0;
@@ -479,6 +501,11 @@ __global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __
       x[pN] = (b1 - a10 * x0) / a11;
     }
   }
+}
+template <typename T>
+__global__ void fdm_bline_kernel(Geom g, FdmK<T> t, int a, int kind, const T* __restrict__ r,
+                                 T* __restrict__ x) {
+  fdm_bline_body(g, t, a, kind, r, x, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -908,6 +935,201 @@ int fdm_apply(const cheb_plan_s* p, Fdm& f, double kref, const T* r, T* x, cudaS
 
 template int fdm_apply<double>(const cheb_plan_s*, Fdm&, double, const double*, double*, cudaStream_t);
 template int fdm_apply<float>(const cheb_plan_s*, Fdm&, double, const float*, float*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Batched preconditioner steps of lockstep batch solves: the lift, the face
+// steps and the boundary-line passes of several instances in one launch
+// each, over a work list of (instance, block) items; each instance's two
+// tcgen05 sweeps (fdm_rot_core) run between them.  The split is that of
+// the FP32 tcgen05 path of fdm_apply: lift, sweep S^{-1} (eigenvalue
+// division fused), sweep S (the last axis' end values written by its
+// epilogue), faces of the other axes, boundary lines.
+// ---------------------------------------------------------------------------
+struct FdmBItem {
+  Geom g;
+  FdmK<float> k;
+  float kref;
+  long long off;                   // offset of the instance in the batch vectors
+  float* U0;                       // its compact work array (lift output)
+  long long xs_off, xs_s1, xs_s2;  // interior of x as face-step source, relative to x + off
+  int lgx, lgy, lgz;               // lift grid
+  int fx_blocks;                   // face step of axis 0: blocks
+  int fy_gx, fy_gy;                // face step of axis 1 (3-D): grid
+};
+
+struct FdmBatch {
+  int count = 0, dim = 3;
+  std::vector<FdmBItem> h;
+  FdmBItem* d_items = nullptr;
+  int* d_pref[4] = {nullptr, nullptr, nullptr, nullptr};  // lift, faces, lines kind 1, kind 2
+  int nblk[4] = {0, 0, 0, 0};
+};
+
+bool fdm_batchable(const cheb_plan_s* p, const Fdm& f) {
+  return f.ready && f.rot && !has_flux(p) && p->dim >= 2 && f.U32[0] != nullptr;
+}
+
+// item of block b: the last i with pref[i] <= b
+__device__ __forceinline__ int fdm_item_of(const int* __restrict__ pref, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(128) fdm_lift_batch_kernel(const FdmBItem* __restrict__ items,
+                                                             const int* __restrict__ pref, int count,
+                                                             const float* __restrict__ rb) {
+  const int i = fdm_item_of(pref, count, blockIdx.x);
+  const FdmBItem& it = items[i];
+  const int lb = blockIdx.x - pref[i];
+  const int bx = lb % it.lgx, by = (lb / it.lgx) % it.lgy, bz = lb / (it.lgx * it.lgy);
+  fdm_lift_body<float>(it.g, it.k, it.kref, rb + it.off, it.U0, bx, by, bz);
+}
+
+__global__ void __launch_bounds__(256) fdm_faces_batch_kernel(const FdmBItem* __restrict__ items,
+                                                              const int* __restrict__ pref, int count,
+                                                              const float* __restrict__ rb, float* __restrict__ xb) {
+  const int i = fdm_item_of(pref, count, blockIdx.x);
+  const FdmBItem& it = items[i];
+  const int lb = blockIdx.x - pref[i];
+  float* x = xb + it.off;
+  const FdmSrc<float> u{x, it.xs_off, it.xs_s1, it.xs_s2};
+  // the two face steps write disjoint nodes and read only interior nodes
+  if (lb < it.fx_blocks) {
+    fdm_faces_x_body<float>(it.g, it.k, u, rb + it.off, x, lb, it.fx_blocks);
+  } else {
+    const int q = lb - it.fx_blocks;
+    fdm_faces_yz_body<float>(it.g, it.k, 1, u, rb + it.off, x, q % it.fy_gx, q / it.fy_gx);
+  }
+}
+
+__global__ void __launch_bounds__(256) fdm_bline_batch_kernel(const FdmBItem* __restrict__ items,
+                                                              const int* __restrict__ pref, int count, int a,
+                                                              int kind, const float* __restrict__ rb,
+                                                              float* __restrict__ xb) {
+  const int i = fdm_item_of(pref, count, blockIdx.x);
+  const FdmBItem& it = items[i];
+  fdm_bline_body<float>(it.g, it.k, a, kind, rb + it.off, xb + it.off, blockIdx.x - pref[i],
+                        pref[i + 1] - pref[i]);
+}
+
+int fdm_batch_create(FdmBatch** out, const std::vector<const cheb_plan_s*>& plans, const std::vector<Fdm*>& fdms,
+                     const std::vector<long long>& off) {
+  FdmBatch* b = new FdmBatch();
+  auto fail = [&](int st) { fdm_batch_free(b); return st; };
+  b->count = (int)plans.size();
+  if (b->count == 0) { *out = b; return CHEB_OK; }
+  b->dim = plans[0]->dim;
+  b->h.resize(b->count);
+  std::vector<int> pref[4];
+  for (auto& v : pref) v.assign(1, 0);
+  for (int i = 0; i < b->count; ++i) {
+    const cheb_plan_s* p = plans[i];
+    Fdm& f = *fdms[i];
+    if (!fdm_batchable(p, f) || p->dim != b->dim) { set_error("instance not batchable"); return fail(CHEB_ERR_ARG); }
+    FdmBItem& it = b->h[i];
+    std::memset(&it, 0, sizeof(it));
+    it.g = p->geom();
+    it.k = make_k<float>(f, p->dim);
+    it.kref = 1.f;
+    it.off = off[i];
+    it.U0 = f.U32[0];
+    const FdmSrc<float> xs = full_src<float>(p, (const float*)nullptr);
+    it.xs_off = xs.off;
+    it.xs_s1 = xs.s1;
+    it.xs_s2 = xs.s2;
+    it.lgx = (f.m[0] + 127) / 128;
+    it.lgy = f.m[1];
+    it.lgz = (f.m[2] + kLiftK - 1) / kLiftK;
+    it.fx_blocks = grid_for((size_t)f.m[1] * f.m[2] * 32);
+    if (p->dim == 3) {
+      it.fy_gx = (f.m[0] + 31) / 32;
+      it.fy_gy = f.m[2];
+    } else {
+      it.fy_gx = 1;
+      it.fy_gy = 0;
+    }
+    pref[0].push_back(pref[0].back() + it.lgx * it.lgy * it.lgz);
+    pref[1].push_back(pref[1].back() + it.fx_blocks + it.fy_gx * it.fy_gy);
+    pref[2].push_back(pref[2].back() + 64);
+    pref[3].push_back(pref[3].back() + 1);
+  }
+  if (cudaMalloc(&b->d_items, sizeof(FdmBItem) * b->count) != cudaSuccess) return fail(CHEB_ERR_NOMEM);
+  if (cudaMemcpy(b->d_items, b->h.data(), sizeof(FdmBItem) * b->count, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(CHEB_ERR_CUDA);
+  for (int q = 0; q < 4; ++q) {
+    b->nblk[q] = pref[q].back();
+    if (cudaMalloc(&b->d_pref[q], sizeof(int) * pref[q].size()) != cudaSuccess) return fail(CHEB_ERR_NOMEM);
+    if (cudaMemcpy(b->d_pref[q], pref[q].data(), sizeof(int) * pref[q].size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return fail(CHEB_ERR_CUDA);
+  }
+  *out = b;
+  return CHEB_OK;
+}
+
+int fdm_batch_kref(FdmBatch* b, const std::vector<double>& kref) {
+  if (!b || b->count == 0) return CHEB_OK;
+  for (int i = 0; i < b->count; ++i) b->h[i].kref = (float)kref[i];
+  CHEB_CUDA(cudaMemcpy(b->d_items, b->h.data(), sizeof(FdmBItem) * b->count, cudaMemcpyHostToDevice));
+  return CHEB_OK;
+}
+
+void fdm_batch_free(FdmBatch* b) {
+  if (!b) return;
+  cudaFree(b->d_items);
+  for (auto* p : b->d_pref) cudaFree(p);
+  delete b;
+}
+
+int fdm_batch_lift(const FdmBatch* b, const float* rb, cudaStream_t s) {
+  if (!b || b->count == 0) return CHEB_OK;
+  fdm_lift_batch_kernel<<<b->nblk[0], 128, 0, s>>>(b->d_items, b->d_pref[0], b->count, rb);
+  CHEB_LAUNCH_CHECK("fdm_lift_batch_kernel");
+  return CHEB_OK;
+}
+
+int fdm_batch_faces(const FdmBatch* b, const float* rb, float* xb, cudaStream_t s) {
+  if (!b || b->count == 0) return CHEB_OK;
+  fdm_faces_batch_kernel<<<b->nblk[1], 256, 0, s>>>(b->d_items, b->d_pref[1], b->count, rb, xb);
+  CHEB_LAUNCH_CHECK("fdm_faces_batch_kernel");
+  // boundary lines: axes in increasing order (an a-line may read an end a lower axis solved)
+  for (int a = 0; a < b->dim; ++a) {
+    fdm_bline_batch_kernel<<<b->nblk[2], 256, 0, s>>>(b->d_items, b->d_pref[2], b->count, a, 1, rb, xb);
+    CHEB_LAUNCH_CHECK("fdm_bline_batch_kernel");
+  }
+  if (b->dim == 3)
+    for (int a = 0; a < 3; ++a) {
+      fdm_bline_batch_kernel<<<b->nblk[3], 256, 0, s>>>(b->d_items, b->d_pref[3], b->count, a, 2, rb, xb);
+      CHEB_LAUNCH_CHECK("fdm_bline_batch_kernel");
+    }
+  return CHEB_OK;
+}
+
+// the two tcgen05 sweeps of the FP32 path, after the lift wrote U[0]
+int fdm_rot_core(const cheb_plan_s* p, Fdm& f, double kref, const float* r, float* x, cudaStream_t s) {
+  float** U = ubuf<float>(f);
+  int cur = 0, st;
+  if ((st = rot_sweep(p, f, U, cur, 1, epi_scale(p, f, kref), s))) return st;
+  UmmaEpi e;
+  e.mode = 2;
+  const FdmSrc<float> xs = full_src<float>(p, x);
+  const int L = p->dim - 1;
+  e.x = x;
+  e.r = r;
+  e.xoff = xs.off;
+  e.xs_f = 1;
+  e.xs_s = xs.s1;
+  e.xs_c = L == 2 ? xs.s2 : xs.s1;
+  e.ncol = p->n[L];
+  e.G = f.d32[L].G;
+  e.Binv = f.d32[L].Binv;
+  return rot_sweep(p, f, U, cur, 0, e, s);
+}
 
 template <typename T>
 int fdm_prepare(const cheb_plan_s* p, Fdm& f, cudaStream_t s) {

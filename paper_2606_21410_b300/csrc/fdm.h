@@ -63,6 +63,22 @@ int fdm_fill_boundary(const cheb_plan_s* p, Fdm& f, const T* r, T* x, cudaStream
 // graph may not allocate).
 template <typename T>
 int fdm_prepare(const cheb_plan_s* p, Fdm& f, cudaStream_t s);
+// Batched steps of lockstep batch solves (FP32, instances with the tcgen05
+// route and no flux faces): z = M^{-1} r for every instance of a batch is
+// fdm_batch_lift (all instances, one launch), fdm_rot_core per instance,
+// fdm_batch_faces (all instances: one launch for the face steps, one per
+// boundary-line stage).  Vectors are the batch's concatenated fields
+// (instance i at element off[i]); each instance's mask (Fdm::active) is
+// read by all of its kernels.
+struct FdmBatch;
+bool fdm_batchable(const cheb_plan_s* p, const Fdm& f);
+int fdm_batch_create(FdmBatch** out, const std::vector<const cheb_plan_s*>& plans, const std::vector<Fdm*>& fdms,
+                     const std::vector<long long>& off);
+int fdm_batch_kref(FdmBatch* b, const std::vector<double>& kref);
+void fdm_batch_free(FdmBatch* b);
+int fdm_batch_lift(const FdmBatch* b, const float* rb, cudaStream_t s);
+int fdm_batch_faces(const FdmBatch* b, const float* rb, float* xb, cudaStream_t s);
+int fdm_rot_core(const cheb_plan_s* p, Fdm& f, double kref, const float* r, float* x, cudaStream_t s);
 // z = M^{-T} y (for the adjoint solve).
 template <typename T>
 int fdm_apply_t(const cheb_plan_s* p, Fdm& f, double kref, const T* y, T* z, cudaStream_t s);

@@ -1547,10 +1547,9 @@ static int batch_route(int count, const cheb_plan* plans, const cheb_solve_opts&
   }
   if (o.batch_mode == CHEB_BATCH_AUTO && ok) {
     // Measured on B300 (Picard batches, 8 steps): lockstep wins where the
-    // instances are many or small (128 x 17^3: 2.8x, 64 x 33^3: 2.0x,
-    // 32 x 49^3: 1.2x), ties at 16 x 65^3 and trails by 15 % on 16 instances
-    // of 33^3 .. 97^3 (mean 363k points), where one solver per instance
-    // already fills the GPU.
+    // instances are many or small (64 x 33^3: 3.7x, 32 x 49^3: 1.7x), ties
+    // at 16 x 65^3 and trails by 14 % on 16 instances of 33^3 .. 97^3 (mean
+    // 363k points), where one solver per instance already fills the GPU.
     size_t tot = 0;
     for (int i = 0; i < count; ++i) tot += plans[i]->size();
     ok = count >= 32 || tot / (size_t)count <= 200000;
