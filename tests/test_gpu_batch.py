@@ -85,20 +85,29 @@ def test_batched_solve_matches_single_solves(batch_mode):
 def test_picard_batch_of_uneven_lognormal_instances():
     """The batched configuration's shape: uneven sizes drawn from U{33..97}
     (seed 1), lognormal K0 (sigma 0.5, correlation length 0.2), Picard with
-    beta = 0.5; here the first 4 instances, each checked for its fixed point."""
+    beta = 0.5; here the first 4 instances (63^3 .. 94^3: the preconditioner
+    takes its tcgen05 route, so lockstep runs the batched lift, face and
+    boundary-line steps), in both iteration modes, each instance against its
+    single-instance Picard solve."""
     import paper_2606_21410_b300 as P
     sizes = W.batch_sizes(1)[:4]
     items = [_instance((n, n, n), 100 + i) for i, n in enumerate(sizes)]
     plans = [it[0] for it in items]
     K0 = [_dev(it[1]) for it in items]
     b = [it[2] for it in items]
-    u, infos, its = P.picard_batched(plans, K0, b, beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1,
-                                     rtol=1e-12, use_graph=1)
+    single = []
     for i, p in enumerate(plans):
-        assert infos[i]["status"] == 0, (sizes[i], infos[i], its[i])
         us, _, its1, _ = p.picard_solve(K0[i], b[i], beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1,
                                         rtol=1e-12)
-        assert _rel(u[i].cpu().numpy(), us.cpu().numpy()) < 1e-9
+        single.append(us.cpu().numpy())
+    for bm in (LOCKSTEP, CONCURRENT):
+        u, infos, its = P.picard_batched(plans, K0, b, beta=0.5, tol=1e-9, maxit=60, omega=0.5, mode=1,
+                                         rtol=1e-12, use_graph=1, batch_mode=bm)
+        for i in range(len(plans)):
+            assert infos[i]["status"] == 0, (bm, sizes[i], infos[i], its[i])
+            assert _rel(u[i].cpu().numpy(), single[i]) < 1e-9, (bm, sizes[i])
+        if bm == LOCKSTEP:
+            assert infos[0]["graph_captures"] > 0
 
 
 @pytest.mark.parametrize("batch_mode", [LOCKSTEP, CONCURRENT])
@@ -137,7 +146,8 @@ def test_lockstep_converged_mask_and_uneven_instances(mode):
     solution equals the concurrent mode's and, for the small ones, the
     oracle's direct solve."""
     import paper_2606_21410_b300 as P
-    sizes = [(17, 17, 17), (25, 12, 7), (9, 9, 9), (33, 19, 11), (13, 13, 13), (11, 11, 11)]
+    # (33, 33, 33): the preconditioner's tcgen05 route, batched lift / face / line steps
+    sizes = [(17, 17, 17), (25, 12, 7), (9, 9, 9), (33, 19, 11), (13, 13, 13), (11, 11, 11), (33, 33, 33)]
     items = [_instance(n, 500 + i) for i, n in enumerate(sizes)]
     plans = [it[0] for it in items]
     K = [_dev(it[1]) for it in items]
