@@ -326,7 +326,8 @@ int cheb_newton_solve(cheb_plan plan, const double* K0, double alpha, const doub
  * call: about (restart + 2 augment + 5) FP32 and 8 FP64 words per DOF of the
  * batch), iterates all instances together, each leaving the iteration when
  * it converges, and copies u back; it waits for the plans' streams first and
- * runs on a private stream.  info.graph_captures counts the step graphs it
+ * runs on a private stream, and the plans must not be used by other calls
+ * until it returns (their preconditioners carry the call's mask).  info.graph_captures counts the step graphs it
  * captured.  CONCURRENT runs one host thread per instance on its plan's
  * stream (plans on the legacy NULL stream get a private stream for the
  * call).  Arrays have `count` entries; infos / picard_iters may be NULL.

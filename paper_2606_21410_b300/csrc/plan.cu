@@ -120,12 +120,45 @@ static int next_pow2(int v) {
   return p;
 }
 
+// In-place forward DFT of length L (a power of two), long double, on the
+// host: iterative radix-2 (bit reversal, then butterflies with exact-index
+// roots exp(-2 pi i q / L)).
+static void host_fft(std::vector<long double>& re, std::vector<long double>& im) {
+  const int L = (int)re.size();
+  for (int i = 1, j = 0; i < L; ++i) {
+    int bit = L >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      std::swap(re[i], re[j]);
+      std::swap(im[i], im[j]);
+    }
+  }
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> wr(L / 2), wi(L / 2);
+  for (int q = 0; q < L / 2; ++q) {
+    wr[q] = cosl(-2.0L * pi * (long double)q / (long double)L);
+    wi[q] = sinl(-2.0L * pi * (long double)q / (long double)L);
+  }
+  for (int len = 2; len <= L; len <<= 1) {
+    const int half = len >> 1, step = L / len;
+    for (int b = 0; b < L; b += len)
+      for (int k = 0; k < half; ++k) {
+        const long double cr = wr[k * step], ci = wi[k * step];
+        const long double xr = re[b + k + half] * cr - im[b + k + half] * ci;
+        const long double xi = re[b + k + half] * ci + im[b + k + half] * cr;
+        re[b + k + half] = re[b + k] - xr;
+        im[b + k + half] = im[b + k] - xi;
+        re[b + k] += xr;
+        im[b + k] += xi;
+      }
+  }
+}
+
 // Tables of the chirp-form DFT of length M = 2N with convolution length L
 // (Bluestein): c_j = exp(-i pi j^2 / M), j < M, with j^2 reduced mod 2M
 // before the angle is formed; bhat = FFT_L(b) / L, b_m = conj(c_m) at
-// m and L - m for 0 <= m < M, zero elsewhere.  Evaluated in long double, the
-// transform by direct summation over the 2M - 1 non-zero b_m with the
-// exponent m k reduced mod L.
+// m and L - m for 0 <= m < M, zero elsewhere.  Long double throughout.
 static void chirp_tables(int N, int L, std::vector<double2>& c, std::vector<double2>& bhat) {
   const int M = 2 * N;
   const long double pi = 3.141592653589793238462643383279502884L;
@@ -136,27 +169,20 @@ static void chirp_tables(int N, int L, std::vector<double2>& c, std::vector<doub
     cr[j] = cosl(ang);
     ci[j] = sinl(ang);
   }
-  std::vector<long double> wr(L), wi(L);  // exp(-2 pi i q / L)
-  for (int q = 0; q < L; ++q) {
-    const long double ang = -2.0L * pi * (long double)q / (long double)L;
-    wr[q] = cosl(ang);
-    wi[q] = sinl(ang);
-  }
   c.resize(M);
   for (int j = 0; j < M; ++j) c[j] = make_double2((double)cr[j], (double)ci[j]);
-  bhat.resize(L);
-  for (int k = 0; k < L; ++k) {
-    long double ar = 0, ai = 0;
-    for (int m = -(M - 1); m <= M - 1; ++m) {
-      const int am = m < 0 ? -m : m;
-      const int idx = (m + L) % L;                         // position of b_m
-      const long double br = cr[am], bi = -ci[am];         // conj(c_|m|)
-      const int q = (int)(((long long)idx * k) % L);
-      ar += br * wr[q] - bi * wi[q];
-      ai += br * wi[q] + bi * wr[q];
+  std::vector<long double> br(L, 0.0L), bi(L, 0.0L);
+  for (int m = 0; m < M; ++m) {
+    br[m] = cr[m];
+    bi[m] = -ci[m];  // conj(c_m)
+    if (m > 0) {
+      br[L - m] = cr[m];
+      bi[L - m] = -ci[m];
     }
-    bhat[k] = make_double2((double)(ar / L), (double)(ai / L));
   }
+  host_fft(br, bi);
+  bhat.resize(L);
+  for (int k = 0; k < L; ++k) bhat[k] = make_double2((double)(br[k] / L), (double)(bi[k] / L));
 }
 
 // Reference CGL coordinate x_j = cos(pi j / N), evaluated as
