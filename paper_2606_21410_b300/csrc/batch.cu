@@ -124,93 +124,149 @@ __device__ void bred_store(const BatchBlocks& bb, T (&acc)[MAXV], int cnt, bool 
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// out[i][l] = <src_l, w> over instance i, l < cnt; with_self: out[i][kMaxVecs] = <w, w>
-template <typename T>
-__global__ void __launch_bounds__(kBThreads)
-bmdot_kernel(BatchBlocks bb, VecList<T> src, int cnt, const T* __restrict__ w, int with_self,
+// 16-byte elements per thread and loop iteration: at least four independent
+// loads in flight.  Resident CTAs asked of the register allocator: one from 16
+// vectors on, where the loads in flight already cover the memory latency.
+template <int NLOADS>
+constexpr int bunroll() { return NLOADS >= 4 ? 1 : NLOADS >= 2 ? 2 : 4; }
+template <int NV>
+constexpr int bmin_ctas() { return NV >= 16 ? 1 : 2; }
+
+// out[i][l] = <src_l, w> over instance i, l < NV; with_self: out[i][NV] = <w, w>.
+// One instantiation per vector count NV, so no load or FMA of an absent
+// vector is issued.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kBThreads, bmin_ctas<NV>())
+bmdot_kernel(BatchBlocks bb, VecList<T> src, const T* __restrict__ w, int with_self,
              const int* __restrict__ act, double* part, unsigned* counter, double* out) {
   typedef typename BV<T>::t V;
   constexpr int W = BV<T>::W;
-  T acc[kMaxVecs + 1];
+  constexpr int U = bunroll<NV + 1>();
+  T acc[NV + 1];
 #pragma unroll
-  for (int l = 0; l <= kMaxVecs; ++l) acc[l] = (T)0;
+  for (int l = 0; l <= NV; ++l) acc[l] = (T)0;
   const int i = bb.inst[blockIdx.x];
   if (act[i]) {
     const long long lo = bb.lo[blockIdx.x], hi = bb.hi[blockIdx.x];
     const long long nv = (hi - lo) / W;
     const V* w4 = reinterpret_cast<const V*>(w + lo);
-    for (long long e = threadIdx.x; e < nv; e += blockDim.x) {
-      const V wv = w4[e];
+    long long e = threadIdx.x;
+    for (; e + (U - 1) * (long long)blockDim.x < nv; e += U * (long long)blockDim.x) {
+      V wv[U];
 #pragma unroll
-      for (int l = 0; l < kMaxVecs; ++l)
-        if (l < cnt) {
-          const V sv = reinterpret_cast<const V*>(src.p[l] + lo)[e];
+      for (int u = 0; u < U; ++u) wv[u] = w4[e + u * blockDim.x];
 #pragma unroll
-          for (int k = 0; k < W; ++k) acc[l] += bget<T>(sv, k) * bget<T>(wv, k);
+      for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int l = 0; l < NV; ++l) {
+          const V sv = reinterpret_cast<const V*>(src.p[l] + lo)[e + u * blockDim.x];
+#pragma unroll
+          for (int k = 0; k < W; ++k) acc[l] += bget<T>(sv, k) * bget<T>(wv[u], k);
         }
-      if (with_self) {
+        if (with_self) {
 #pragma unroll
-        for (int k = 0; k < W; ++k) acc[kMaxVecs] += bget<T>(wv, k) * bget<T>(wv, k);
+          for (int k = 0; k < W; ++k) acc[NV] += bget<T>(wv[u], k) * bget<T>(wv[u], k);
+        }
       }
     }
-    for (long long e = lo + nv * W + threadIdx.x; e < hi; e += blockDim.x) {
-      const T x = w[e];
+    for (; e < nv; e += blockDim.x) {
+      const V wv = w4[e];
 #pragma unroll
-      for (int l = 0; l < kMaxVecs; ++l)
-        if (l < cnt) acc[l] += src.p[l][e] * x;
-      if (with_self) acc[kMaxVecs] += x * x;
+      for (int l = 0; l < NV; ++l) {
+        const V sv = reinterpret_cast<const V*>(src.p[l] + lo)[e];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[l] += bget<T>(sv, k) * bget<T>(wv, k);
+      }
+      if (with_self) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[NV] += bget<T>(wv, k) * bget<T>(wv, k);
+      }
+    }
+    for (long long t = lo + nv * W + threadIdx.x; t < hi; t += blockDim.x) {
+      const T x = w[t];
+#pragma unroll
+      for (int l = 0; l < NV; ++l) acc[l] += src.p[l][t] * x;
+      if (with_self) acc[NV] += x * x;
     }
   }
-  bred_store<kMaxVecs + 1, T>(bb, acc, cnt, with_self != 0, part, counter, out, kDv);
+  bred_store<NV + 1, T>(bb, acc, NV, with_self != 0, part, counter, out, kDv);
 }
 
-// y_i = beta y_i + sum_l c_il src_l over instance i (c_il = csign cdev[i kDv + l],
-// or chost[i * cnt + l] when cdev is null); want_norm: |y_i|^2 -> norm[i kDv]
-template <typename T>
-__global__ void __launch_bounds__(kBThreads)
+// y_i = beta y_i + sum_l c_il src_l over instance i, l < NV (c_il = csign
+// cdev[i kDv + l], or cmat[i * NV + l] when cdev is null); want_norm:
+// |y_i|^2 -> norm[i kDv]
+template <typename T, int NV>
+__global__ void __launch_bounds__(kBThreads, bmin_ctas<NV>())
 bmaxpy_kernel(BatchBlocks bb, VecList<T> src, const double* __restrict__ cdev, double csign,
-              const double* __restrict__ cmat, int cnt, double beta, T* __restrict__ y,
+              const double* __restrict__ cmat, double beta, T* __restrict__ y,
               const int* __restrict__ act, int want_norm, double* part, unsigned* counter, double* norm) {
   typedef typename BV<T>::t V;
   constexpr int W = BV<T>::W;
+  constexpr int U = bunroll<NV + 1>();
   const int i = bb.inst[blockIdx.x];
   T acc[1] = {(T)0};
   if (act[i]) {
-    T c[kMaxVecs];
+    T c[NV > 0 ? NV : 1];
 #pragma unroll
-    for (int l = 0; l < kMaxVecs; ++l)
-      c[l] = l < cnt ? (T)(cdev ? csign * cdev[(size_t)i * kDv + l] : cmat[(size_t)i * cnt + l]) : (T)0;
+    for (int l = 0; l < NV; ++l)
+      c[l] = (T)(cdev ? csign * cdev[(size_t)i * kDv + l] : cmat[(size_t)i * NV + l]);
     const T b = (T)beta;
+    const bool keep = beta != 0.0;
     const long long lo = bb.lo[blockIdx.x], hi = bb.hi[blockIdx.x];
     const long long nv = (hi - lo) / W;
     V* y4 = reinterpret_cast<V*>(y + lo);
-    for (long long e = threadIdx.x; e < nv; e += blockDim.x) {
-      V v;
-      if (beta == 0.0) {
+    long long e = threadIdx.x;
+    for (; e + (U - 1) * (long long)blockDim.x < nv; e += U * (long long)blockDim.x) {
+      V v[U];
 #pragma unroll
-        for (int k = 0; k < W; ++k) bset<T>(v, k, (T)0);
-      } else {
+      for (int u = 0; u < U; ++u) {
+        if (keep) {
+          const V yo = y4[e + u * blockDim.x];
+#pragma unroll
+          for (int k = 0; k < W; ++k) bset<T>(v[u], k, b * bget<T>(yo, k));
+        } else {
+#pragma unroll
+          for (int k = 0; k < W; ++k) bset<T>(v[u], k, (T)0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int l = 0; l < NV; ++l) {
+          const V sv = reinterpret_cast<const V*>(src.p[l] + lo)[e + u * blockDim.x];
+#pragma unroll
+          for (int k = 0; k < W; ++k) bset<T>(v[u], k, bget<T>(v[u], k) + c[l] * bget<T>(sv, k));
+        }
+        y4[e + u * blockDim.x] = v[u];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[0] += bget<T>(v[u], k) * bget<T>(v[u], k);
+      }
+    }
+    for (; e < nv; e += blockDim.x) {
+      V v;
+      if (keep) {
         const V yo = y4[e];
 #pragma unroll
         for (int k = 0; k < W; ++k) bset<T>(v, k, b * bget<T>(yo, k));
+      } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) bset<T>(v, k, (T)0);
       }
 #pragma unroll
-      for (int l = 0; l < kMaxVecs; ++l)
-        if (l < cnt) {
-          const V sv = reinterpret_cast<const V*>(src.p[l] + lo)[e];
+      for (int l = 0; l < NV; ++l) {
+        const V sv = reinterpret_cast<const V*>(src.p[l] + lo)[e];
 #pragma unroll
-          for (int k = 0; k < W; ++k) bset<T>(v, k, bget<T>(v, k) + c[l] * bget<T>(sv, k));
-        }
+        for (int k = 0; k < W; ++k) bset<T>(v, k, bget<T>(v, k) + c[l] * bget<T>(sv, k));
+      }
       y4[e] = v;
 #pragma unroll
       for (int k = 0; k < W; ++k) acc[0] += bget<T>(v, k) * bget<T>(v, k);
     }
-    for (long long e = lo + nv * W + threadIdx.x; e < hi; e += blockDim.x) {
-      T v = (beta == 0.0) ? (T)0 : b * y[e];
+    for (long long t = lo + nv * W + threadIdx.x; t < hi; t += blockDim.x) {
+      T v = keep ? b * y[t] : (T)0;
 #pragma unroll
-      for (int l = 0; l < kMaxVecs; ++l)
-        if (l < cnt) v += c[l] * src.p[l][e];
-      y[e] = v;
+      for (int l = 0; l < NV; ++l) v += c[l] * src.p[l][t];
+      y[t] = v;
       acc[0] += v * v;
     }
   }
@@ -662,10 +718,12 @@ template <typename T>
 int bmdot(Engine& E, const T* const* src, int cnt, const T* w, bool with_self, const int* mask, cudaStream_t s) {
   VecList<T> vl;
   for (int l = 0; l < kMaxVecs; ++l) vl.p[l] = l < cnt ? src[l] : nullptr;
-  bmdot_kernel<T><<<E.bb.nblk, kBThreads, 0, s>>>(E.bb, vl, cnt, w, with_self ? 1 : 0, mask, E.part, E.counter,
-                                                  E.dv);
-  CHEB_LAUNCH_CHECK("bmdot_kernel");
-  return CHEB_OK;
+  return count_dispatch(cnt, [&](auto c) -> int {
+    bmdot_kernel<T, decltype(c)::value><<<E.bb.nblk, kBThreads, 0, s>>>(E.bb, vl, w, with_self ? 1 : 0, mask,
+                                                                        E.part, E.counter, E.dv);
+    CHEB_LAUNCH_CHECK("bmdot_kernel");
+    return CHEB_OK;
+  });
 }
 
 // y = beta y + sum_l c_l src_l: coefficients from dv (dev, sign) or from the
@@ -673,6 +731,7 @@ int bmdot(Engine& E, const T* const* src, int cnt, const T* w, bool with_self, c
 template <typename T>
 int bmaxpy(Engine& E, const T* const* src, int cnt, bool from_dv, double sign, const double* hmat, double beta,
            T* y, const int* mask, bool want_norm, cudaStream_t s) {
+  if (cnt < 0 || cnt > kMaxVecs) { set_error("bad vector count in a batched multi-axpy"); return CHEB_ERR_ARG; }
   VecList<T> vl;
   for (int l = 0; l < kMaxVecs; ++l) vl.p[l] = l < cnt ? src[l] : nullptr;
   const double* cm = nullptr;
@@ -682,10 +741,12 @@ int bmaxpy(Engine& E, const T* const* src, int cnt, bool from_dv, double sign, c
     CHEB_CUDA(cudaMemcpyAsync(E.coef, hmat, sizeof(double) * (size_t)E.B * cnt, cudaMemcpyHostToDevice, s));
     cm = E.coef;
   }
-  bmaxpy_kernel<T><<<E.bb.nblk, kBThreads, 0, s>>>(E.bb, vl, from_dv ? E.dv : nullptr, sign, cm, cnt, beta, y, mask,
-                                                   want_norm ? 1 : 0, E.part, E.counter, E.dv);
-  CHEB_LAUNCH_CHECK("bmaxpy_kernel");
-  return CHEB_OK;
+  return count_dispatch(cnt, [&](auto c) -> int {
+    bmaxpy_kernel<T, decltype(c)::value><<<E.bb.nblk, kBThreads, 0, s>>>(
+        E.bb, vl, from_dv ? E.dv : nullptr, sign, cm, beta, y, mask, want_norm ? 1 : 0, E.part, E.counter, E.dv);
+    CHEB_LAUNCH_CHECK("bmaxpy_kernel");
+    return CHEB_OK;
+  });
 }
 
 // y = f_i x with host factors f (copied to the device)

@@ -99,88 +99,144 @@ template <> struct Vec16<double> {
   }
 };
 
-// out[i] = <src_i, w>, i < cnt (cnt <= kMaxVecs); optionally also <w, w>
-// stored at out[cnt].  16-byte vector loads; element-wise tail.
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
-mdot_kernel(VecList<T> src, int cnt, const T* __restrict__ w, size_t n, int with_self, int vec,
-            double* part, unsigned* counter, double* out) {
+// Elements per thread and loop iteration of the fused kernels: enough that a
+// thread has at least four independent 16-byte loads in flight.
+template <int NLOADS>
+constexpr int unroll_for() { return NLOADS >= 4 ? 1 : NLOADS >= 2 ? 2 : 4; }
+// Resident CTAs asked of the register allocator: two below 16 vectors, one
+// above, where a thread's 16 or more loads in flight already cover the
+// memory latency and the larger register budget avoids spills.
+template <int NV>
+constexpr int min_ctas() { return NV >= 16 ? 1 : 2; }
+
+// out[i] = <src_i, w>, i < NV; with_self: also <w, w>, stored at out[NV].
+// 16-byte vector loads (when vec), element-wise tail.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kRedThreads, min_ctas<NV>())
+mdot_kernel(VecList<T> src, const T* __restrict__ w, size_t n, int with_self, int vec, double* part,
+            unsigned* counter, double* out) {
   typedef typename Vec16<T>::t V;
   constexpr int W = Vec16<T>::W;
-  T acc[kMaxVecs + 1];
+  constexpr int U = unroll_for<NV + 1>();
+  T acc[NV + 1];
 #pragma unroll
-  for (int i = 0; i <= kMaxVecs; ++i) acc[i] = (T)0;
+  for (int i = 0; i <= NV; ++i) acc[i] = (T)0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t nv = vec ? n / W : 0;
   const V* wv4 = reinterpret_cast<const V*>(w);
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nv; e += stride) {
-    const V wv = wv4[e];
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + (U - 1) * stride < nv; e += U * stride) {
+    V wv[U];
 #pragma unroll
-    for (int i = 0; i < kMaxVecs; ++i)
-      if (i < cnt) {
-        const V sv = reinterpret_cast<const V*>(src.p[i])[e];
+    for (int u = 0; u < U; ++u) wv[u] = wv4[e + u * stride];
 #pragma unroll
-        for (int k = 0; k < W; ++k) acc[i] += Vec16<T>::at(sv, k) * Vec16<T>::at(wv, k);
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const V sv = reinterpret_cast<const V*>(src.p[i])[e + u * stride];
+#pragma unroll
+        for (int k = 0; k < W; ++k) acc[i] += Vec16<T>::at(sv, k) * Vec16<T>::at(wv[u], k);
       }
-    if (with_self) {
+      if (with_self) {
 #pragma unroll
-      for (int k = 0; k < W; ++k) acc[kMaxVecs] += Vec16<T>::at(wv, k) * Vec16<T>::at(wv, k);
+        for (int k = 0; k < W; ++k) acc[NV] += Vec16<T>::at(wv[u], k) * Vec16<T>::at(wv[u], k);
+      }
     }
   }
-  for (size_t e = nv * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-    const T x = w[e];
+  for (; e < nv; e += stride) {
+    const V wv = wv4[e];
 #pragma unroll
-    for (int i = 0; i < kMaxVecs; ++i)
-      if (i < cnt) acc[i] += src.p[i][e] * x;
-    if (with_self) acc[kMaxVecs] += x * x;
+    for (int i = 0; i < NV; ++i) {
+      const V sv = reinterpret_cast<const V*>(src.p[i])[e];
+#pragma unroll
+      for (int k = 0; k < W; ++k) acc[i] += Vec16<T>::at(sv, k) * Vec16<T>::at(wv, k);
+    }
+    if (with_self) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) acc[NV] += Vec16<T>::at(wv, k) * Vec16<T>::at(wv, k);
+    }
   }
-  block_reduce_store<T, kMaxVecs + 1>(acc, cnt, with_self != 0, part, counter, out);
+  for (size_t t = nv * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += stride) {
+    const T x = w[t];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] += src.p[i][t] * x;
+    if (with_self) acc[NV] += x * x;
+  }
+  block_reduce_store<T, NV + 1>(acc, NV, with_self != 0, part, counter, out);
 }
 
-// y = beta * y + sum_i c_i src_i (cnt <= kMaxVecs); optionally ||y||^2 -> out[0].
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads)
-maxpy_kernel(VecList<T> src, CoefList coef, const double* __restrict__ cdev, double csign, int cnt,
-             double beta, T* __restrict__ y, size_t n, int want_norm, int vec, double* part,
-             unsigned* counter, double* out) {
+// y = beta * y + sum_i c_i src_i, i < NV; c_i = csign * cdev[i] when cdev,
+// else coef.c[i].  want_norm: ||y||^2 -> out[0].
+template <typename T, int NV>
+__global__ void __launch_bounds__(kRedThreads, min_ctas<NV>())
+maxpy_kernel(VecList<T> src, CoefList coef, const double* __restrict__ cdev, double csign, double beta,
+             T* __restrict__ y, size_t n, int want_norm, int vec, double* part, unsigned* counter,
+             double* out) {
   typedef typename Vec16<T>::t V;
   constexpr int W = Vec16<T>::W;
-  T c[kMaxVecs];
+  constexpr int U = unroll_for<NV + 1>();
+  T c[NV > 0 ? NV : 1];
 #pragma unroll
-  for (int i = 0; i < kMaxVecs; ++i)
-    c[i] = (T)(cdev ? (i < cnt ? csign * cdev[i] : 0.0) : coef.c[i]);
+  for (int i = 0; i < NV; ++i) c[i] = (T)(cdev ? csign * cdev[i] : coef.c[i]);
   T acc[1] = {(T)0};
   const T b = (T)beta;
+  const bool keep = beta != 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t nv = vec ? n / W : 0;
   V* y4 = reinterpret_cast<V*>(y);
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nv; e += stride) {
-    V v;
-    if (beta == 0.0) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + (U - 1) * stride < nv; e += U * stride) {
+    V v[U];
 #pragma unroll
-      for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, (T)0);
-    } else {
+    for (int u = 0; u < U; ++u) {
+      if (keep) {
+        const V yo = y4[e + u * stride];
+#pragma unroll
+        for (int k = 0; k < W; ++k) Vec16<T>::set(v[u], k, b * Vec16<T>::at(yo, k));
+      } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) Vec16<T>::set(v[u], k, (T)0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        const V sv = reinterpret_cast<const V*>(src.p[i])[e + u * stride];
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+          Vec16<T>::set(v[u], k, Vec16<T>::at(v[u], k) + c[i] * Vec16<T>::at(sv, k));
+      }
+      y4[e + u * stride] = v[u];
+#pragma unroll
+      for (int k = 0; k < W; ++k) acc[0] += Vec16<T>::at(v[u], k) * Vec16<T>::at(v[u], k);
+    }
+  }
+  for (; e < nv; e += stride) {
+    V v;
+    if (keep) {
       const V yo = y4[e];
 #pragma unroll
       for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, b * Vec16<T>::at(yo, k));
+    } else {
+#pragma unroll
+      for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, (T)0);
     }
 #pragma unroll
-    for (int i = 0; i < kMaxVecs; ++i)
-      if (i < cnt) {
-        const V sv = reinterpret_cast<const V*>(src.p[i])[e];
+    for (int i = 0; i < NV; ++i) {
+      const V sv = reinterpret_cast<const V*>(src.p[i])[e];
 #pragma unroll
-        for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, Vec16<T>::at(v, k) + c[i] * Vec16<T>::at(sv, k));
-      }
+      for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, Vec16<T>::at(v, k) + c[i] * Vec16<T>::at(sv, k));
+    }
     y4[e] = v;
 #pragma unroll
     for (int k = 0; k < W; ++k) acc[0] += Vec16<T>::at(v, k) * Vec16<T>::at(v, k);
   }
-  for (size_t e = nv * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
-    T v = (beta == 0.0) ? (T)0 : b * y[e];
+  for (size_t t = nv * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += stride) {
+    T v = keep ? b * y[t] : (T)0;
 #pragma unroll
-    for (int i = 0; i < kMaxVecs; ++i)
-      if (i < cnt) v += c[i] * src.p[i][e];
-    y[e] = v;
+    for (int i = 0; i < NV; ++i) v += c[i] * src.p[i][t];
+    y[t] = v;
     acc[0] += v * v;
   }
   if (want_norm) block_reduce_store<T, 1>(acc, 1, false, part, counter, out);
@@ -229,7 +285,7 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 template <typename T>
 int k_mdot(const ReduceScratch& rs, const T* const* src, int cnt, const T* w, size_t n,
            bool with_self, double* out_dev, cudaStream_t s) {
-  if (cnt > kMaxVecs) { set_error("too many vectors in multi-dot"); return CHEB_ERR_ARG; }
+  if (cnt < 0 || cnt > kMaxVecs) { set_error("bad vector count in multi-dot"); return CHEB_ERR_ARG; }
   VecList<T> L;
   bool vec = aligned16(w);
   for (int i = 0; i < kMaxVecs; ++i) {
@@ -237,48 +293,46 @@ int k_mdot(const ReduceScratch& rs, const T* const* src, int cnt, const T* w, si
     if (i < cnt) vec = vec && aligned16(src[i]);
   }
   const int nb = red_blocks(n);
-  mdot_kernel<T><<<nb, kRedThreads, 0, s>>>(L, cnt, w, n, with_self ? 1 : 0, vec ? 1 : 0, rs.part, rs.counter,
-                                            out_dev);
-  CHEB_LAUNCH_CHECK("mdot_kernel");
-  return CHEB_OK;
+  return count_dispatch(cnt, [&](auto c) -> int {
+    mdot_kernel<T, decltype(c)::value><<<nb, kRedThreads, 0, s>>>(L, w, n, with_self ? 1 : 0, vec ? 1 : 0,
+                                                                  rs.part, rs.counter, out_dev);
+    CHEB_LAUNCH_CHECK("mdot_kernel");
+    return CHEB_OK;
+  });
+}
+
+template <typename T>
+static int maxpy_launch(const ReduceScratch& rs, const T* const* src, const double* coef, const double* coef_dev,
+                        double sign, int cnt, double beta, T* y, size_t n, double* norm2_dev, cudaStream_t s) {
+  if (cnt < 0 || cnt > kMaxVecs) { set_error("bad vector count in multi-axpy"); return CHEB_ERR_ARG; }
+  VecList<T> L;
+  CoefList C;
+  bool vec = aligned16(y);
+  for (int i = 0; i < kMaxVecs; ++i) {
+    L.p[i] = i < cnt ? src[i] : nullptr;
+    C.c[i] = (i < cnt && coef) ? coef[i] : 0.0;
+    if (i < cnt) vec = vec && aligned16(src[i]);
+  }
+  const int nb = red_blocks(n);
+  return count_dispatch(cnt, [&](auto c) -> int {
+    maxpy_kernel<T, decltype(c)::value><<<nb, kRedThreads, 0, s>>>(L, C, coef_dev, sign, beta, y, n,
+                                                                   norm2_dev ? 1 : 0, vec ? 1 : 0, rs.part,
+                                                                   rs.counter, norm2_dev);
+    CHEB_LAUNCH_CHECK("maxpy_kernel");
+    return CHEB_OK;
+  });
 }
 
 template <typename T>
 int k_maxpy(const ReduceScratch& rs, const T* const* src, const double* coef, int cnt, double beta,
             T* y, size_t n, double* norm2_dev, cudaStream_t s) {
-  if (cnt > kMaxVecs) { set_error("too many vectors in multi-axpy"); return CHEB_ERR_ARG; }
-  VecList<T> L;
-  CoefList C;
-  bool vec = aligned16(y);
-  for (int i = 0; i < kMaxVecs; ++i) {
-    L.p[i] = i < cnt ? src[i] : nullptr;
-    C.c[i] = i < cnt ? coef[i] : 0.0;
-    if (i < cnt) vec = vec && aligned16(src[i]);
-  }
-  const int nb = red_blocks(n);
-  maxpy_kernel<T><<<nb, kRedThreads, 0, s>>>(L, C, nullptr, 0.0, cnt, beta, y, n, norm2_dev ? 1 : 0,
-                                             vec ? 1 : 0, rs.part, rs.counter, norm2_dev);
-  CHEB_LAUNCH_CHECK("maxpy_kernel");
-  return CHEB_OK;
+  return maxpy_launch<T>(rs, src, coef, nullptr, 0.0, cnt, beta, y, n, norm2_dev, s);
 }
 
 template <typename T>
 int k_maxpy_dev(const ReduceScratch& rs, const T* const* src, const double* coef_dev, double sign,
                 int cnt, double beta, T* y, size_t n, double* norm2_dev, cudaStream_t s) {
-  if (cnt > kMaxVecs) { set_error("too many vectors in multi-axpy"); return CHEB_ERR_ARG; }
-  VecList<T> L;
-  CoefList C;
-  bool vec = aligned16(y);
-  for (int i = 0; i < kMaxVecs; ++i) {
-    L.p[i] = i < cnt ? src[i] : nullptr;
-    C.c[i] = 0.0;
-    if (i < cnt) vec = vec && aligned16(src[i]);
-  }
-  const int nb = red_blocks(n);
-  maxpy_kernel<T><<<nb, kRedThreads, 0, s>>>(L, C, coef_dev, sign, cnt, beta, y, n, norm2_dev ? 1 : 0,
-                                             vec ? 1 : 0, rs.part, rs.counter, norm2_dev);
-  CHEB_LAUNCH_CHECK("maxpy_kernel");
-  return CHEB_OK;
+  return maxpy_launch<T>(rs, src, nullptr, coef_dev, sign, cnt, beta, y, n, norm2_dev, s);
 }
 
 // y *= 1 / sqrt(*norm2) (when positive)

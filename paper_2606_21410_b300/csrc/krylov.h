@@ -1,6 +1,9 @@
 // Vector-kernel launchers shared by the solver drivers.
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "internal.h"
 
 namespace cheb {
@@ -11,6 +14,22 @@ constexpr int kRedBlocks = 592;   // reduction CTAs (4 per SM)
 template <typename T>
 struct VecList { const T* p[kMaxVecs]; };
 struct CoefList { double c[kMaxVecs]; };
+
+// f(std::integral_constant<int, N>()) for N == cnt, 0 <= cnt <= kMaxVecs
+// (else CHEB_ERR_ARG).  The fused multi-vector kernels are compiled for each
+// exact vector count: a kernel written for a bound with a run-time count
+// issues the loads and FMAs of the absent vectors as predicated-off
+// instructions (for a one-vector norm, 40 times the issue slots it needs).
+template <typename F, int... I>
+inline int count_dispatch_impl(int cnt, F& f, std::integer_sequence<int, I...>) {
+  int r = CHEB_ERR_ARG;
+  (void)((cnt == I ? (r = f(std::integral_constant<int, I>()), true) : false) || ...);
+  return r;
+}
+template <typename F>
+inline int count_dispatch(int cnt, F&& f) {
+  return count_dispatch_impl(cnt, f, std::make_integer_sequence<int, kMaxVecs + 1>());
+}
 
 // Scratch of the deterministic reductions: kMaxVecs+1 partial rows of
 // kRedBlocks doubles and a completion counter (zero between launches).
