@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--ncu-step", action="store_true",
                     help="after the warm-up, run one step between cudaProfilerStart/Stop and exit "
                          "(for ncu --profile-from-start off)")
+    ap.add_argument("--pmat", type=int, default=0, choices=[0, 1],
+                    help="FP32 preconditioner matrices: 0 rounded to TF32 (the library default, two "
+                         "tensor-core products per step), 1 to FP32 accuracy (three products)")
     ap.add_argument("--recycle", type=int, default=0,
                     help="carry LGMRES augmentation vectors across refinement steps (1) or not (0)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-instance batch keys")
@@ -291,8 +294,9 @@ def profile_record(kernel, workload):
     """Counters of `kernel` on `workload` from a ``traffic-record:`` line of a
     summary under profiles/ (one ncu capture: DRAM bytes read + written per
     launch, and for FP64 kernels the executed FP64 flops per launch).  The
-    record names the kernel's source file and its SHA-256 at capture time;
-    when the source has changed since, the counters no longer describe the
+    record names the kernel's source files and their SHA-256 at capture time
+    ("sources": [{"path", "sha256"}, ...], or one "source" / "source_sha256");
+    when any of them has changed since, the counters no longer describe the
     kernel and are reported as null."""
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
@@ -304,8 +308,9 @@ def profile_record(kernel, workload):
                 continue
             if rec.get("kernel") != kernel or rec.get("workload") != workload:
                 continue
-            src = os.path.join(ROOT, rec["source"])
-            fresh = os.path.exists(src) and _sha256(src) == rec.get("source_sha256")
+            srcs = rec.get("sources") or [{"path": rec.get("source"), "sha256": rec.get("source_sha256")}]
+            fresh = all(s.get("path") and os.path.exists(os.path.join(ROOT, s["path"])) and
+                        _sha256(os.path.join(ROOT, s["path"])) == s.get("sha256") for s in srcs)
             return {"bytes_per_launch": rec.get("dram_bytes_per_launch") if fresh else None,
                     "fp64_flops_per_launch": rec.get("fp64_flops_per_launch") if fresh else None,
                     "summary": os.path.relpath(path, ROOT), "fresh": fresh,
@@ -331,7 +336,7 @@ def apply_only(args, n):
 
     def op():
         if args.fdm_only:
-            p.precond_apply(u, 1.5, out)
+            p.precond_apply(u, 1.5, out, matrices=args.pmat)
         else:
             p.apply(K, u, out)
     for _ in range(max(3, args.warmup)):
@@ -494,7 +499,7 @@ def main():
     plans, Ks, bs, hostK, hostb = setup_gpu(levels, args.contrast, args.route32)
     opts = dict(mode=1, rtol=1e-12, reorth=args.reorth, inner_rtol=args.inner_rtol,
                 restart=args.restart, use_graph=args.use_graph, recycle=args.recycle,
-                coarse_rtol=args.coarse_rtol)
+                coarse_rtol=args.coarse_rtol, precond_matrices=args.pmat)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -676,23 +681,25 @@ def main():
         newton = newton_table()
 
     # ---- finest-level timing of the preconditioner (the dominant phase)
-    def time_prec(dtype, reps=10):
+    def time_prec(dtype, matrices, reps=10):
         r = bs[-1].to(dtype)
         out = torch.empty_like(r)
         kref = float(infos[-1]["kref"])
         for _ in range(3):
-            pf.precond_apply(r, kref, out)
+            pf.precond_apply(r, kref, out, matrices=matrices)
         torch.cuda.synchronize()
         a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(reps):
-            pf.precond_apply(r, kref, out)
+            pf.precond_apply(r, kref, out, matrices=matrices)
         b2.record(stream)
         torch.cuda.synchronize()
         return a.elapsed_time(b2) / 1e3 / reps
 
-    tp32 = time_prec(torch.float32)
+    tp32 = time_prec(torch.float32, args.pmat)
     apply["fdm_fp32_ms"] = tp32 * 1e3
+    apply["fdm_fp32_ms_fp32_matrices"] = time_prec(torch.float32, 1) * 1e3
+    apply["fdm_fp32_ms_tf32_matrices"] = time_prec(torch.float32, 0) * 1e3
 
     # ---- roofline of the dominant kernel: the FP32 operator apply (the
     # largest single-kernel share of the solve; the Arnoldi dot/axpy work is
@@ -746,7 +753,8 @@ def main():
                  "achieved": fl / tp32 / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
                  "frac": fl / tp32 / 1e12 / tf32_peak,
                  "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 ratio)",
-                 "note": "whole preconditioner time; split-TF32 issues 3 TF32 MMAs per useful flop"}
+                 "note": "whole preconditioner time; the contractions issue %d TF32 MMAs per useful flop "
+                         "(%s matrices)" % (2 if args.pmat == 0 else 3, "TF32" if args.pmat == 0 else "FP32")}
 
     # ---- the oracle's hierarchical solve on the host cores: CPU baseline and
     # the relative L2 error of the GPU solutions at every level
@@ -773,7 +781,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
             "config": dict(workload_config(levels, args.contrast),
                            coarse_levels_rtol=args.coarse_rtol or 1e-12, recycle=args.recycle,
-                           inner_rtol=args.inner_rtol),
+                           inner_rtol=args.inner_rtol,
+                           precond_matrices="tf32" if args.pmat == 0 else "fp32"),
             "solves_per_s": world * args.steps / elapsed,
             "iterations_per_level": [i["iterations"] for i in infos],
             "seconds_per_level": [i["seconds"] for i in infos],

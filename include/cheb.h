@@ -215,7 +215,19 @@ typedef struct cheb_solve_opts {
   double coarse_rtol;  /* hierarchies: rtol of the levels below the finest (their
                           solutions only start the next level); 0 = rtol */
   int batch_mode;      /* cheb_solve_batched / cheb_picard_batched: CHEB_BATCH_* */
+  int precond_matrices; /* FP32 FDM applications on the tensor cores: CHEB_PMAT_TF32
+                          (the default) uses the eigenvector matrices rounded to TF32,
+                          two TF32 products per step; CHEB_PMAT_FP32 the matrices to
+                          FP32 accuracy (split pair), three products.  Either way the
+                          field is contracted to FP32 accuracy, so the preconditioner
+                          is a fixed linear map; TF32 matrices change it by about 2^-11
+                          relative and leave the solve's tolerance as it is (the FP64
+                          refinement and its stopping test keep their form).  FP64
+                          applications always use FP64 matrices. */
 } cheb_solve_opts;
+
+/* Precision of the FP32 preconditioner's eigenvector matrices (opts.precond_matrices). */
+enum cheb_pmat { CHEB_PMAT_TF32 = 0, CHEB_PMAT_FP32 = 1 };
 
 /* How a batch iterates: LOCKSTEP = every instance in one iteration stream
  * (batched line passes over an (instance, line-tile) work list, batched
@@ -251,7 +263,7 @@ typedef struct cheb_solve_info {
 /* Defaults: MIXED, rtol 1e-12, restart 30, augment 3, maxiter 2000,
  * inner_rtol 1e-4, inner_maxiter 400, max_refinements 30, FDM, kref auto,
  * use_graph 0, recycle 0, formulation REPLACE, coarse_rtol 0 (= rtol),
- * batch_mode AUTO. */
+ * batch_mode AUTO, precond_matrices TF32. */
 void cheb_solve_opts_default(cheb_solve_opts* opts);
 
 /* Solve A u = b (Alg. 2 with the Krylov solver LGMRES; boundary rows as in
@@ -418,8 +430,15 @@ int cheb_solve_hierarchy_fine(int levels, const cheb_plan* plans, const double* 
 int cheb_precond_apply_t(cheb_plan plan, int prec, double kref, const void* y, void* z);
 
 /* z = M^{-1} r for the FDM preconditioner with conductivity kref > 0
- * (device fields of type prec). */
+ * (device fields of type prec; FP32 with the eigenvector matrices to FP32
+ * accuracy, i.e. cheb_precond_apply_m with CHEB_PMAT_FP32). */
 int cheb_precond_apply(cheb_plan plan, int prec, double kref, const void* r, void* z);
+
+/* Same with the FP32 matrix precision given (matrices: CHEB_PMAT_*; ignored
+ * for CHEB_FP64 and on grids the tensor-core contraction does not cover).
+ * CHEB_PMAT_TF32 is the preconditioner the FP32 inner solves apply by default.
+ * CHEB_ERR_ARG for an unknown matrices value. */
+int cheb_precond_apply_m(cheb_plan plan, int prec, int matrices, double kref, const void* r, void* z);
 
 /* ------------------------------------------------------------------------
  * Instrumentation

@@ -25,6 +25,7 @@ ROUTE_AUTO, ROUTE_TRANSFORM, ROUTE_DENSE, ROUTE_TENSOR = -1, 0, 1, 2
 PRECOND_NONE, PRECOND_FDM = 0, 2
 FORM_REPLACE, FORM_ELIMINATE = 0, 1
 BATCH_AUTO, BATCH_LOCKSTEP, BATCH_CONCURRENT = 0, 1, 2
+PMAT_TF32, PMAT_FP32 = 0, 1
 
 
 def solve_opts(**kw) -> SolveOpts:
@@ -326,13 +327,16 @@ class Plan:
               "cheb_precond_apply_t")
         return out
 
-    def precond_apply(self, r: torch.Tensor, kref: float, out=None) -> torch.Tensor:
-        """z = M^{-1} r for the fast-diagonalization preconditioner (``cheb_precond_apply``)."""
+    def precond_apply(self, r: torch.Tensor, kref: float, out=None, matrices: int = PMAT_FP32) -> torch.Tensor:
+        """z = M^{-1} r for the fast-diagonalization preconditioner
+        (``cheb_precond_apply_m``); matrices = PMAT_FP32 (eigenvector matrices
+        to FP32 accuracy) or PMAT_TF32 (rounded to TF32, the FP32 inner
+        solves' default) for FP32 fields."""
         r = self._field(r, "r")
         out = self._out(out, r)
         self._sync_stream()
-        check(lib.cheb_precond_apply(self._h, _PREC[r.dtype], float(kref), _vp(r), _vp(out)),
-              "cheb_precond_apply")
+        check(lib.cheb_precond_apply_m(self._h, _PREC[r.dtype], int(matrices), float(kref), _vp(r), _vp(out)),
+              "cheb_precond_apply_m")
         return out
 
 

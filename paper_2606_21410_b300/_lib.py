@@ -45,6 +45,7 @@ class SolveOpts(C.Structure):
         ("formulation", i32),
         ("coarse_rtol", C.c_double),
         ("batch_mode", C.c_int),
+        ("precond_matrices", i32),
     ]
 
 
@@ -91,6 +92,7 @@ _SIGS = {
     "cheb_solve_opts_default": (None, [C.POINTER(SolveOpts)]),
     "cheb_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolveOpts), C.POINTER(SolveInfo)]),
     "cheb_precond_apply": (i32, [vp, i32, C.c_double, vp, vp]),
+    "cheb_precond_apply_m": (i32, [vp, i32, i32, C.c_double, vp, vp]),
     "cheb_picard_solve": (i32, [vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, i32,
                                 C.POINTER(SolveOpts), C.POINTER(SolveInfo), i32p, f64p]),
     "cheb_solve_batched": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),

@@ -37,6 +37,7 @@ namespace cheb {
 int plan_fdm(cheb_plan_s* p, Fdm** f);
 int plan_kref(cheb_plan_s* p, const double* K, double* kref, cudaStream_t s);
 void resolve_opts(const cheb_solve_opts* in, cheb_solve_opts* out);
+bool pmat_ok(const cheb_solve_opts& o);
 
 namespace {
 
@@ -1220,9 +1221,13 @@ int lockstep_solve(int count, const cheb_plan* plans, const double* const* K, co
     }
   } unmask{&E};
   int st;
+  if (!pmat_ok(o)) return CHEB_ERR_ARG;
   if ((st = engine_setup(E, count, plans, o.precond))) return st;
   for (int i = 0; i < count; ++i)
-    if (E.fdm[i]) E.fdm[i]->active = E.act + i;
+    if (E.fdm[i]) {
+      E.fdm[i]->active = E.act + i;
+      E.fdm[i]->tf32_mats = o.precond_matrices == CHEB_PMAT_TF32;
+    }
   const size_t tb = sizeof(double) * (size_t)E.total;
   double *Kb = nullptr, *bb = nullptr, *ub = nullptr, *Kp = nullptr, *u0 = nullptr, *G[3] = {nullptr, nullptr, nullptr};
   struct Free {

@@ -84,24 +84,24 @@ template <typename T> struct Dft<T, 8> {
     C a1 = cadd(v[1], v[5]), a5 = csub(v[1], v[5]);
     C a2 = cadd(v[2], v[6]), a6 = csub(v[2], v[6]);
     C a3 = cadd(v[3], v[7]), a7 = csub(v[3], v[7]);
-    {  // a5 *= w8 = h (1 - i); a6 *= -i; a7 *= w8^3 = h (-1 - i)
-      C t;
-      t.x = h * (a5.x + a5.y); t.y = h * (a5.y - a5.x); a5 = t;
-      a6 = cmul_mi(a6);
-      t.x = h * (a7.y - a7.x); t.y = -h * (a7.x + a7.y); a7 = t;
-    }
+    // a5 w8 = h p5 (w8 = h (1 - i)), a7 w8^3 = h p7 (w8^3 = h (-1 - i)), a6 w8^2 = -i a6;
+    // the factor h is applied by the output FMAs
+    C p5, p7;
+    p5.x = a5.x + a5.y; p5.y = a5.y - a5.x;
+    p7.x = a7.y - a7.x; p7.y = -(a7.x + a7.y);
+    a6 = cmul_mi(a6);
     C b0 = cadd(a0, a2), b2 = csub(a0, a2);
     C b1 = cadd(a1, a3), b3 = cmul_mi(csub(a1, a3));
     C b4 = cadd(a4, a6), b6 = csub(a4, a6);
-    C b5 = cadd(a5, a7), b7 = cmul_mi(csub(a5, a7));
+    const C q5 = cadd(p5, p7), q7 = cmul_mi(csub(p5, p7));  // b5 = h q5, b7 = h q7
     v[0] = cadd(b0, b1);
     v[4] = csub(b0, b1);
     v[2] = cadd(b2, b3);
     v[6] = csub(b2, b3);
-    v[1] = cadd(b4, b5);
-    v[5] = csub(b4, b5);
-    v[3] = cadd(b6, b7);
-    v[7] = csub(b6, b7);
+    v[1].x = b4.x + h * q5.x; v[1].y = b4.y + h * q5.y;
+    v[5].x = b4.x - h * q5.x; v[5].y = b4.y - h * q5.y;
+    v[3].x = b6.x + h * q7.x; v[3].y = b6.y + h * q7.y;
+    v[7].x = b6.x - h * q7.x; v[7].y = b6.y - h * q7.y;
   }
 };
 

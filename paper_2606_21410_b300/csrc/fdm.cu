@@ -772,8 +772,8 @@ static int rot_sweep(const cheb_plan_s* p, Fdm& f, float** U, int& cur, int q, U
     UmmaEpi plain;
     plain.active = f.active;
     last.active = f.active;
-    const int st = umma_tf32x3_rot(U[cur], f.uw[a][2 * q], f.uw[a][2 * q + 1], U[1 - cur], (int)(ptot / K), K, K,
-                                   a == L ? last : plain, s);
+    const int st = umma_tf32x3_rot(U[cur], f.uw[a][2 * q], f.tf32_mats ? nullptr : f.uw[a][2 * q + 1], U[1 - cur],
+                                   (int)(ptot / K), K, K, a == L ? last : plain, s);
     if (st) return st;
     if (!(a == L && last.mode == 2)) cur = 1 - cur;
   }

@@ -37,6 +37,10 @@ struct Fdm {
   // (hi, lo) of S, S^{-1}, S^T, S^{-T}, each umma_n_tile(mp) x mp.
   bool rot = false;
   float* uw[3][8] = {};
+  // the contractions use the TF32-rounded matrices alone (hi of each pair:
+  // two products per step) instead of the split pairs (three products); set
+  // by each solve from its options
+  bool tf32_mats = false;
   // batched solves: the kernels of this preconditioner return at entry while
   // *active == 0 (the instance has converged); null outside batches.  The
   // small-grid GEMM contractions (no tcgen05 route) are not masked.

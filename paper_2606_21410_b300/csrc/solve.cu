@@ -36,7 +36,7 @@ struct CycleGraph {
   int m_eff = -1;
   const void* K = nullptr;
   double kref = 0.0;
-  int precond = -1, reorth = -1, transpose = -1, m = -1, k = -1;
+  int precond = -1, pmat = -1, reorth = -1, transpose = -1, m = -1, k = -1;
 };
 
 template <typename T>
@@ -160,6 +160,7 @@ struct LgOpts {
   bool transpose = false;  // solve with A^T and M^{-T} (adjoint)
   bool use_graph = false;  // run Arnoldi cycles as captured CUDA graphs
   int precond = CHEB_PRECOND_FDM;
+  int pmat = CHEB_PMAT_TF32;  // FP32 preconditioner matrices (part of the graph key)
   double kref = 1.0;
   double tol_abs = 0.0;  // stop when ||c - B x|| <= tol_abs
   const void* jac[3] = {nullptr, nullptr, nullptr};  // Newton: operator J (C_a fields, type T)
@@ -285,7 +286,8 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
   CHEB_CUDA(cudaMemcpyAsync(w.dorder, w.horder, sizeof(int) * std::max(1, naug), cudaMemcpyHostToDevice, s));
   CycleGraph& cg = B.graphs[m_eff];
   const bool match = cg.exec && cg.m_eff == m_eff && cg.K == (const void*)K && cg.kref == o.kref &&
-                     cg.precond == o.precond && cg.reorth == (int)o.reorth && cg.transpose == (int)o.transpose &&
+                     cg.precond == o.precond && cg.pmat == o.pmat && cg.reorth == (int)o.reorth &&
+                     cg.transpose == (int)o.transpose &&
                      cg.m == o.m && cg.k == o.k;
   if (!match) {
     if (cg.exec) { cudaGraphExecDestroy(cg.exec); cg.exec = nullptr; }
@@ -334,7 +336,7 @@ static int graph_cycle(cheb_plan_s* p, Workspace& w, const LgOpts& o, const T* K
     ce = cudaGraphInstantiate(&cg.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ce != cudaSuccess) { cg.exec = nullptr; return cuda_fail(ce, "cudaGraphInstantiate"); }
-    cg.m_eff = m_eff; cg.K = K; cg.kref = o.kref; cg.precond = o.precond; cg.reorth = o.reorth;
+    cg.m_eff = m_eff; cg.K = K; cg.kref = o.kref; cg.precond = o.precond; cg.pmat = o.pmat; cg.reorth = o.reorth;
     cg.transpose = o.transpose; cg.m = o.m; cg.k = o.k;
     cg.nkernels = thread_launches() - l0;
     add_launches(-cg.nkernels);  // recorded, not run: counted at each replay
@@ -618,6 +620,7 @@ static void default_opts(cheb_solve_opts& o) {
   o.formulation = CHEB_FORM_REPLACE;
   o.coarse_rtol = 0.0;
   o.batch_mode = CHEB_BATCH_AUTO;
+  o.precond_matrices = CHEB_PMAT_TF32;
 }
 
 // lockstep batch engine (batch.cu)
@@ -644,6 +647,12 @@ int plan_kref(cheb_plan_s* p, const double* K, double* kref, cudaStream_t s) {
   if ((st = sync_read(w, 1, s))) return st;
   *kref = std::exp(w.hscal[0] / (double)w.n);
   return CHEB_OK;
+}
+
+bool pmat_ok(const cheb_solve_opts& o) {
+  if (o.precond_matrices == CHEB_PMAT_TF32 || o.precond_matrices == CHEB_PMAT_FP32) return true;
+  set_error("precond_matrices must be CHEB_PMAT_TF32 or CHEB_PMAT_FP32");
+  return false;
 }
 
 void resolve_opts(const cheb_solve_opts* in, cheb_solve_opts* out) {
@@ -770,16 +779,19 @@ static int solve_impl(cheb_plan_s* p, const double* K, const double* b, double* 
   if ((st = ensure_ws(p))) return st;
   Workspace& w = *p->ws;
   const size_t n = w.n;
+  if (!pmat_ok(o)) return CHEB_ERR_ARG;
   LgOpts lo;
   lo.m = o.restart;
   lo.k = o.augment;
   lo.reorth = o.reorth != 0;
   lo.precond = o.precond;
+  lo.pmat = o.precond_matrices;
   lo.transpose = transpose;
   lo.use_graph = o.use_graph != 0;
   if (o.precond == CHEB_PRECOND_FDM) {
     if ((st = fdm_setup(p, w.fdm))) return st;
     if ((st = fdm_clear(w.fdm, s))) return st;
+    w.fdm.tf32_mats = o.precond_matrices == CHEB_PMAT_TF32;
     if (o.kref > 0) lo.kref = o.kref;
     else {
       if ((st = k_sum_log(w.rs, K, n, w.dscal, s))) return st;
@@ -1089,6 +1101,7 @@ static int newton_impl(cheb_plan_s* p, const double* K0, double alpha, const dou
   if (o.restart < 1 || o.augment < 0 || o.restart + o.augment + 1 > kMaxVecs) {
     set_error("need restart >= 1, augment >= 0, restart + augment < 40"); return CHEB_ERR_ARG;
   }
+  if (!pmat_ok(o)) return CHEB_ERR_ARG;
   if ((st = ensure_ws(p))) return st;
   Workspace& w = *p->ws;
   const size_t n = w.n;
@@ -1111,6 +1124,7 @@ static int newton_impl(cheb_plan_s* p, const double* K0, double alpha, const dou
   if (o.precond == CHEB_PRECOND_FDM) {
     if ((st = fdm_setup(p, w.fdm))) return st;
     if ((st = fdm_clear(w.fdm, s))) return st;
+    w.fdm.tf32_mats = o.precond_matrices == CHEB_PMAT_TF32;
   }
   const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 148 * 8));
   int rc = CHEB_ERR_NOT_CONVERGED;
@@ -1137,6 +1151,7 @@ static int newton_impl(cheb_plan_s* p, const double* K0, double alpha, const dou
     lo.k = o.augment;
     lo.reorth = o.reorth != 0;
     lo.precond = o.precond;
+    lo.pmat = o.precond_matrices;
     if (o.precond == CHEB_PRECOND_FDM) {
       if (o.kref > 0) lo.kref = o.kref;
       else {
@@ -1436,6 +1451,7 @@ int cheb_precond_apply_t(cheb_plan p, int prec, double kref, const void* y, void
   if ((st = ensure_ws(p))) return st;
   if ((st = fdm_setup(p, p->ws->fdm))) return st;
   if ((st = fdm_clear(p->ws->fdm, p->stream))) return st;
+  p->ws->fdm.tf32_mats = false;  // FP32: the matrices to FP32 accuracy
   if (prec == CHEB_FP64) return fdm_apply_t<double>(p, p->ws->fdm, kref, (const double*)y, (double*)z, p->stream);
   if (prec == CHEB_FP32) {
     st = fdm_apply_t<float>(p, p->ws->fdm, kref, (const float*)y, (float*)z, p->stream);
@@ -1614,11 +1630,20 @@ int cheb_flux_average(cheb_plan p, int axis, const double* K, const double* u, d
 }
 
 int cheb_precond_apply(cheb_plan p, int prec, double kref, const void* r, void* z) {
+  return cheb_precond_apply_m(p, prec, CHEB_PMAT_FP32, kref, r, z);
+}
+
+int cheb_precond_apply_m(cheb_plan p, int prec, int matrices, double kref, const void* r, void* z) {
   if (!p || !r || !z || !(kref > 0)) { set_error("bad argument"); return CHEB_ERR_ARG; }
+  if (matrices != CHEB_PMAT_TF32 && matrices != CHEB_PMAT_FP32) {
+    set_error("matrices must be CHEB_PMAT_TF32 or CHEB_PMAT_FP32");
+    return CHEB_ERR_ARG;
+  }
   int st;
   if ((st = ensure_ws(p))) return st;
   if ((st = fdm_setup(p, p->ws->fdm))) return st;
   if ((st = fdm_clear(p->ws->fdm, p->stream))) return st;
+  p->ws->fdm.tf32_mats = matrices == CHEB_PMAT_TF32;
   if (prec == CHEB_FP64) return fdm_apply<double>(p, p->ws->fdm, kref, (const double*)r, (double*)z, p->stream);
   if (prec == CHEB_FP32) {
     st = fdm_apply<float>(p, p->ws->fdm, kref, (const float*)r, (float*)z, p->stream);

@@ -235,13 +235,21 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-template <int BK>
+// Stage ring of the contraction: [Xh | Xl | Wh | Wl] per stage for three
+// products, [Xh | Xl | Wh] for two, as many stages as about 192 KB hold (the
+// line tile is the one operand streamed from HBM: more stages keep more of
+// it in flight).
+template <int BK, int TERMS>
 struct UmmaCfg {
-  static constexpr int kStages = BK == 32 ? 2 : 4;
+  static constexpr int kStages = TERMS == 3 ? (BK == 32 ? 2 : 4) : (BK == 32 ? 3 : 6);
   static constexpr uint32_t kRow = BK * 4;  // bytes per operand row
 };
 
-template <int BK>
+// TERMS = 3: W given as its split pair, three products per K step.
+// TERMS = 2: W is exactly TF32 (Wl = 0 and never loaded), two products
+// Xh W + Xl W per K step: the matrix is applied as given, the line tile
+// still to FP32 accuracy.
+template <int BK, int TERMS>
 __global__ void __launch_bounds__(kUThreads, 1)
     umma_tf32x3_rot_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmWh,
                            const __grid_constant__ CUtensorMap tmWl, float* __restrict__ Y, int M, int N, int K,
@@ -249,14 +257,14 @@ __global__ void __launch_bounds__(kUThreads, 1)
   // a converged instance of a batched solve: nothing is initialised or
   // allocated yet, every thread of the CTA returns
   if (ep.active && *ep.active == 0) return;
-  constexpr int S = UmmaCfg<BK>::kStages;
-  constexpr uint32_t RB = UmmaCfg<BK>::kRow;
+  constexpr int S = UmmaCfg<BK, TERMS>::kStages;
+  constexpr uint32_t RB = UmmaCfg<BK, TERMS>::kRow;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
   const uint32_t xbytes = kBM * RB, wbytes = (uint32_t)n_tile * RB;
-  const uint32_t stage_bytes = 2u * xbytes + 2u * wbytes;  // [Xh | Xl | Wh | Wl]
+  const uint32_t stage_bytes = 2u * xbytes + (uint32_t)(TERMS - 1) * wbytes;  // [Xh | Xl | Wh (| Wl)]
   const uint32_t bars = base + S * stage_bytes;
   // barriers: full[S] conv[S] empty[S] tfull[2] tempty[2] fin
   auto full = [&](int s) { return bars + 8u * s; };
@@ -309,7 +317,7 @@ __global__ void __launch_bounds__(kUThreads, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmWh)) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmWl)) : "memory");
+      if (TERMS == 3) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmWl)) : "memory");
       int last[S];
       for (int s = 0; s < S; ++s) last[s] = -1;
       int g = 0;
@@ -319,10 +327,10 @@ __global__ void __launch_bounds__(kUThreads, 1)
           const uint32_t ph = (uint32_t)(g / S) & 1u;
           if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
           const uint32_t st = base + s * stage_bytes;
-          mbar_expect_tx(full(s), xbytes + 2u * wbytes);
+          mbar_expect_tx(full(s), xbytes + (uint32_t)(TERMS - 1) * wbytes);
           tma_load_2d(st, &tmX, full(s), c * BK, tile * kBM);
           tma_load_2d(st + 2u * xbytes, &tmWh, full(s), c * BK, 0);
-          tma_load_2d(st + 2u * xbytes + wbytes, &tmWl, full(s), c * BK, 0);
+          if (TERMS == 3) tma_load_2d(st + 2u * xbytes + wbytes, &tmWl, full(s), c * BK, 0);
           last[s] = g;
         }
       }
@@ -354,9 +362,8 @@ __global__ void __launch_bounds__(kUThreads, 1)
             const uint64_t ah = sdesc_k<BK>(st + 32u * kk);
             const uint64_t al = sdesc_k<BK>(st + xbytes + 32u * kk);
             const uint64_t bh = sdesc_k<BK>(st + 2u * xbytes + 32u * kk);
-            const uint64_t bl = sdesc_k<BK>(st + 2u * xbytes + wbytes + 32u * kk);
             umma_tf32(d, ah, bh, idesc, (c | kk) != 0);
-            umma_tf32(d, ah, bl, idesc, 1u);
+            if (TERMS == 3) umma_tf32(d, ah, sdesc_k<BK>(st + 2u * xbytes + wbytes + 32u * kk), idesc, 1u);
             umma_tf32(d, al, bh, idesc, 1u);
           }
           umma_commit(empty(s));
@@ -528,11 +535,11 @@ int make_map(CUtensorMap* m, const float* ptr, int inner, int rows, int box_rows
   return CHEB_OK;
 }
 
-template <int BK>
+template <int BK, int TERMS>
 size_t smem_bytes(int n_tile) {
-  constexpr int S = UmmaCfg<BK>::kStages;
+  constexpr int S = UmmaCfg<BK, TERMS>::kStages;
   // stages, alignment slack, barriers + TMEM slot + abort flag (256 B), tables (2 x 256 floats)
-  return (size_t)S * (2u * kBM + 2u * (size_t)n_tile) * UmmaCfg<BK>::kRow + 1024 + 256 + 2048;
+  return (size_t)S * (2u * kBM + (TERMS - 1u) * (size_t)n_tile) * UmmaCfg<BK, TERMS>::kRow + 1024 + 256 + 2048;
 }
 
 int sm_count() {
@@ -565,12 +572,19 @@ int launch_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M
   int st;
   if ((st = make_map(&mx, X, K, M, kBM, BK))) return st;
   if ((st = make_map(&mh, Wh, K, n_tile, n_tile, BK))) return st;
-  if ((st = make_map(&ml, Wl, K, n_tile, n_tile, BK))) return st;
-  if ((st = ensure_smem_attr((const void*)umma_tf32x3_rot_kernel<BK>, smem_bytes<BK>(256)))) return st;
+  // two-product form: the map of Wl is passed but never read
+  if ((st = make_map(&ml, Wl ? Wl : Wh, K, n_tile, n_tile, BK))) return st;
   const int ntiles = (M + kBM - 1) / kBM;
   const int grid = std::min(ntiles, sm_count());
-  umma_tf32x3_rot_kernel<BK><<<grid, kUThreads, smem_bytes<BK>(n_tile), s>>>(mx, mh, ml, Y, M, N, K, n_tile,
-                                                                               tmem_cols, ep);
+  if (Wl) {
+    if ((st = ensure_smem_attr((const void*)umma_tf32x3_rot_kernel<BK, 3>, smem_bytes<BK, 3>(256)))) return st;
+    umma_tf32x3_rot_kernel<BK, 3><<<grid, kUThreads, smem_bytes<BK, 3>(n_tile), s>>>(mx, mh, ml, Y, M, N, K, n_tile,
+                                                                                  tmem_cols, ep);
+  } else {
+    if ((st = ensure_smem_attr((const void*)umma_tf32x3_rot_kernel<BK, 2>, smem_bytes<BK, 2>(256)))) return st;
+    umma_tf32x3_rot_kernel<BK, 2><<<grid, kUThreads, smem_bytes<BK, 2>(n_tile), s>>>(mx, mh, ml, Y, M, N, K, n_tile,
+                                                                                  tmem_cols, ep);
+  }
   CHEB_LAUNCH_CHECK("umma_tf32x3_rot_kernel");
   return CHEB_OK;
 }
@@ -1209,7 +1223,7 @@ void tf32_split_host(const double* x, size_t n, float* hi, float* lo) {
 
 int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, int M, int N, int K,
                     const UmmaEpi& ep, cudaStream_t s) {
-  if (!umma_ok(M, N, K) || (((uintptr_t)X | (uintptr_t)Wh | (uintptr_t)Wl) & 15)) {
+  if (!umma_ok(M, N, K) || (((uintptr_t)X | (uintptr_t)Wh | (uintptr_t)Wl) & 15) || !Wh) {
     set_error("umma_tf32x3_rot: unsupported shape or alignment");
     return CHEB_ERR_UNSUPPORTED;
   }

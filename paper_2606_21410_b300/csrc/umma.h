@@ -14,7 +14,9 @@ namespace cheb {
 // split-TF32 pair (Wh = tf32(W), Wl = tf32(W - Wh), both n_rows x K with
 // n_rows = umma_n_tile(N) and zero rows past N), Y written as [N][M].
 // Arithmetic: three TF32 tensor-core products Xh Wh + Xh Wl + Xl Wh with
-// FP32 accumulation, X split on the fly; FP32-level accuracy.
+// FP32 accumulation, X split on the fly; FP32-level accuracy.  Wl = null:
+// W is taken as exactly TF32 (Wh) and two products Xh Wh + Xl Wh are formed,
+// so Wh is applied to X with FP32-level accuracy.
 // Requirements (checked by umma_ok): K >= 32, K % 4 == 0, 32 <= N <= 256,
 // M >= 128, 16-byte aligned X and W.  X and Y must not overlap.
 //

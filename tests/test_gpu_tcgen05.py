@@ -223,3 +223,86 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
     ref = FDMPreconditioner(g, 1.1)(r)
     got = _plan(n, bc).precond_apply(_dev(r, torch.float32), 1.1).double().cpu().numpy()
     assert _rel(got, ref) < 1e-4
+
+
+# ------------------------------------- preconditioner with TF32-rounded matrices
+#
+# CHEB_PMAT_TF32 (the default of the FP32 inner solves) contracts the field,
+# split hi + lo, against the eigenvector matrices rounded to TF32 (10 fraction
+# bits: relative entry error <= 2^-11), two products per step.  What must hold:
+# it is a fixed linear map to FP32 accuracy (the Krylov relation of the inner
+# LGMRES needs that, not the exact matrices); it differs from the FP32-matrix
+# preconditioner (the rounding is real); its distance from the exact FDM
+# inverse stays within the perturbation of six rounded matrices,
+# 6 * 2^-11 * max cond(S_a) (measured 3.4e-4 .. 4.2e-4 with the oracle's own
+# bases); and the mixed solves it preconditions reach the same solutions in
+# about as many iterations.
+
+def _cond_S(g):
+    from oracle.precond import _axis_tables
+    return max(np.linalg.cond(_axis_tables(g, a)["S"]) for a in g.axes)
+
+
+@pytest.mark.parametrize("n,bc", CASES)
+def test_tf32_matrix_precond_is_linear_and_close_to_exact(n, bc):
+    import paper_2606_21410_b300 as P
+    g = O.Grid(n, bc=bc)
+    kref = 1.3
+    r1 = W.random_field(g.shape, 26)
+    r2 = W.random_field(g.shape, 27)
+    ref = FDMPreconditioner(g, kref)(r1)
+    p = _plan(n, bc)
+
+    def tf(r):
+        return p.precond_apply(_dev(r, torch.float32), kref, matrices=P.PMAT_TF32).double().cpu().numpy()
+
+    z1, z2 = tf(r1), tf(r2)
+    a, b = 0.75, -1.5
+    z12 = tf(a * r1 + b * r2)
+    lin = _rel(z12, a * z1 + b * z2)
+    assert lin < 1e-5, lin
+    zf = p.precond_apply(_dev(r1, torch.float32), kref, matrices=P.PMAT_FP32).double().cpu().numpy()
+    assert _rel(zf, ref) < 1e-4
+    d_mode = _rel(z1, zf)
+    assert d_mode > 2e-5, d_mode            # the TF32 matrices are in use
+    bound = 6 * 2.0 ** -11 * _cond_S(g)
+    assert _rel(z1, ref) < bound, (_rel(z1, ref), bound)
+
+
+def test_tf32_matrix_mixed_solves_match_oracle_and_fp32_matrices():
+    """Mixed solves of a 65^3 two-phase problem (contrast 100) with either
+    matrix precision reach the oracle's solution; iteration counts within
+    10 %; a captured-graph solve of one precision is not replayed for the
+    other (the graph key holds it)."""
+    import paper_2606_21410_b300 as P
+    n = (65, 65, 65)
+    bc = [0, 0, 1, 1, 1, 1]
+    g = O.Grid(n, bc=bc)
+    X, Y, Z = g.mesh()
+    K = W.two_phase_conductivity(X, Y, Z, W.sphere_packing(0), 1.0, 100.0)
+    b = W.random_field(g.shape, 36)
+    uo, io = O.solve_preconditioned(K, b, g, rtol=1e-12)
+    p = _plan(n, bc)
+    res = {}
+    for pm in (P.PMAT_TF32, P.PMAT_FP32):
+        u, info = p.solve(_dev(K), _dev(b), mode=1, rtol=1e-12, precond_matrices=pm)
+        assert info["status"] == 0
+        assert _rel(u.cpu().numpy(), uo) < 1e-9, (pm, _rel(u.cpu().numpy(), uo))
+        res[pm] = (u.cpu().numpy(), info["iterations"])
+    it_t, it_f = res[P.PMAT_TF32][1], res[P.PMAT_FP32][1]
+    assert abs(it_t - it_f) <= max(3, 0.1 * it_f), (it_t, it_f)
+    for pm in (P.PMAT_TF32, P.PMAT_FP32, P.PMAT_TF32):
+        ug, _ = p.solve(_dev(K), _dev(b), mode=1, rtol=1e-12, precond_matrices=pm, use_graph=1)
+        assert _rel(ug.cpu().numpy(), res[pm][0]) < 1e-11, pm
+
+
+def test_precond_matrices_option_is_checked():
+    import paper_2606_21410_b300 as P
+    from paper_2606_21410_b300._lib import ChebError
+    n, bc = (35, 34, 41), [0, 1, 1, 0, 0, 1]
+    p = _plan(n, bc)
+    r = _dev(W.random_field(p.shape, 28), torch.float32)
+    with pytest.raises(ChebError):
+        p.precond_apply(r, 1.0, matrices=7)
+    with pytest.raises(ChebError):
+        p.solve(_dev(np.ones(p.shape)), _dev(W.random_field(p.shape, 29)), precond_matrices=2)
