@@ -11,11 +11,12 @@
 // FP32 accumulators in tensor memory.  The kernel is persistent (one CTA per
 // SM, tiles strided by the grid) with two accumulators, so the epilogue of
 // one tile overlaps the MMAs of the next.  K runs in chunks of BK FP32
-// (BK = 16: 64-byte swizzle, 4 stages; BK = 32: 128-byte swizzle, 2 stages)
-// through a TMA ring that continues across tiles.  Split-TF32: the line tile
-// is split in shared memory into hi = tf32(x) and lo = tf32(x - hi); the
-// matrix comes pre-split; three MMAs per K step (hi*hi + hi*lo + lo*hi) keep
-// FP32-level accuracy.
+// (BK = 16: 64-byte swizzle; BK = 32: 128-byte swizzle) through a TMA ring
+// that continues across tiles.  Split-TF32: the line tile is split in shared
+// memory into hi = tf32(x) and lo = tf32(x - hi); the matrix comes pre-split,
+// three MMAs per K step (hi*hi + hi*lo + lo*hi) keep FP32-level accuracy
+// (BK = 16, 4 stages); or the matrix is taken as exactly TF32 and two MMAs
+// (hi*W + lo*W) apply it to FP32 accuracy (BK = 32, 3 stages).
 //
 // Warp roles (384 threads): warp 0 issues TMA loads, warp 1 owns tensor
 // memory and issues the MMAs (one lane), warps 4..7 split the line tiles,
@@ -554,15 +555,21 @@ int sm_count() {
   return n;
 }
 
-// K chunk of the pipeline: 16 unless overridden by CHEB_UMMA_BK=32.
-int chunk_k() {
-  static int bk = 0;
+// K chunk of the contraction's ring: 16 columns (64-byte swizzle) for the
+// three-product form, 32 (128-byte swizzle) for the two-product form, where
+// the freed matrix slots leave room for three 64 KB stages (measured at 257^3:
+// 0.433 ms per preconditioner application against 0.455 ms with 16); the
+// environment variable CHEB_UMMA_BK = 16 or 32 overrides both.
+int chunk_k(bool three_products) {
+  static int forced = -1;
   static std::once_flag once;
   std::call_once(once, [] {
     const char* e = std::getenv("CHEB_UMMA_BK");
-    bk = (e && std::atoi(e) == 32) ? 32 : 16;
+    const int v = e ? std::atoi(e) : 0;
+    forced = (v == 16 || v == 32) ? v : 0;
   });
-  return bk;
+  if (forced) return forced;
+  return three_products ? 16 : 32;
 }
 
 template <int BK>
@@ -1230,7 +1237,7 @@ int umma_tf32x3_rot(const float* X, const float* Wh, const float* Wl, float* Y, 
   const int n_tile = umma_n_tile(N);
   int tmem_cols = 32;
   while (tmem_cols < n_tile) tmem_cols *= 2;
-  return chunk_k() == 32 ? launch_rot<32>(X, Wh, Wl, Y, M, N, K, n_tile, tmem_cols, ep, s)
+  return chunk_k(Wl != nullptr) == 32 ? launch_rot<32>(X, Wh, Wl, Y, M, N, K, n_tile, tmem_cols, ep, s)
                          : launch_rot<16>(X, Wh, Wl, Y, M, N, K, n_tile, tmem_cols, ep, s);
 }
 
