@@ -242,34 +242,74 @@ maxpy_kernel(VecList<T> src, CoefList coef, const double* __restrict__ cdev, dou
   if (want_norm) block_reduce_store<T, 1>(acc, 1, false, part, counter, out);
 }
 
+// The element-wise kernels below walk their grid-stride loop four elements
+// at a time (the four loads issued before the first store: four loads in
+// flight per thread instead of one), then the remainder one by one.
 template <typename T>
 __global__ void scale_kernel(T* __restrict__ y, const T* __restrict__ x, double s, size_t n) {
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
   const T sv = (T)s;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) y[e] = sv * x[e];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = x[e + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y[e + u * stride] = sv * v[u];
+  }
+  for (; e < n; e += stride) y[e] = sv * x[e];
 }
 
 // y (To) = s * x (Ti)
 template <typename To, typename Ti>
 __global__ void cast_scale_kernel(To* __restrict__ y, const Ti* __restrict__ x, double s, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride)
-    y[e] = (To)(s * (double)x[e]);
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    Ti v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = x[e + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y[e + u * stride] = (To)(s * (double)v[u]);
+  }
+  for (; e < n; e += stride) y[e] = (To)(s * (double)x[e]);
 }
 
 // y (FP64) += s * x (Ti)
 template <typename Ti>
 __global__ void axpy64_kernel(double* __restrict__ y, const Ti* __restrict__ x, double s, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride)
-    y[e] += s * (double)x[e];
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    Ti v[4];
+    double w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = x[e + u * stride];
+      w[u] = y[e + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y[e + u * stride] = w[u] + s * (double)v[u];
+  }
+  for (; e < n; e += stride) y[e] += s * (double)x[e];
 }
 
 // r = b - r  (r holds A x on entry)
 template <typename T>
 __global__ void residual_kernel(T* __restrict__ r, const T* __restrict__ b, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) r[e] = b[e] - r[e];
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    T v[4], w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = b[e + u * stride];
+      w[u] = r[e + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[e + u * stride] = v[u] - w[u];
+  }
+  for (; e < n; e += stride) r[e] = b[e] - r[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -335,19 +375,42 @@ int k_maxpy_dev(const ReduceScratch& rs, const T* const* src, const double* coef
   return maxpy_launch<T>(rs, src, nullptr, coef_dev, sign, cnt, beta, y, n, norm2_dev, s);
 }
 
-// y *= 1 / sqrt(*norm2) (when positive)
+// y *= 1 / sqrt(*norm2) (when positive).  vec: y is 16-byte aligned, and
+// each thread keeps four 16-byte loads in flight.
 template <typename T>
-__global__ void scale_inv_norm_kernel(T* __restrict__ y, const double* __restrict__ norm2, size_t n) {
-  const double nv = *norm2;
-  if (!(nv > 0.0)) return;
-  const T sv = (T)(1.0 / sqrt(nv));
+__global__ void scale_inv_norm_kernel(T* __restrict__ y, const double* __restrict__ norm2, size_t n, int vec) {
+  typedef typename Vec16<T>::t V;
+  constexpr int W = Vec16<T>::W;
+  const double nrm2 = *norm2;
+  if (!(nrm2 > 0.0)) return;
+  const T sv = (T)(1.0 / sqrt(nrm2));
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) y[e] *= sv;
+  const size_t nv = vec ? n / W : 0;
+  V* y4 = reinterpret_cast<V*>(y);
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < nv; e += 4 * stride) {
+    V v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = y4[e + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) Vec16<T>::set(v[u], k, sv * Vec16<T>::at(v[u], k));
+      y4[e + u * stride] = v[u];
+    }
+  }
+  for (; e < nv; e += stride) {
+    V v = y4[e];
+#pragma unroll
+    for (int k = 0; k < W; ++k) Vec16<T>::set(v, k, sv * Vec16<T>::at(v, k));
+    y4[e] = v;
+  }
+  for (size_t t = nv * W + blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += stride) y[t] *= sv;
 }
 
 template <typename T>
 int k_scale_inv_norm(T* y, const double* norm2_dev, size_t n, cudaStream_t s) {
-  scale_inv_norm_kernel<T><<<elem_blocks(n), 256, 0, s>>>(y, norm2_dev, n);
+  scale_inv_norm_kernel<T><<<elem_blocks(n), 256, 0, s>>>(y, norm2_dev, n, aligned16(y) ? 1 : 0);
   CHEB_LAUNCH_CHECK("scale_inv_norm_kernel");
   return CHEB_OK;
 }
