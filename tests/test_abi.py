@@ -72,3 +72,27 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     mod = importlib.util.module_from_spec(spec)
     with pytest.raises(ImportError):
         spec.loader.exec_module(mod)
+
+
+def test_solve_opts_mirror_matches_the_c_struct():
+    """ctypes' SolveOpts has the size and field defaults of cheb_solve_opts:
+    cheb_solve_opts_default clears sizeof(cheb_solve_opts) bytes and fills
+    the defaults, so on a buffer larger than the mirror pre-filled with 0xAB
+    it must touch exactly the mirror's bytes."""
+    import paper_2606_21410_b300 as P
+    size = C.sizeof(P.SolveOpts)
+    buf = (C.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    P.lib.cheb_solve_opts_default(C.cast(buf, C.POINTER(P.SolveOpts)))
+    raw = bytes(buf)
+    assert raw[size:] == b"\xab" * 64
+    assert raw[size - 8:size] != b"\xab" * 8
+    o = P.solve_opts()
+    assert (o.mode, o.rtol, o.restart, o.augment, o.inner_rtol) == (P.SOLVE_MIXED, 1e-12, 30, 3, 1e-4)
+    assert (o.precond, o.batch_mode, o.precond_matrices) == (P.PRECOND_FDM, P.BATCH_AUTO, P.PMAT_TF32)
+
+
+def test_precond_apply_m_rejects_bad_arguments_without_cuda():
+    import paper_2606_21410_b300 as P
+    lib = P.lib
+    assert lib.cheb_precond_apply_m(None, 1, P.PMAT_TF32, 1.0, None, None) == -1
+    assert lib.cheb_precond_apply(None, 1, 1.0, None, None) == -1
