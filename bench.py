@@ -86,6 +86,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, world, device="cuda"):
+    """The largest of the ranks' values (the interval of the slowest replica);
+    one process returns its own.  Every rank must call it (a collective)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
         int(os.environ.get("LOCAL_RANK", 0))
@@ -534,12 +546,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
     launches = lib.cheb_launch_count() - l0
-    elapsed = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
     per_step = elapsed / args.steps
 
     # ---- phase split from one more step with the event profiler on (outside
@@ -661,7 +668,7 @@ def main():
     ue, _, _ = P.solve_hierarchy(plans, Kd2, bd2, **opts)
     out_host.copy_(ue[-1], non_blocking=True)
     torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world)
     h2d = sum(k.numel() * 8 + b.numel() * 8 for k, b in zip(hostK, hostb))
     d2h = out_host.numel() * 8
 
